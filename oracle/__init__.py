@@ -1,0 +1,21 @@
+"""CPU FP64 oracle for the plane-wave Kohn-Sham Hamiltonian and its Davidson
+eigensolver.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or run anything in this package.  The
+CUDA library never calls it and shares no code with it: the only thing both sides
+share is the seeded input generator ``paper_1709_10010_gb300.synthetic``, which
+holds none of the method's arithmetic.
+
+Everything here is plain numpy in float64 / complex128, written to be checked by
+eye against the method's definitions:
+
+* ``basis``       the plane-wave sphere, its reproducible ordering, FFT box size
+* ``hamiltonian`` H|psi> by its plain definition (dense convolution with the grid
+                  potential's DFT) and by the FFT route; the dense H matrix
+* ``davidson``    block Davidson with the Teter-Payne-Allan preconditioner
+* ``mlp``         the learned preconditioner's network, loss, gradients and Adam
+
+Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``) tie each function
+to closed forms, invariants, brute force or library routines, never to itself.
+"""
