@@ -1,0 +1,138 @@
+/*
+ * pwh.h — C ABI of libpwh: the plane-wave pseudopotential Kohn–Sham Hamiltonian
+ * applied to a block of bands, H|psi>, and a block Davidson eigensolver built on
+ * it, on one NVIDIA GB300 (sm_103a).
+ *
+ * The operator is the norm-conserving form (overlap S = 1) of Eq. pauli_ks
+ * (Sec. "Fully relativistic projector augmented-wave method"): the kinetic term
+ * p^2/2m acting on the FFT mesh, the local potential V_LOC(r), and the separable
+ * nonlocal term sum_{ij} D_ij |beta_i><beta_j|.  In the plane-wave basis
+ * c_{k,n}(G) (Sec. "New parallelization levels"), Hartree atomic units:
+ *
+ *   (H psi)_G = 1/2|k+G|^2 psi_G + sum_{G'} Vt(G-G') psi_{G'}
+ *             + sum_{ij} beta_i(G) D_ij <beta_j|psi>
+ *
+ * where Vt is the discrete Fourier transform of V sampled on the FFT grid.
+ *
+ * Conventions for every entry point:
+ *  - Every call validates its arguments and returns a pwh_status; no C++
+ *    exception crosses the ABI.  On failure pwh_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Complex numbers are interleaved (re, im) pairs of doubles (complex128).
+ *  - Band blocks are column-major: band b occupies elements [b*ld, b*ld + npw).
+ *  - Plane waves are in the public order of pwh_get_miller(): ascending |k+G|^2,
+ *    plane waves whose |k+G|^2 agree to a relative 1e-10 ordered
+ *    lexicographically by signed Miller indices (the reproducible ordering of
+ *    Sec. "Large-record data file format").
+ *  - The caller owns psi / hpsi / eigenvalue buffers; the library owns its
+ *    copies of V, beta, D, index maps and workspaces (freed by
+ *    pwh_destroy_system).
+ *  - All device work is ordered on the stream given at creation.  Calls on one
+ *    system are not thread-safe; different systems are independent.
+ */
+#ifndef PWH_H
+#define PWH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pwh_system pwh_system; /* opaque, library-owned */
+
+typedef enum {
+  PWH_OK = 0,
+  PWH_ERR_ARG = 1,           /* invalid argument (null pointer, size, layout) */
+  PWH_ERR_CUDA = 2,          /* a CUDA runtime call or kernel failed */
+  PWH_ERR_OOM = 3,           /* device allocation failed */
+  PWH_ERR_NOT_CONVERGED = 4, /* eigensolver stopped at max_iter; results written */
+  PWH_ERR_NONFINITE = 5,     /* a NaN/Inf appeared in a residual */
+  PWH_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  PWH_ERR_STATE = 7          /* call out of order (e.g. apply before set_potential) */
+} pwh_status;
+
+typedef enum {
+  PWH_FP64 = 0,  /* every step in FP64 */
+  PWH_MIXED = 1  /* FFT + potential in FP32, projector GEMMs on BF16 tensor cores
+                    (FP32 accumulation); inputs and outputs stay complex128 */
+} pwh_precision;
+
+typedef struct {
+  double lattice[9];  /* rows a1, a2, a3 in bohr (row-major 3x3) */
+  double kpoint[3];   /* k in fractional units of the reciprocal vectors b_i */
+  double ecut_ha;     /* wavefunction cutoff, Hartree: 1/2|k+G|^2 <= ecut_ha */
+  int32_t fft[3];     /* FFT grid; 0 => smallest even 2,3,5-smooth N_i >= 4*mmax_i+1,
+                         the alias-free box for G_max = 2 G_c (Sec. "Advanced
+                         implementation of exact (Fock) exchange") */
+  int32_t precision;  /* pwh_precision used by pwh_apply_h */
+  void* stream;       /* cudaStream_t; NULL = legacy default stream */
+} pwh_system_desc;
+
+/* Build the plane-wave sphere {G : 1/2|k+G|^2 <= ecut_ha} (membership decided in
+ * FP64 from integer Miller indices), its public ordering, the FFT box, the
+ * z-stick decomposition used by the FFT passes and the kinetic diagonal.  Host
+ * work plus device uploads on desc->stream.  *out receives a new system.
+ * Errors: PWH_ERR_ARG (null, non-positive cutoff, singular lattice, an explicit
+ * FFT size that is odd, not 2,3,5-smooth, above 512 or below 4*mmax+1),
+ * PWH_ERR_OOM, PWH_ERR_CUDA. */
+pwh_status pwh_create_system(const pwh_system_desc* desc, pwh_system** out);
+
+/* Synchronize the system's stream and free everything it owns.  NULL is a no-op. */
+pwh_status pwh_destroy_system(pwh_system* sys);
+
+/* npw = number of plane waves; fft_out = (N1, N2, N3); nsticks = number of
+ * nonzero z-columns of the sphere.  Any output pointer may be NULL. */
+pwh_status pwh_get_dims(const pwh_system* sys, int64_t* npw, int32_t fft_out[3],
+                        int64_t* nsticks);
+
+/* Copy the Miller indices (m1, m2, m3) of every plane wave, in public order, into
+ * the host array miller[npw*3] (row-major, caller-owned). */
+pwh_status pwh_get_miller(const pwh_system* sys, int32_t* miller);
+
+/* Copy the kinetic diagonal 1/2|k+G|^2 (public order) into host kin[npw]. */
+pwh_status pwh_get_kinetic(const pwh_system* sys, double* kin);
+
+/* Set V_LOC(r): N1*N2*N3 doubles in C order (i3 fastest); grid point
+ * (i1,i2,i3) is r = sum_d (i_d/N_d) a_d.  Copied in (host pointer if
+ * on_device == 0, device pointer otherwise); the caller keeps ownership. */
+pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_device);
+
+/* Set the nonlocal part: nproj projectors beta (complex128, nproj columns of
+ * length npw, column-major ld = npw, public order) and D, either nproj real
+ * diagonal entries (d_is_diag = 1) or an nproj x nproj complex128 Hermitian
+ * matrix (column-major).  nproj = 0 removes the nonlocal term.  Copied in. */
+pwh_status pwh_set_projectors(pwh_system* sys, int32_t nproj, const void* beta,
+                              const void* D, int32_t d_is_diag, int32_t on_device);
+
+/* Select the compute precision of pwh_apply_h (pwh_precision). */
+pwh_status pwh_set_precision(pwh_system* sys, int32_t precision);
+
+/* hpsi = H psi for nb bands.  psi, hpsi: DEVICE complex128, column-major with
+ * leading dimensions ld_psi, ld_hpsi >= npw; they must not overlap.
+ * Asynchronous on the system's stream.  Requires pwh_set_potential first
+ * (PWH_ERR_STATE otherwise).  nb = 0 is a no-op. */
+pwh_status pwh_apply_h(pwh_system* sys, int32_t nb, const void* psi, int64_t ld_psi,
+                       void* hpsi, int64_t ld_hpsi);
+
+/* Same as pwh_apply_h on HOST buffers (ld = npw): copies psi to the device,
+ * applies H, copies hpsi back and synchronizes the stream before returning. */
+pwh_status pwh_apply_h_host(pwh_system* sys, int32_t nb, const void* psi_host,
+                            void* hpsi_host);
+
+/* Internal-order entry used by the eigensolver and by tests of the passes:
+ * band data already permuted to the library's stick order (see
+ * pwh_get_internal_order).  Same layout rules as pwh_apply_h. */
+pwh_status pwh_apply_h_internal(pwh_system* sys, int32_t nb, const void* psi,
+                                int64_t ld_psi, void* hpsi, int64_t ld_hpsi);
+
+/* Copy the permutation from internal (stick-major) to public order into host
+ * int_to_pub[npw]: internal plane wave i is public plane wave int_to_pub[i]. */
+pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);
+
+const char* pwh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWH_H */

@@ -2,7 +2,9 @@
 
 * The basis is the sphere ``{G : 1/2 |k+G|^2 <= ecut}`` (plane-wave coefficients
   c_{k,n}(G) of the Kohn-Sham orbitals, Sec. "New parallelization levels"), with
-  membership decided in FP64 from the integer Miller indices.
+  membership decided in FP64 from the integer Miller indices, inclusive with a
+  relative slack of 1e-12 so that plane waves lying exactly on the cutoff are
+  kept whatever the last-bit rounding of |k+G|^2.
 * Ordering (Sec. "Large-record data file format" asks for a reproducible,
   machine-independent ordering including inside shells of equal modulus):
   ascending |k+G|^2; plane waves whose |k+G|^2 agree to a relative 1e-10 form one
@@ -74,7 +76,7 @@ def sphere(lattice, kpoint, ecut_ha, fft=None) -> Basis:
     M1, M2, M3 = np.meshgrid(r[0], r[1], r[2], indexing="ij")
     cand = np.stack([M1.ravel(), M2.ravel(), M3.ravel()], axis=1)
     q2 = kplusg_sq(lattice, kpoint, cand)
-    keep = 0.5 * q2 <= ecut_ha
+    keep = 0.5 * q2 <= ecut_ha * (1.0 + 1e-12)   # inclusive, robust to 1-ulp rounding
     cand, q2 = cand[keep], q2[keep]
     # sort by |k+G|^2, cut into shells, then lexicographic inside each shell
     o = np.lexsort((cand[:, 2], cand[:, 1], cand[:, 0], q2))

@@ -1,0 +1,224 @@
+"""Python binding of libpwh: the plane-wave Kohn-Sham Hamiltonian H|psi> and a
+block Davidson eigensolver on one GB300.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_lib/libpwh.so`` (built by ``paper_1709_10010_gb300.build``).  PyTorch
+supplies device memory and the CUDA stream.  There is no CPU fallback: if the
+library is missing, loading it raises.
+
+Band blocks are torch complex128 tensors of shape (nb, npw) with unit stride
+along npw: row b is band b, i.e. column-major npw x nb with ld = stride(0).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpwh.so")
+
+PWH_FP64, PWH_MIXED = 0, 1
+PRECISIONS = {"fp64": PWH_FP64, "mixed": PWH_MIXED}
+STATUS = {0: "PWH_OK", 1: "PWH_ERR_ARG", 2: "PWH_ERR_CUDA", 3: "PWH_ERR_OOM",
+          4: "PWH_ERR_NOT_CONVERGED", 5: "PWH_ERR_NONFINITE", 6: "PWH_ERR_TIMEOUT",
+          7: "PWH_ERR_STATE"}
+
+_c_i32, _c_i64, _c_p, _c_d = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+
+
+class SystemDesc(ctypes.Structure):
+    _fields_ = [("lattice", _c_d * 9), ("kpoint", _c_d * 3), ("ecut_ha", _c_d),
+                ("fft", _c_i32 * 3), ("precision", _c_i32), ("stream", _c_p)]
+
+
+class PwhError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# name -> (restype, argtypes); must match include/pwh.h
+SIGNATURES = {
+    "pwh_create_system": (_c_i32, [ctypes.POINTER(SystemDesc), ctypes.POINTER(_c_p)]),
+    "pwh_destroy_system": (_c_i32, [_c_p]),
+    "pwh_get_dims": (_c_i32, [_c_p, ctypes.POINTER(_c_i64), ctypes.POINTER(_c_i32),
+                              ctypes.POINTER(_c_i64)]),
+    "pwh_get_miller": (_c_i32, [_c_p, _c_p]),
+    "pwh_get_kinetic": (_c_i32, [_c_p, _c_p]),
+    "pwh_get_internal_order": (_c_i32, [_c_p, _c_p]),
+    "pwh_set_potential": (_c_i32, [_c_p, _c_p, _c_i32]),
+    "pwh_set_projectors": (_c_i32, [_c_p, _c_i32, _c_p, _c_p, _c_i32, _c_i32]),
+    "pwh_set_precision": (_c_i32, [_c_p, _c_i32]),
+    "pwh_apply_h": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
+    "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libpwh (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpwh not built: {LIB_PATH} is missing "
+                               "(run python -m paper_1709_10010_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise PwhError(status, lib().pwh_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _band_ptr(t, npw: int):
+    """Device pointer and leading dimension of a (nb, npw) complex128 tensor."""
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex128):
+        raise TypeError("band blocks must be CUDA complex128 tensors")
+    if t.dim() != 2 or t.shape[1] != npw or t.stride(1) != 1:
+        raise ValueError(f"expected shape (nb, {npw}) with unit stride along npw")
+    ld = t.stride(0) if t.shape[0] > 1 else npw
+    return ctypes.c_void_p(t.data_ptr()), ld
+
+
+class System:
+    """One plane-wave system (cell, k-point, cutoff) living on the current GPU."""
+
+    def __init__(self, lattice, kpoint=(0.0, 0.0, 0.0), ecut_ha=10.0, fft=(0, 0, 0),
+                 precision="fp64", stream=None):
+        d = SystemDesc()
+        lat = np.asarray(lattice, dtype=np.float64).reshape(9)
+        for i in range(9):
+            d.lattice[i] = float(lat[i])
+        for i in range(3):
+            d.kpoint[i] = float(kpoint[i])
+            d.fft[i] = int(fft[i])
+        d.ecut_ha = float(ecut_ha)
+        d.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        d.stream = ctypes.c_void_p(int(stream))
+        h = ctypes.c_void_p()
+        _check(lib().pwh_create_system(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        n = _c_i64()
+        f = (_c_i32 * 3)()
+        ns = _c_i64()
+        _check(lib().pwh_get_dims(h, ctypes.byref(n), f, ctypes.byref(ns)))
+        self.npw, self.fft, self.nsticks = int(n.value), tuple(int(x) for x in f), int(ns.value)
+        self.nproj = 0
+
+    @classmethod
+    def from_cell(cls, cell, **kw):
+        return cls(cell.lattice, cell.kpoint, cell.ecut_ha, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().pwh_destroy_system(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- basis
+    def miller(self) -> np.ndarray:
+        out = np.empty((self.npw, 3), dtype=np.int32)
+        _check(lib().pwh_get_miller(self._h, out.ctypes.data_as(_c_p)))
+        return out
+
+    def kinetic(self) -> np.ndarray:
+        out = np.empty(self.npw, dtype=np.float64)
+        _check(lib().pwh_get_kinetic(self._h, out.ctypes.data_as(_c_p)))
+        return out
+
+    def internal_order(self) -> np.ndarray:
+        out = np.empty(self.npw, dtype=np.int32)
+        _check(lib().pwh_get_internal_order(self._h, out.ctypes.data_as(_c_p)))
+        return out
+
+    # ---------------------------------------------------------------- inputs
+    def set_potential(self, v_r):
+        torch = _torch()
+        if isinstance(v_r, torch.Tensor):
+            t = v_r.contiguous()
+            assert t.dtype == torch.float64 and t.numel() == int(np.prod(self.fft))
+            _check(lib().pwh_set_potential(self._h, ctypes.c_void_p(t.data_ptr()), int(t.is_cuda)))
+            torch.cuda.current_stream().synchronize() if t.is_cuda else None
+        else:
+            a = np.ascontiguousarray(v_r, dtype=np.float64)
+            assert a.size == int(np.prod(self.fft))
+            _check(lib().pwh_set_potential(self._h, a.ctypes.data_as(_c_p), 0))
+
+    def set_projectors(self, beta, D):
+        """beta: (P, npw) complex128 in public order; D: (P,) real diagonal or
+        (P, P) complex Hermitian."""
+        beta = np.ascontiguousarray(beta, dtype=np.complex128)
+        P = beta.shape[0] if beta.ndim == 2 else 0
+        if P == 0:
+            _check(lib().pwh_set_projectors(self._h, 0, None, None, 1, 0))
+            self.nproj = 0
+            return
+        assert beta.shape == (P, self.npw)
+        D = np.asarray(D)
+        if D.ndim == 1:
+            Dd = np.ascontiguousarray(D, dtype=np.float64)
+            diag = 1
+        else:
+            Dd = np.asfortranarray(D, dtype=np.complex128)  # column-major
+            diag = 0
+        _check(lib().pwh_set_projectors(self._h, P, beta.ctypes.data_as(_c_p),
+                                        Dd.ctypes.data_as(_c_p), diag, 0))
+        self.nproj = P
+
+    def set_precision(self, precision):
+        p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().pwh_set_precision(self._h, p))
+
+    # ---------------------------------------------------------------- apply
+    def apply_h(self, psi, hpsi=None):
+        """hpsi = H psi on the device; psi (nb, npw) complex128 CUDA tensor."""
+        torch = _torch()
+        if hpsi is None:
+            hpsi = torch.empty_like(psi, memory_format=torch.contiguous_format)
+        p, ldp = _band_ptr(psi, self.npw)
+        h, ldh = _band_ptr(hpsi, self.npw)
+        _check(lib().pwh_apply_h(self._h, int(psi.shape[0]), p, ldp, h, ldh))
+        return hpsi
+
+    def apply_h_internal(self, psi, hpsi=None):
+        torch = _torch()
+        if hpsi is None:
+            hpsi = torch.empty_like(psi, memory_format=torch.contiguous_format)
+        p, ldp = _band_ptr(psi, self.npw)
+        h, ldh = _band_ptr(hpsi, self.npw)
+        _check(lib().pwh_apply_h_internal(self._h, int(psi.shape[0]), p, ldp, h, ldh))
+        return hpsi
+
+    def apply_h_host(self, psi: np.ndarray, hpsi: np.ndarray | None = None) -> np.ndarray:
+        """Host (nb, npw) complex128 in, host out; copies inside the call."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        if hpsi is None:
+            hpsi = np.empty_like(psi)
+        assert psi.shape[1] == self.npw and hpsi.shape == psi.shape and hpsi.flags.c_contiguous
+        _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
+                                      hpsi.ctypes.data_as(_c_p)))
+        return hpsi

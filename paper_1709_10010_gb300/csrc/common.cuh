@@ -1,0 +1,185 @@
+// Shared internals of libpwh: status plumbing, complex helpers, the system
+// object.  Host and device code.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pwh.h"
+
+namespace pwh {
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+
+struct Error {
+  pwh_status st;
+  std::string msg;
+};
+
+#define PWH_CHECK_ARG(cond, msg)                                   \
+  do {                                                             \
+    if (!(cond)) throw ::pwh::Error{PWH_ERR_ARG, std::string(msg)}; \
+  } while (0)
+
+#define PWH_CUDA(call)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      throw ::pwh::Error{e_ == cudaErrorMemoryAllocation ? PWH_ERR_OOM : PWH_ERR_CUDA,  \
+                         std::string(#call) + ": " + cudaGetErrorString(e_)};           \
+    }                                                                                   \
+  } while (0)
+
+#define PWH_LAUNCH_CHECK() PWH_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------- complex ------
+template <typename T> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float> { using t = float2; };
+template <typename T> using cx = typename cplx<T>::t;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z; z.x = r; z.y = i; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> add(cx<T> a, cx<T> b) {
+  return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> sub(cx<T> a, cx<T> b) {
+  return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> mul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T> __host__ __device__ __forceinline__ cx<T> mulc(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> scl(cx<T> a, T s) {
+  return mk<T>(a.x * s, a.y * s);
+}
+
+// ------------------------------------------------------------- FFT plan -----
+constexpr int kMaxStages = 10;
+constexpr int kMaxFft = 512;
+
+// One 1D transform length N = prod(radix).  Stage s combines sub-transforms of
+// length M[s] into length L[s] = M[s] * radix[s] (decimation in time); the
+// decimation-in-frequency transform runs the stages in reverse.
+struct FftPlan {
+  int n;
+  int nstages;
+  int radix[kMaxStages];
+  int M[kMaxStages];
+  int L[kMaxStages];
+  int tw_off;    // offset of this length's table e^{+2 pi i t/n}, t in [0,n)
+  int perm_off;  // offset of its digit-reversal table rev[p]
+};
+
+// ------------------------------------------------------------- system -------
+template <typename T> struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct System {
+  // description
+  double lattice[9];
+  double kpoint[3];
+  double ecut;
+  int n1, n2, n3;
+  int precision;
+  cudaStream_t stream;
+
+  // basis (host)
+  int64_t npw = 0;
+  std::vector<int32_t> miller;   // public order, npw*3
+  std::vector<double> kin_pub;   // public order
+  std::vector<int32_t> int_to_pub;
+  int nsticks = 0, ncols = 0;
+  std::vector<int32_t> stick_off;  // nsticks+1, internal offsets
+  std::vector<int32_t> stick_col, stick_y;  // column index, y grid index
+  std::vector<int32_t> col_x;      // x grid index of each column
+
+  // device: maps and tables
+  int32_t* d_int_to_pub = nullptr;
+  double* d_kin = nullptr;          // internal order
+  int32_t* d_stick_off = nullptr;
+  int32_t* d_stick_of = nullptr;    // stick of each internal plane wave
+  int16_t* d_zpos = nullptr;        // m3 mod N3 of each internal plane wave
+  int32_t* d_stick_col = nullptr;
+  int32_t* d_stick_y = nullptr;
+  int32_t* d_col_x = nullptr;
+  FftPlan plan[3];
+  double2* d_tw64 = nullptr;        // twiddle tables, FP64
+  float2* d_tw32 = nullptr;         // same, rounded to FP32
+  int16_t* d_perm = nullptr;        // digit-reversal tables
+
+  // potential (internal layout [i3][i2][i1], scaled by 1/(N1 N2 N3))
+  bool have_v = false;
+  double* d_v64 = nullptr;
+  float* d_v32 = nullptr;
+
+  // projectors (internal plane-wave order, column-major ld = npw)
+  int nproj = 0;
+  bool d_diag = true;
+  double2* d_beta64 = nullptr;
+  double* d_ddiag = nullptr;        // nproj
+  double2* d_dfull = nullptr;       // nproj x nproj
+  float2* d_beta32 = nullptr;       // FP32 copy (mixed mode)
+  void* d_beta_bf16 = nullptr;      // BF16 planar copies for the tensor-core GEMMs
+  void* d_beta_bf16_t = nullptr;
+
+  // workspaces (grown on demand)
+  DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
+  int fft_batch = 32;               // bands per FFT batch (bounded by workspace)
+
+  ~System();
+};
+
+template <typename T> void ensure(DevBuf<T>& b, size_t n) {
+  if (b.n >= n) return;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  PWH_CUDA(cudaMalloc((void**)&b.p, n * sizeof(T)));
+  b.n = n;
+}
+
+// --------------------------------------------------------- entry helpers ----
+template <typename F> pwh_status guarded(F&& f) {
+  try {
+    f();
+    return PWH_OK;
+  } catch (const Error& e) {
+    set_error(e.msg);
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return PWH_ERR_OOM;
+  } catch (...) {
+    set_error("unknown internal error");
+    return PWH_ERR_CUDA;
+  }
+}
+
+// internal launchers (defined in the .cu files)
+void build_fft_plans(System& s);
+template <typename T>
+void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
+                   int64_t ldh, cudaStream_t st);
+void nonlocal_fp64(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
+                   int64_t ldh, cudaStream_t st);
+void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
+                    int64_t ldh, cudaStream_t st);
+void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
+                    int64_t ldh, int precision);
+
+}  // namespace pwh
+
+struct pwh_system {
+  pwh::System s;
+};

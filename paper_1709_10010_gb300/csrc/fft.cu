@@ -1,0 +1,414 @@
+// Local + kinetic part of H|psi>: scatter the plane-wave sphere to z-sticks,
+// inverse 3D FFT, multiply by V_LOC(r), forward 3D FFT, gather back to the
+// sphere and add 1/2|k+G|^2 psi.  The kinetic term acts on the plane-wave
+// coefficients and V_LOC on the real-space FFT mesh (Eq. pauli_ks, Sec. "Fully
+// relativistic projector augmented-wave method"); bands are pushed through the
+// FFT in batches, the single-GPU counterpart of the task-group distribution of
+// V psi_i products (Sec. "New parallelization levels").
+//
+// Conventions: G -> r uses exp(+iG.r) unscaled; r -> G uses exp(-iG.r); the
+// 1/(N1 N2 N3) of the forward transform is folded into the stored V.  The
+// result is the circular convolution sum_{G'} Vt(G-G') psi_{G'} with Vt the
+// grid DFT of V, exactly, for any grid V.
+//
+// Three passes per band batch, all in shared memory:
+//   k_zinv   sticks -> inverse FFT along z               (sphere -> W[b][z][s])
+//   k_plane  per (band, z-plane): inverse FFT along y on the columns that hold
+//            sticks, inverse FFT along x on every row, x V(r), forward FFT
+//            along x, keep the stick columns, forward FFT along y, keep the
+//            stick rows                                  (W -> W, in place)
+//   k_zfwd   forward FFT along z, gather to the sphere, add the kinetic term
+//
+// 1D transforms are in-place mixed-radix (2,3,4,5) Cooley-Tukey: inverse ones
+// decimate in time from digit-reversed input (the scatter writes reversed
+// positions), forward ones decimate in frequency from natural input to
+// digit-reversed output (the gather reads reversed positions), so no pass needs
+// a separate permutation.  Twiddles e^{2 pi i t/N} come from a host FP64 table.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pwh {
+
+// ------------------------------------------------------------ host plans ----
+static void make_plan(int n, FftPlan& p, std::vector<double2>& tw, std::vector<int16_t>& perm) {
+  p.n = n;
+  int r = n, ns = 0;
+  int rad[32];
+  while (r % 4 == 0) { rad[ns++] = 4; r /= 4; }
+  while (r % 2 == 0) { rad[ns++] = 2; r /= 2; }
+  while (r % 3 == 0) { rad[ns++] = 3; r /= 3; }
+  while (r % 5 == 0) { rad[ns++] = 5; r /= 5; }
+  if (r != 1 || ns > kMaxStages) throw Error{PWH_ERR_ARG, "FFT length not 2,3,5-smooth"};
+  if (ns == 0) rad[ns++] = 1;  // n == 1: identity stage
+  p.nstages = ns;
+  int m = 1;
+  for (int s = 0; s < ns; ++s) {
+    p.radix[s] = rad[s];
+    p.M[s] = m;
+    m *= rad[s];
+    p.L[s] = m;
+  }
+  p.tw_off = (int)tw.size();
+  for (int t = 0; t < n; ++t) {
+    double a = 2.0 * M_PI * (double)t / (double)n;
+    tw.push_back(make_double2(std::cos(a), std::sin(a)));
+  }
+  // rev(p): digits c_s of p with place values prod(r_0..r_{s-1}), recombined
+  // as c_{S-1} + r_{S-1}(c_{S-2} + r_{S-2}(... + r_1 c_0)); store its inverse.
+  p.perm_off = (int)perm.size();
+  std::vector<int16_t> irev(n);
+  for (int q = 0; q < n; ++q) {
+    int rem = q, acc = 0;
+    int digit[kMaxStages];
+    for (int s = 0; s < ns; ++s) { digit[s] = rem % rad[s]; rem /= rad[s]; }
+    acc = digit[0];
+    for (int s = 1; s < ns; ++s) acc = digit[s] + rad[s] * acc;
+    irev[acc] = (int16_t)q;
+  }
+  perm.insert(perm.end(), irev.begin(), irev.end());
+}
+
+void build_fft_plans(System& s) {
+  std::vector<double2> tw;
+  std::vector<int16_t> perm;
+  int n[3] = {s.n1, s.n2, s.n3};
+  for (int d = 0; d < 3; ++d) make_plan(n[d], s.plan[d], tw, perm);
+  std::vector<float2> tw32(tw.size());
+  for (size_t i = 0; i < tw.size(); ++i) tw32[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+  PWH_CUDA(cudaMalloc((void**)&s.d_tw64, tw.size() * sizeof(double2)));
+  PWH_CUDA(cudaMalloc((void**)&s.d_tw32, tw.size() * sizeof(float2)));
+  PWH_CUDA(cudaMalloc((void**)&s.d_perm, perm.size() * sizeof(int16_t)));
+  PWH_CUDA(cudaMemcpy(s.d_tw64, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  PWH_CUDA(cudaMemcpy(s.d_tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  PWH_CUDA(cudaMemcpy(s.d_perm, perm.data(), perm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+}
+
+// ---------------------------------------------------------- device FFT ------
+// sin/cos of 2 pi/3, 2 pi/5, 4 pi/5 (mathematical constants)
+#define PWH_S3 0.866025403784438646763723170753
+#define PWH_C5A 0.309016994374947424102293417183
+#define PWH_S5A 0.951056516295153572116439333379
+#define PWH_C5B (-0.809016994374947424102293417183)
+#define PWH_S5B 0.587785252292473129168705954639
+
+// z * (sg * i)
+template <typename T> __device__ __forceinline__ cx<T> rot(cx<T> z, T sg) {
+  return mk<T>(-sg * z.y, sg * z.x);
+}
+
+// In-register DFT of length R with sign sg (+1 inverse, -1 forward).
+template <typename T, int R> __device__ __forceinline__ void dft(cx<T>* a, T sg);
+
+template <typename T> __device__ __forceinline__ void dft2(cx<T>* a) {
+  cx<T> t = a[0];
+  a[0] = add<T>(t, a[1]);
+  a[1] = sub<T>(t, a[1]);
+}
+template <typename T, int R> __device__ __forceinline__ void dft(cx<T>* a, T sg) {
+  if constexpr (R == 2) {
+    dft2<T>(a);
+  } else if constexpr (R == 3) {
+    cx<T> t1 = add<T>(a[1], a[2]);
+    cx<T> t2 = rot<T>(sub<T>(a[1], a[2]), sg * (T)PWH_S3);
+    cx<T> m = sub<T>(a[0], scl<T>(t1, (T)0.5));
+    a[0] = add<T>(a[0], t1);
+    a[1] = add<T>(m, t2);
+    a[2] = sub<T>(m, t2);
+  } else if constexpr (R == 4) {
+    cx<T> s02 = add<T>(a[0], a[2]), d02 = sub<T>(a[0], a[2]);
+    cx<T> s13 = add<T>(a[1], a[3]), d13 = rot<T>(sub<T>(a[1], a[3]), sg);
+    a[0] = add<T>(s02, s13);
+    a[2] = sub<T>(s02, s13);
+    a[1] = add<T>(d02, d13);
+    a[3] = sub<T>(d02, d13);
+  } else if constexpr (R == 5) {
+    cx<T> b1 = add<T>(a[1], a[4]), b2 = add<T>(a[2], a[3]);
+    cx<T> d1 = sub<T>(a[1], a[4]), d2 = sub<T>(a[2], a[3]);
+    cx<T> a0 = a[0];
+    cx<T> r1 = add<T>(a0, add<T>(scl<T>(b1, (T)PWH_C5A), scl<T>(b2, (T)PWH_C5B)));
+    cx<T> r2 = add<T>(a0, add<T>(scl<T>(b1, (T)PWH_C5B), scl<T>(b2, (T)PWH_C5A)));
+    cx<T> i1 = rot<T>(add<T>(scl<T>(d1, (T)PWH_S5A), scl<T>(d2, (T)PWH_S5B)), sg);
+    cx<T> i2 = rot<T>(sub<T>(scl<T>(d1, (T)PWH_S5B), scl<T>(d2, (T)PWH_S5A)), sg);
+    a[0] = add<T>(a0, add<T>(b1, b2));
+    a[1] = add<T>(r1, i1);
+    a[4] = sub<T>(r1, i1);
+    a[2] = add<T>(r2, i2);
+    a[3] = sub<T>(r2, i2);
+  }
+}
+
+// One butterfly of radix R at stage (M, L) of an n-point transform.
+// DIT: twiddle the inputs, then DFT.  DIF (the transpose): DFT, then twiddle.
+template <typename T, int R, bool DIT>
+__device__ __forceinline__ void butterfly(cx<T>* base, int estride, int M, int k1, int twstep,
+                                          const cx<T>* tw, T sg) {
+  cx<T> a[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) a[q] = base[q * M * estride];
+  if (DIT) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      cx<T> w = tw[q * k1 * twstep];
+      w.y *= sg;
+      a[q] = mul<T>(a[q], w);
+    }
+  }
+  dft<T, R>(a, sg);
+  if (!DIT) {
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      cx<T> w = tw[q * k1 * twstep];
+      w.y *= sg;
+      a[q] = mul<T>(a[q], w);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) base[q * M * estride] = a[q];
+}
+
+// nfft independent transforms of length pl.n in shared memory: transform f
+// element e lives at data[f*fstride + e*estride].  All threads of the block
+// take part; ends with __syncthreads().  tw: this length's table in shared
+// memory.  INV: inverse (DIT, +i sign) else forward (DIF, -i sign).
+template <typename T, bool INV>
+__device__ void fft_block(cx<T>* data, int nfft, int fstride, int estride, const FftPlan& pl,
+                          const cx<T>* tw) {
+  const T sg = INV ? (T)1 : (T)-1;
+  const int n = pl.n;
+  for (int ss = 0; ss < pl.nstages; ++ss) {
+    const int s = INV ? ss : pl.nstages - 1 - ss;
+    const int R = pl.radix[s], M = pl.M[s], L = pl.L[s];
+    const int nbf = n / R;
+    const int twstep = n / L;
+    const int total = nfft * nbf;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      int f = t / nbf, j = t - f * nbf;
+      int g = j / M, k1 = j - g * M;
+      cx<T>* base = data + (size_t)f * fstride + (size_t)(g * L + k1) * estride;
+      switch (R) {
+        case 2: butterfly<T, 2, INV>(base, estride, M, k1, twstep, tw, sg); break;
+        case 3: butterfly<T, 3, INV>(base, estride, M, k1, twstep, tw, sg); break;
+        case 4: butterfly<T, 4, INV>(base, estride, M, k1, twstep, tw, sg); break;
+        case 5: butterfly<T, 5, INV>(base, estride, M, k1, twstep, tw, sg); break;
+        default: break;  // radix 1: identity
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T> struct TwT;
+template <> struct TwT<double> { static const double2* get(const System& s) { return s.d_tw64; } };
+template <> struct TwT<float> { static const float2* get(const System& s) { return s.d_tw32; } };
+
+template <typename T> __device__ __forceinline__ cx<T> from64(double2 z) {
+  return mk<T>((T)z.x, (T)z.y);
+}
+
+// ---------------------------------------------------- pass 1: z inverse ----
+template <typename T>
+__global__ void __launch_bounds__(256) k_zinv(const double2* __restrict__ psi, int64_t ldp,
+                                              const int32_t* __restrict__ stick_off,
+                                              const int32_t* __restrict__ stick_of,
+                                              const int16_t* __restrict__ zpos, int nsticks,
+                                              FftPlan pl3, const cx<T>* __restrict__ tw_g,
+                                              const int16_t* __restrict__ perm_g,
+                                              cx<T>* __restrict__ W, int64_t wband,
+                                              int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n3 = pl3.n, ld = n3 + 1;
+  cx<T>* buf = (cx<T>*)smem_raw;
+  cx<T>* tw = buf + spb * ld;
+  int16_t* irev = (int16_t*)(tw + n3);
+  const int b = blockIdx.y;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+    tw[t] = tw_g[pl3.tw_off + t];
+    irev[t] = perm_g[pl3.perm_off + t];
+  }
+  for (int t = threadIdx.x; t < spb * ld; t += blockDim.x) buf[t] = mk<T>(0, 0);
+  __syncthreads();
+  const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
+  const double2* src = psi + (size_t)b * ldp;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    int s = stick_of[i] - s0;
+    buf[s * ld + irev[zpos[i]]] = from64<T>(src[i]);
+  }
+  __syncthreads();
+  fft_block<T, true>(buf, ns, ld, 1, pl3, tw);
+  cx<T>* dst = W + (size_t)b * wband;
+  for (int t = threadIdx.x; t < n3 * spb; t += blockDim.x) {
+    int z = t / spb, s = t - z * spb;
+    if (s < ns) dst[(size_t)z * nsticks + s0 + s] = buf[s * ld + z];
+  }
+}
+
+// ----------------------------------------------------- pass 2: planes ------
+template <typename T>
+__global__ void __launch_bounds__(512) k_plane(cx<T>* __restrict__ W, int64_t wband, int nsticks,
+                                               int ncols, const int32_t* __restrict__ stick_col,
+                                               const int32_t* __restrict__ stick_y,
+                                               const int32_t* __restrict__ col_x,
+                                               const T* __restrict__ V, FftPlan pl1, FftPlan pl2,
+                                               const cx<T>* __restrict__ tw_g,
+                                               const int16_t* __restrict__ perm_g, int rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = pl1.n, n2 = pl2.n;
+  const int ld2 = n2 + 1, ld1 = n1 + 1;
+  cx<T>* C = (cx<T>*)smem_raw;                 // ncols x ld2
+  cx<T>* Rw = C + (size_t)ncols * ld2;         // rows x ld1
+  cx<T>* tw1 = Rw + (size_t)rows * ld1;
+  cx<T>* tw2 = tw1 + n1;
+  int16_t* irev1 = (int16_t*)(tw2 + n2);
+  int16_t* irev2 = irev1 + n1;
+  const int z = blockIdx.x, b = blockIdx.y;
+  const int n3 = gridDim.x;
+  cx<T>* plane = W + (size_t)b * wband + (size_t)z * nsticks;
+  for (int t = threadIdx.x; t < n1; t += blockDim.x) {
+    tw1[t] = tw_g[pl1.tw_off + t];
+    irev1[t] = perm_g[pl1.perm_off + t];
+  }
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    tw2[t] = tw_g[pl2.tw_off + t];
+    irev2[t] = perm_g[pl2.perm_off + t];
+  }
+  for (int t = threadIdx.x; t < ncols * ld2; t += blockDim.x) C[t] = mk<T>(0, 0);
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    C[stick_col[s] * ld2 + irev2[stick_y[s]]] = plane[s];
+  __syncthreads();
+  fft_block<T, true>(C, ncols, ld2, 1, pl2, tw2);   // inverse along y, natural order out
+  const T* Vz = V + (size_t)z * n1 * n2;
+  for (int y0 = 0; y0 < n2; y0 += rows) {
+    const int nr = min(rows, n2 - y0);
+    for (int t = threadIdx.x; t < nr * ld1; t += blockDim.x) Rw[t] = mk<T>(0, 0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
+      int r = t / ncols, c = t - r * ncols;
+      Rw[r * ld1 + irev1[col_x[c]]] = C[c * ld2 + y0 + r];
+    }
+    __syncthreads();
+    fft_block<T, true>(Rw, nr, ld1, 1, pl1, tw1);   // inverse along x
+    for (int t = threadIdx.x; t < nr * n1; t += blockDim.x) {
+      int r = t / n1, x = t - r * n1;
+      Rw[r * ld1 + x] = scl<T>(Rw[r * ld1 + x], Vz[(size_t)(y0 + r) * n1 + x]);
+    }
+    __syncthreads();
+    fft_block<T, false>(Rw, nr, ld1, 1, pl1, tw1);  // forward along x, reversed out
+    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
+      int r = t / ncols, c = t - r * ncols;
+      C[c * ld2 + y0 + r] = Rw[r * ld1 + irev1[col_x[c]]];
+    }
+    __syncthreads();
+  }
+  fft_block<T, false>(C, ncols, ld2, 1, pl2, tw2);  // forward along y, reversed out
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    plane[s] = C[stick_col[s] * ld2 + irev2[stick_y[s]]];
+  (void)n3;
+}
+
+// ---------------------------------------- pass 3: z forward + gather + T ----
+template <typename T>
+__global__ void __launch_bounds__(256) k_zfwd(const cx<T>* __restrict__ W, int64_t wband,
+                                              const int32_t* __restrict__ stick_off,
+                                              const int32_t* __restrict__ stick_of,
+                                              const int16_t* __restrict__ zpos, int nsticks,
+                                              FftPlan pl3, const cx<T>* __restrict__ tw_g,
+                                              const int16_t* __restrict__ perm_g,
+                                              const double* __restrict__ kin,
+                                              const double2* __restrict__ psi, int64_t ldp,
+                                              double2* __restrict__ hpsi, int64_t ldh, int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n3 = pl3.n, ld = n3 + 1;
+  cx<T>* buf = (cx<T>*)smem_raw;
+  cx<T>* tw = buf + spb * ld;
+  int16_t* irev = (int16_t*)(tw + n3);
+  const int b = blockIdx.y;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  for (int t = threadIdx.x; t < n3; t += blockDim.x) {
+    tw[t] = tw_g[pl3.tw_off + t];
+    irev[t] = perm_g[pl3.perm_off + t];
+  }
+  const cx<T>* src = W + (size_t)b * wband;
+  for (int t = threadIdx.x; t < n3 * spb; t += blockDim.x) {
+    int z = t / spb, s = t - z * spb;
+    if (s < ns) buf[s * ld + z] = src[(size_t)z * nsticks + s0 + s];
+  }
+  __syncthreads();
+  fft_block<T, false>(buf, ns, ld, 1, pl3, tw);
+  const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
+  const double2* pb = psi + (size_t)b * ldp;
+  double2* hb = hpsi + (size_t)b * ldh;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    int s = stick_of[i] - s0;
+    cx<T> v = buf[s * ld + irev[zpos[i]]];
+    double2 p = pb[i];
+    double k = kin[i];
+    hb[i] = make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
+  }
+}
+
+// ------------------------------------------------------------ launcher ------
+static int stick_block(int n3) { return n3 <= 64 ? 32 : 16; }
+
+template <typename T>
+static size_t plane_smem(const System& s, int rows) {
+  return ((size_t)s.ncols * (s.n2 + 1) + (size_t)rows * (s.n1 + 1) + s.n1 + s.n2) * sizeof(cx<T>) +
+         (size_t)(s.n1 + s.n2) * sizeof(int16_t);
+}
+
+template <typename T>
+void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
+                   cudaStream_t st) {
+  if (nb <= 0) return;
+  const int64_t wband = (int64_t)s.n3 * s.nsticks;
+  // batch so that the stick buffer stays around 64 MB (L2-resident between passes)
+  int64_t per = wband * (int64_t)sizeof(cx<T>);
+  int batch = (int)std::max<int64_t>(1, std::min<int64_t>(nb, (64ll << 20) / std::max<int64_t>(per, 1)));
+  ensure(s.ws_fft, (size_t)(batch * per));
+  cx<T>* W = (cx<T>*)s.ws_fft.p;
+  const cx<T>* tw = TwT<T>::get(s);
+  const int spb = stick_block(s.n3);
+  const size_t zsmem = ((size_t)spb * (s.n3 + 1) + s.n3) * sizeof(cx<T>) + s.n3 * sizeof(int16_t);
+  // plane pass: as many rows per chunk as fit in 200 KB of shared memory
+  const size_t budget = 200 * 1024;
+  int rows = s.n2;
+  while (rows > 1 && plane_smem<T>(s, rows) > budget) rows = (rows + 1) / 2;
+  const size_t psmem = plane_smem<T>(s, rows);
+  if (psmem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
+  static bool attr_done[2] = {false, false};
+  int ti = sizeof(T) == 8 ? 0 : 1;
+  if (!attr_done[ti]) {
+    PWH_CUDA(cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    PWH_CUDA(cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    PWH_CUDA(cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr_done[ti] = true;
+  }
+  const T* V = sizeof(T) == 8 ? (const T*)s.d_v64 : (const T*)s.d_v32;
+  for (int b0 = 0; b0 < nb; b0 += batch) {
+    int bb = std::min(batch, nb - b0);
+    dim3 gz((s.nsticks + spb - 1) / spb, bb);
+    k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
+                                       s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
+    PWH_LAUNCH_CHECK();
+    dim3 gp(s.n3, bb);
+    k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
+                                        s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
+    PWH_LAUNCH_CHECK();
+    k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
+                                       s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
+                                       hpsi + (size_t)b0 * ldh, ldh, spb);
+    PWH_LAUNCH_CHECK();
+  }
+}
+
+template void local_kinetic<double>(System&, int, const double2*, int64_t, double2*, int64_t,
+                                    cudaStream_t);
+template void local_kinetic<float>(System&, int, const double2*, int64_t, double2*, int64_t,
+                                   cudaStream_t);
+
+}  // namespace pwh

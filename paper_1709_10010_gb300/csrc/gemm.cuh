@@ -1,0 +1,15 @@
+// Internal GEMM launchers of libpwh.
+#pragma once
+#include "common.cuh"
+
+namespace pwh {
+
+// C = alpha * op(A) * B + beta * C (column-major complex); op(A) = A^H when
+// conjA.  rowscale (device, length M, optional) multiplies row m of op(A)*B
+// before alpha: the diagonal D of the nonlocal term.
+template <typename T>
+void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
+           const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
+           const double* rowscale = nullptr);
+
+}  // namespace pwh

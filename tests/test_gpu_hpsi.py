@@ -1,0 +1,158 @@
+"""Parity of the CUDA H|psi> with the FP64 oracle, element by element, through
+the C ABI.  FP64 bar: max |dH| / max |H psi| <= 1e-12.  Mixed bar: derived from
+FP32 FFT + BF16 projector GEMMs (see the tolerance constants)."""
+import numpy as np
+import pytest
+
+from oracle import basis as ob
+from oracle import hamiltonian as oh
+from paper_1709_10010_gb300 import synthetic as syn
+from tests.helpers import case, rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+# FP32 FFT: ~1e-6 relative; BF16 operands (8-bit mantissa) in the projector
+# GEMMs with FP32 accumulation: each product carries <= 2^-8 relative error, the
+# nonlocal term is a fraction of |H psi| -> bound 1e-2 of max |H psi|.
+MIXED_TOL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    from paper_1709_10010_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    return torch
+
+
+def make_system(torch, cell, b, v, beta, D, precision="fp64"):
+    import paper_1709_10010_gb300 as pwh
+    s = pwh.System.from_cell(cell, precision=precision)
+    s.set_potential(v)
+    s.set_projectors(beta, D)
+    return s
+
+
+CASES = [
+    dict(seed=0, a=8.0, natoms=4, ecut_ry=14.0, lmax=1),
+    dict(seed=1, a=10.0, natoms=8, ecut_ry=20.0, lmax=1),          # the 1503-plane-wave cell
+    dict(seed=2, a=9.0, natoms=3, ecut_ry=16.0, lmax=2, k=(0.25, -0.25, 0.25)),
+    dict(seed=3, a=7.3, natoms=5, ecut_ry=12.0, lmax=2, k=(0.1, 0.2, -0.3)),
+]
+
+
+@pytest.mark.parametrize("kw", CASES)
+def test_miller_and_kinetic_match_oracle(torch, kw):
+    cell, b, v, beta, D = case(**kw)
+    s = make_system(torch, cell, b, v, beta, D)
+    np.testing.assert_array_equal(s.miller(), b.miller)
+    assert s.fft == b.fft
+    np.testing.assert_allclose(s.kinetic(), b.kinetic, rtol=1e-15, atol=0)
+    order = s.internal_order()
+    assert sorted(order.tolist()) == list(range(b.npw))
+
+
+@pytest.mark.parametrize("kw", CASES)
+@pytest.mark.parametrize("nb", [1, 7, 40])
+def test_apply_h_fp64_parity(torch, kw, nb):
+    cell, b, v, beta, D = case(**kw)
+    s = make_system(torch, cell, b, v, beta, D)
+    psi = syn.initial_bands(10 + nb, b.npw, nb)
+    ref = oh.apply_h(b, v, beta, D, psi)
+    out = s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    assert rel_err(out, ref) <= FP64_TOL
+    # host-buffer entry point gives the same numbers
+    out_h = s.apply_h_host(psi)
+    assert rel_err(out_h, ref) <= FP64_TOL
+
+
+def test_apply_h_strided_and_full_D(torch):
+    cell, b, v, beta, D = case(seed=5, a=8.0, natoms=3, ecut_ry=14.0, lmax=2)
+    rng = np.random.default_rng(0)
+    P = beta.shape[0]
+    Df = rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P))
+    Df = 0.5 * (Df + Df.conj().T)
+    s = make_system(torch, cell, b, v, beta, Df)
+    psi = syn.initial_bands(3, b.npw, 5)
+    ref = oh.apply_h(b, v, beta, Df, psi)
+    big = torch.zeros((5, b.npw + 37), dtype=torch.complex128, device="cuda")
+    big[:, :b.npw] = torch.from_numpy(psi).cuda()
+    hbig = torch.full((5, b.npw + 11), 7.0 + 0j, dtype=torch.complex128, device="cuda")
+    s.apply_h(big[:, :b.npw], hbig[:, :b.npw])
+    out = hbig[:, :b.npw].cpu().numpy()
+    assert rel_err(out, ref) <= FP64_TOL
+    assert torch.all(hbig[:, b.npw:] == 7.0)   # padding untouched
+
+
+def test_apply_h_edge_cases(torch):
+    cell, b, v, beta, D = case(seed=6)
+    s = make_system(torch, cell, b, v, beta, D)
+    # zero bands: no-op
+    empty = torch.zeros((0, b.npw), dtype=torch.complex128, device="cuda")
+    s.apply_h(empty, empty.clone())
+    # no projectors: kinetic + local only
+    s.set_projectors(np.zeros((0, b.npw), complex), np.zeros(0))
+    psi = syn.initial_bands(4, b.npw, 3)
+    ref = oh.apply_h(b, v, None, None, psi)
+    assert rel_err(s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy(), ref) <= FP64_TOL
+    # V = 0 and no projectors: exactly the kinetic diagonal
+    s.set_potential(np.zeros(b.fft))
+    out = s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    np.testing.assert_allclose(out, b.kinetic[None] * psi, rtol=0, atol=1e-13)
+
+
+def test_apply_before_potential_is_state_error(torch):
+    import paper_1709_10010_gb300 as pwh
+    cell, b, v, beta, D = case(seed=7)
+    s = pwh.System.from_cell(cell)
+    psi = torch.zeros((1, s.npw), dtype=torch.complex128, device="cuda")
+    with pytest.raises(pwh.PwhError) as e:
+        s.apply_h(psi)
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("kw", CASES[:3])
+def test_apply_h_mixed_parity(torch, kw):
+    cell, b, v, beta, D = case(**kw)
+    s = make_system(torch, cell, b, v, beta, D, precision="mixed")
+    psi = syn.initial_bands(21, b.npw, 9)
+    ref = oh.apply_h(b, v, beta, D, psi)
+    out = s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    err = rel_err(out, ref)
+    assert err <= MIXED_TOL
+    assert err > 1e-15        # really ran in reduced precision
+    # the local + kinetic part alone is FP32-accurate
+    s.set_projectors(np.zeros((0, b.npw), complex), np.zeros(0))
+    ref_loc = oh.apply_h(b, v, None, None, psi)
+    out_loc = s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    assert rel_err(out_loc, ref_loc) <= 2e-6
+
+
+def test_apply_h_medium_sampled(torch):
+    """The 34,265-plane-wave cell (a=20, 40 Ry, 64 atoms, 576 projectors) at its
+    FFT box 90^3, 128 bands in the bench's launch configuration; sampled rows of
+    H psi computed one by one by the plain definition."""
+    cfg = syn.CONFIGS["medium"]
+    cell = syn.config_cell("medium", 0)
+    b = ob.sphere(cell.lattice, cell.kpoint, cell.ecut_ha)
+    assert b.npw == 34265 and b.fft == (90, 90, 90)
+    v = syn.potential_grid(cell, b.fft)
+    beta = syn.projectors(cell, b.miller)
+    D = syn.d_diagonal(cell)
+    s = make_system(torch, cell, b, v, beta, D)
+    nb = cfg["nb"]
+    psi = syn.initial_bands(0, b.npw, nb)
+    out = s.apply_h(torch.from_numpy(psi).cuda()).cpu().numpy()
+    rng = np.random.default_rng(1)
+    rows = rng.choice(b.npw, 24, replace=False)
+    bands = rng.choice(nb, 6, replace=False)
+    vt = oh.v_tilde(v)
+    p = oh.becp(beta, psi[bands])                  # (P, nbands)
+    for g in rows:
+        d = b.miller[g][None, :] - b.miller
+        vrow = vt[d[:, 0] % 90, d[:, 1] % 90, d[:, 2] % 90]
+        ref = b.kinetic[g] * psi[bands, g] + psi[bands] @ vrow + (beta[:, g] * D) @ p
+        scale = np.abs(out[bands]).max()
+        assert np.abs(out[bands, g] - ref).max() <= FP64_TOL * scale
