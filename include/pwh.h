@@ -53,9 +53,12 @@ typedef enum {
 } pwh_status;
 
 typedef enum {
-  PWH_FP64 = 0,  /* every step in FP64 */
-  PWH_MIXED = 1  /* FFT + potential in FP32, projector GEMMs on BF16 tensor cores
-                    (FP32 accumulation); inputs and outputs stay complex128 */
+  PWH_FP64 = 0,       /* every step in FP64 */
+  PWH_MIXED = 1,      /* FFT + potential in FP32; projector GEMMs on the BF16
+                         tensor cores with FP32 accumulation, each operand split
+                         into two BF16 terms (hi*hi + hi*lo + lo*hi, about 16
+                         significant bits); inputs and outputs stay complex128 */
+  PWH_MIXED_FAST = 2  /* as PWH_MIXED with one BF16 term per operand (8 bits) */
 } pwh_precision;
 
 typedef struct {
@@ -129,6 +132,11 @@ pwh_status pwh_apply_h_internal(pwh_system* sys, int32_t nb, const void* psi,
 /* Copy the permutation from internal (stick-major) to public order into host
  * int_to_pub[npw]: internal plane wave i is public plane wave int_to_pub[i]. */
 pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);
+
+/* Synchronize the system's stream and report device-side failures: returns
+ * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave
+ * up since the last call, so that its results must be discarded. */
+pwh_status pwh_sync(pwh_system* sys);
 
 const char* pwh_last_error(void);
 

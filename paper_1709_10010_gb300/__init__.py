@@ -19,8 +19,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpwh.so")
 
-PWH_FP64, PWH_MIXED = 0, 1
-PRECISIONS = {"fp64": PWH_FP64, "mixed": PWH_MIXED}
+PWH_FP64, PWH_MIXED, PWH_MIXED_FAST = 0, 1, 2
+PRECISIONS = {"fp64": PWH_FP64, "mixed": PWH_MIXED, "mixed_fast": PWH_MIXED_FAST}
 STATUS = {0: "PWH_OK", 1: "PWH_ERR_ARG", 2: "PWH_ERR_CUDA", 3: "PWH_ERR_OOM",
           4: "PWH_ERR_NOT_CONVERGED", 5: "PWH_ERR_NONFINITE", 6: "PWH_ERR_TIMEOUT",
           7: "PWH_ERR_STATE"}
@@ -54,6 +54,7 @@ SIGNATURES = {
     "pwh_apply_h": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_sync": (_c_i32, [_c_p]),
     "pwh_last_error": (ctypes.c_char_p, []),
 }
 
@@ -192,6 +193,11 @@ class System:
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(lib().pwh_set_precision(self._h, p))
+
+    def sync(self):
+        """Wait for the stream; raises PwhError(PWH_ERR_TIMEOUT) if a bounded
+        device wait gave up."""
+        _check(lib().pwh_sync(self._h))
 
     # ---------------------------------------------------------------- apply
     def apply_h(self, psi, hpsi=None):

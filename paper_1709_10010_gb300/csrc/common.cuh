@@ -135,6 +135,9 @@ struct System {
 
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
+  DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
+  int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
+  int* d_err = nullptr;             // device error word (bounded waits that gave up)
   int fft_batch = 32;               // bands per FFT batch (bounded by workspace)
 
   ~System();
@@ -174,7 +177,8 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
 void nonlocal_fp64(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                    int64_t ldh, cudaStream_t st);
 void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
-                    int64_t ldh, cudaStream_t st);
+                    int64_t ldh, cudaStream_t st, int terms);
+int* device_error_word(System& s);
 void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                     int64_t ldh, int precision);
 

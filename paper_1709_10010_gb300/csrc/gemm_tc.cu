@@ -1,7 +1,37 @@
-// Nonlocal projector step in mixed precision (Eq. pauli_ks, D |beta><beta|):
-// becp = beta^H psi, D-scaling, hpsi += beta (D becp), with FP32 operands and
-// FP32 accumulation on the CUDA cores; the FP64 input bands are rounded to FP32
-// on the way in and the FP32 result is added to the FP64 output.
+// Nonlocal projector step on the 5th-generation tensor cores (tcgen05), BF16
+// operands with FP32 accumulation in tensor memory (Eq. pauli_ks, the separable
+// term sum_ij D_ij |beta_i><beta_j|; the products p_ij = <beta|psi> are the
+// "becp" of Sec. "New parallelization levels"):
+//
+//   becp   = beta^H psi            (M = 2P, N = 2nb, K = npw)
+//   becp'  = D becp                (diagonal D in the reduction, full D as a GEMM)
+//   hpsi  += beta becp'            (M = npw, N = 2nb, K = 2P)
+//
+// Complex products become one real GEMM each by interleaving real and
+// imaginary parts:
+//   becp:  A1[2p+c][G] = (Re,Im) beta_p(G),  B1[2b+c][G] = (Re,Im) psi_b(G);
+//          C1[2p..2p+1][2b..2b+1] holds the four real products, combined as
+//          Re = C[2p][2b] + C[2p+1][2b+1], Im = C[2p][2b+1] - C[2p+1][2b].
+//   back:  A2[G][2p+c] = (Re,Im) beta_p(G),
+//          B2[2b][2p] = Re p', B2[2b][2p+1] = -Im p',
+//          B2[2b+1][2p] = Im p', B2[2b+1][2p+1] = Re p',
+//          so that C2[G][2b] = Re (beta p')_b(G) and C2[G][2b+1] = Im.
+// Both operands are K-major.  Each operand is stored as [hi | lo] with
+// hi = bf16(x), lo = bf16(x - hi); with terms = 3 the GEMM accumulates
+// hi*hi + hi*lo + lo*hi (about 16 significant bits), with terms = 1 hi*hi.
+//
+// Kernel: 128 threads, one 128 x 256 output tile per CTA (tcgen05.mma
+// cta_group::1, M = 128, N = 256, K = 16 per instruction), 4-stage TMA ring of
+// 64-wide K slabs with 128-byte swizzle, one elected thread producing TMA
+// loads, one issuing MMAs, then all four warps draining TMEM with tcgen05.ld.
+// Every mbarrier wait is bounded (about one second of %globaltimer); on
+// timeout the kernel records PWH_ERR_TIMEOUT in a device word, stops issuing,
+// waits (bounded) for the copies it started, frees its tensor memory and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -9,26 +39,350 @@
 
 namespace pwh {
 
-__global__ void k_to_f32(const double2* __restrict__ src, int64_t lds, int64_t npw, int nb,
-                         float2* __restrict__ dst) {
-  int64_t tot = npw * nb;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t % npw, b = t / npw;
-    double2 z = src[b * lds + i];
-    dst[t] = make_float2((float)z.x, (float)z.y);
+constexpr int TC_BM = 128, TC_BN = 256, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;            // 16 KB
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;            // 32 KB
+constexpr int TC_STAGE_BYTES = TC_A_BYTES + TC_B_BYTES;  // 48 KB
+constexpr int TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int TC_TMEM_COLS = 256;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // 1 s
+
+struct TcArgs {
+  int M, N;          // output rows (A rows) and columns (B rows)
+  int kb_seg;        // 64-wide K blocks per [hi|lo] segment
+  int terms;         // 1: hi*hi; 3: hi*hi + hi*lo + lo*hi
+  int kb_per_split;  // logical K blocks per blockIdx.z
+  float* part;       // mode 0: FP32 out[z][n][m]
+  double2* hpsi;     // mode 1: hpsi[b*ldh + m] += (C[m][2b], C[m][2b+1])
+  int64_t ldh;
+  int nb;
+  int* err;          // device error word
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; also gives up early once *abort is raised by another role.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (abort && *abort) return false;
+    if (gtimer() - t0 > TC_WAIT_NS) return false;
+  }
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand tile, rows of 128 bytes,
+// 128-byte swizzle, 8-row groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;                  // version
+  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Logical K block kb -> (A column, B column) in elements, for the [hi|lo]
+// operand layout: term 0 = (hi, hi), term 1 = (hi, lo), term 2 = (lo, hi).
+__device__ __forceinline__ void kb_coords(int kb, int kb_seg, int& xa, int& xb) {
+  int t = kb / kb_seg, r = kb - t * kb_seg;
+  int sa = (t == 2) ? 1 : 0, sb = (t == 1) ? 1 : 0;
+  xa = (sa * kb_seg + r) * TC_BK;
+  xb = (sb * kb_seg + r) * TC_BK;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
+              TcArgs args) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
+  const int kb_total = args.terms * args.kb_seg;
+  const int kb0 = blockIdx.z * args.kb_per_split;
+  const int nkb = max(0, min(kb_total, kb0 + args.kb_per_split) - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // producer: number of K blocks whose loads were started
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = ((kb / TC_STAGES) & 1) ^ 1;
+      if (!mbar_wait(&empty[s], ph, abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      int xa, xb;
+      kb_coords(kb0 + kb, args.kb_seg, xa, xb);
+      uint8_t* sa = smem + s * TC_STAGE_BYTES;
+      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+      tma_load_2d(sa, &tma_a, xa, m0, &full[s]);
+      tma_load_2d(sa + TC_A_BYTES, &tma_b, xb, n0, &full[s]);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = (kb / TC_STAGES) & 1;
+      if (!mbar_wait(&full[s], ph, abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = su32(smem + s * TC_STAGE_BYTES);
+      const uint32_t b0 = a0 + TC_A_BYTES;
+#pragma unroll
+      for (int k = 0; k < TC_BK / 16; ++k)
+        mma_bf16(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc,
+                 (kb > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue: TMEM -> registers -> global
+  const bool ok = mbar_wait(done, 0, nullptr) && !*abort_flag && nkb > 0;
+  tc_fence_after();
+  if (ok) {
+    const int row = warp * 32 + lane;
+    const int m = m0 + row;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (m < args.M) {
+        if (MODE == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            int n = n0 + c0 + j;
+            if (n < args.N) args.part[((size_t)blockIdx.z * args.N + n) * args.M + m] = v[j];
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            int b = (n0 + c0 + j) >> 1;
+            if (b < args.nb) {
+              double2* h = args.hpsi + (size_t)b * args.ldh + m;
+              double2 o = *h;
+              o.x += (double)v[j];
+              o.y += (double)v[j + 1];
+              *h = o;
+            }
+          }
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicExch(args.err, (int)PWH_ERR_TIMEOUT);
+  }
+  // producer: make sure every copy it started has landed before smem goes away
+  if (warp == 0 && lane == 0) {
+    for (int kb = max(0, issued - TC_STAGES); kb < issued; ++kb)
+      mbar_wait(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1, nullptr);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
   }
 }
 
-__global__ void k_add_f32(const float2* __restrict__ src, int64_t npw, int nb,
-                          double2* __restrict__ dst, int64_t ldd) {
+// ------------------------------------------------------- operand packing ----
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// A1[2p+c][G] (becp A operand) and A2[G][2p+c] (back-projection A operand),
+// each [hi | lo] along K, from beta (internal order, FP64, column-major npw x P).
+__global__ void k_pack_beta(const double2* __restrict__ beta, int64_t npw, int P,
+                            __nv_bfloat16* __restrict__ A1, int64_t pitch1, int64_t seg1,
+                            __nv_bfloat16* __restrict__ A2, int64_t pitch2, int64_t seg2) {
+  int64_t tot = npw * P;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t g = t % npw, p = t / npw;
+    double2 z = beta[t];
+    __nv_bfloat16 rh, rl, ih, il;
+    split_bf16((float)z.x, rh, rl);
+    split_bf16((float)z.y, ih, il);
+    __nv_bfloat16* r0 = A1 + (2 * p) * pitch1 + g;
+    __nv_bfloat16* r1 = A1 + (2 * p + 1) * pitch1 + g;
+    r0[0] = rh; r0[seg1] = rl;
+    r1[0] = ih; r1[seg1] = il;
+    __nv_bfloat16* q = A2 + g * pitch2 + 2 * p;
+    q[0] = rh; q[1] = ih;
+    q[seg2] = rl; q[seg2 + 1] = il;
+  }
+}
+
+// B1[2b+c][G] from psi (FP64 complex, column-major npw x nb, leading dim ldp).
+__global__ void k_pack_psi(const double2* __restrict__ psi, int64_t ldp, int64_t npw, int nb,
+                           __nv_bfloat16* __restrict__ B1, int64_t pitch, int64_t seg) {
   int64_t tot = npw * nb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = t % npw, b = t / npw;
-    float2 z = src[t];
-    double2 h = dst[b * ldd + i];
-    dst[b * ldd + i] = make_double2(h.x + (double)z.x, h.y + (double)z.y);
+    int64_t g = t % npw, b = t / npw;
+    double2 z = psi[b * ldp + g];
+    __nv_bfloat16 rh, rl, ih, il;
+    split_bf16((float)z.x, rh, rl);
+    split_bf16((float)z.y, ih, il);
+    __nv_bfloat16* r0 = B1 + (2 * b) * pitch + g;
+    __nv_bfloat16* r1 = B1 + (2 * b + 1) * pitch + g;
+    r0[0] = rh; r0[seg] = rl;
+    r1[0] = ih; r1[seg] = il;
+  }
+}
+
+// becp[p][b] (complex FP32, P x nb column-major) from the split-K partials of
+// C1 (FP32, part[z][n][m], M = 2P, N = 2nb); diagonal D applied when given.
+__global__ void k_becp_reduce(const float* __restrict__ part, int nsplit, int P, int nb,
+                              const double* __restrict__ ddiag, float2* __restrict__ becp) {
+  const int M = 2 * P, N = 2 * nb;
+  int64_t tot = (int64_t)P * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(t % P), b = (int)(t / P);
+    float rr = 0, ri = 0, ir = 0, ii = 0;  // C[2p+x][2b+y]
+    for (int z = 0; z < nsplit; ++z) {
+      const float* pz = part + (size_t)z * M * N;
+      rr += pz[(size_t)(2 * b) * M + 2 * p];
+      ir += pz[(size_t)(2 * b) * M + 2 * p + 1];
+      ri += pz[(size_t)(2 * b + 1) * M + 2 * p];
+      ii += pz[(size_t)(2 * b + 1) * M + 2 * p + 1];
+    }
+    float re = rr + ii, im = ri - ir;
+    if (ddiag) {
+      float d = (float)ddiag[p];
+      re *= d;
+      im *= d;
+    }
+    becp[t] = make_float2(re, im);
+  }
+}
+
+// B2[2b+c'][2p+c] ([hi | lo] along K) from becp' (complex FP32, P x nb).
+__global__ void k_pack_becp(const float2* __restrict__ becp, int P, int nb,
+                            __nv_bfloat16* __restrict__ B2, int64_t pitch, int64_t seg) {
+  int64_t tot = (int64_t)P * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(t % P), b = (int)(t / P);
+    float2 z = becp[t];
+    __nv_bfloat16 rh, rl, ih, il, nh, nl;
+    split_bf16(z.x, rh, rl);
+    split_bf16(z.y, ih, il);
+    split_bf16(-z.y, nh, nl);
+    __nv_bfloat16* r0 = B2 + (size_t)(2 * b) * pitch + 2 * p;
+    __nv_bfloat16* r1 = B2 + (size_t)(2 * b + 1) * pitch + 2 * p;
+    r0[0] = rh; r0[1] = nh; r0[seg] = rl; r0[seg + 1] = nl;
+    r1[0] = ih; r1[1] = rh; r1[seg] = il; r1[seg + 1] = rl;
   }
 }
 
@@ -38,36 +392,154 @@ __global__ void k_d_to_f32(const double2* __restrict__ src, int64_t n, float2* _
     dst[t] = make_float2((float)src[t].x, (float)src[t].y);
 }
 
-void prepare_tc_projectors(System& s) { (void)s; }
+// ---------------------------------------------------------------- host -----
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    PWH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                              cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw Error{PWH_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2D BF16 K-major tensor map: rows x cols (cols contiguous, pitch in elements),
+// box 64 x box_rows, 128-byte swizzle, zero fill out of bounds.
+static CUtensorMap make_map(const void* base, int64_t rows, int64_t cols, int64_t pitch,
+                            int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  if (((uintptr_t)base & 15) || ((pitch * 2) & 15))
+    throw Error{PWH_ERR_ARG, "tensor map base or pitch not 16-byte aligned"};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error{PWH_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
+  return m;
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Operand geometry for this system (K segments padded to whole 64-wide blocks).
+struct TcGeom {
+  int64_t seg1, pitch1;  // becp: K = npw
+  int64_t seg2, pitch2;  // back-projection: K = 2P
+};
+static TcGeom geom(const System& s) {
+  TcGeom g;
+  g.seg1 = round_up(s.npw, TC_BK);
+  g.pitch1 = 2 * g.seg1;
+  g.seg2 = round_up(2 * (int64_t)s.nproj, TC_BK);
+  g.pitch2 = 2 * g.seg2;
+  return g;
+}
+
+void prepare_tc_projectors(System& s) {
+  if (s.nproj == 0) return;
+  TcGeom g = geom(s);
+  const size_t n1 = (size_t)2 * s.nproj * g.pitch1, n2 = (size_t)s.npw * g.pitch2;
+  PWH_CUDA(cudaMalloc(&s.d_beta_bf16, n1 * sizeof(__nv_bfloat16)));
+  PWH_CUDA(cudaMalloc(&s.d_beta_bf16_t, n2 * sizeof(__nv_bfloat16)));
+  PWH_CUDA(cudaMemsetAsync(s.d_beta_bf16, 0, n1 * sizeof(__nv_bfloat16), s.stream));
+  PWH_CUDA(cudaMemsetAsync(s.d_beta_bf16_t, 0, n2 * sizeof(__nv_bfloat16), s.stream));
+  k_pack_beta<<<2048, 256, 0, s.stream>>>(s.d_beta64, s.npw, s.nproj,
+                                         (__nv_bfloat16*)s.d_beta_bf16, g.pitch1, g.seg1,
+                                         (__nv_bfloat16*)s.d_beta_bf16_t, g.pitch2, g.seg2);
+  PWH_LAUNCH_CHECK();
+}
+
+static void launch_tc(int mode, const CUtensorMap& ma, const CUtensorMap& mb, TcArgs a, int gm,
+                      int gn, int gz, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    PWH_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    PWH_CUDA(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    attr = true;
+  }
+  dim3 grid(gm, gn, gz);
+  if (mode == 0)
+    k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  else
+    k_tc_gemm<1><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  PWH_LAUNCH_CHECK();
+}
+
+int* device_error_word(System& s);  // davidson.cu / hpsi.cu
 
 void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
-                    cudaStream_t st) {
+                    cudaStream_t st, int terms) {
   if (s.nproj == 0 || nb <= 0) return;
   const int P = s.nproj;
-  const int64_t n = s.npw * (int64_t)nb;
-  // ws_becp: [psi32 | out32 | becp32 x2 | D32]
-  size_t need = (size_t)(2 * n + 2 * (int64_t)P * nb + (s.d_diag ? 0 : (int64_t)P * P)) * sizeof(float2);
-  ensure(s.ws_becp, need);
-  float2* psi32 = (float2*)s.ws_becp.p;
-  float2* out32 = psi32 + n;
-  float2* becp = out32 + n;
+  TcGeom g = geom(s);
+  // ws_tc: B1 (2 cap x pitch1 bf16) | B2 (2 cap x pitch2 bf16) | becp, becp2, D32 (float2),
+  // laid out for a band capacity; the K padding of B1/B2 is zeroed once per layout
+  if (nb > s.tc_nb_cap || P != s.tc_P) {
+    const int cap = std::max(nb, s.tc_nb_cap);
+    const size_t need = ((size_t)2 * cap * (g.pitch1 + g.pitch2)) * sizeof(__nv_bfloat16) +
+                        ((size_t)2 * P * cap + (size_t)P * P) * sizeof(float2) + 512;
+    ensure(s.ws_tc, need);
+    PWH_CUDA(cudaMemsetAsync(s.ws_tc.p, 0, s.ws_tc.n, st));
+    s.tc_nb_cap = cap;
+    s.tc_P = P;
+  }
+  const size_t b1 = (size_t)2 * s.tc_nb_cap * g.pitch1, b2 = (size_t)2 * s.tc_nb_cap * g.pitch2;
+  __nv_bfloat16* B1 = (__nv_bfloat16*)s.ws_tc.p;
+  __nv_bfloat16* B2 = B1 + b1;
+  float2* becp = (float2*)(((uintptr_t)(B2 + b2) + 255) & ~(uintptr_t)255);
   float2* becp2 = becp + (size_t)P * nb;
   float2* d32 = becp2 + (size_t)P * nb;
-  int g = (int)std::min<int64_t>(152 * 16, (n + 255) / 256);
-  k_to_f32<<<g, 256, 0, st>>>(psi, ldp, s.npw, nb, psi32);
+
+  int gblk = (int)std::min<int64_t>(152 * 16, (s.npw * (int64_t)nb + 255) / 256);
+  k_pack_psi<<<gblk, 256, 0, st>>>(psi, ldp, s.npw, nb, B1, g.pitch1, g.seg1);
   PWH_LAUNCH_CHECK();
-  const float2 one = make_float2(1, 0), zero = make_float2(0, 0);
+
+  // ---- becp GEMM, split over K to fill the GPU
+  const int gm1 = (2 * P + TC_BM - 1) / TC_BM, gn1 = (2 * nb + TC_BN - 1) / TC_BN;
+  const int kbs1 = (int)(g.seg1 / TC_BK);
+  const int kbt1 = terms * kbs1;
+  int split = std::max(1, std::min(kbt1, (2 * 152 + gm1 * gn1 - 1) / (gm1 * gn1)));
+  int kper = (kbt1 + split - 1) / split;
+  split = (kbt1 + kper - 1) / kper;  // every split gets >= 1 block
+  ensure(s.ws_split, (size_t)split * 2 * P * 2 * nb * sizeof(float));
+  CUtensorMap ma1 = make_map(s.d_beta_bf16, 2 * P, 2 * g.seg1, g.pitch1, TC_BM);
+  CUtensorMap mb1 = make_map(B1, 2 * nb, 2 * g.seg1, g.pitch1, TC_BN);
+  TcArgs a1{};
+  a1.M = 2 * P; a1.N = 2 * nb; a1.kb_seg = kbs1; a1.terms = terms; a1.kb_per_split = kper;
+  a1.part = (float*)s.ws_split.p; a1.err = device_error_word(s);
+  launch_tc(0, ma1, mb1, a1, gm1, gn1, split, st);
+  int rb = (int)std::min<int64_t>(1024, ((int64_t)P * nb + 255) / 256);
   if (s.d_diag) {
-    cgemm<float>(s, true, P, nb, (int)s.npw, one, s.d_beta32, s.npw, psi32, s.npw, zero, becp, P, st,
-                 s.d_ddiag);
+    k_becp_reduce<<<rb, 256, 0, st>>>((const float*)s.ws_split.p, split, P, nb, s.d_ddiag, becp);
+    PWH_LAUNCH_CHECK();
   } else {
+    k_becp_reduce<<<rb, 256, 0, st>>>((const float*)s.ws_split.p, split, P, nb, nullptr, becp2);
+    PWH_LAUNCH_CHECK();
     k_d_to_f32<<<64, 256, 0, st>>>(s.d_dfull, (int64_t)P * P, d32);
-    cgemm<float>(s, true, P, nb, (int)s.npw, one, s.d_beta32, s.npw, psi32, s.npw, zero, becp2, P, st);
+    PWH_LAUNCH_CHECK();
+    const float2 one = make_float2(1, 0), zero = make_float2(0, 0);
     cgemm<float>(s, false, P, nb, P, one, d32, P, becp2, P, zero, becp, P, st);
   }
-  cgemm<float>(s, false, (int)s.npw, nb, P, one, s.d_beta32, s.npw, becp, P, zero, out32, s.npw, st);
-  k_add_f32<<<g, 256, 0, st>>>(out32, s.npw, nb, hpsi, ldh);
+  k_pack_becp<<<rb, 256, 0, st>>>(becp, P, nb, B2, g.pitch2, g.seg2);
   PWH_LAUNCH_CHECK();
+
+  // ---- back-projection GEMM, accumulated into hpsi
+  const int gm2 = (int)((s.npw + TC_BM - 1) / TC_BM), gn2 = (2 * nb + TC_BN - 1) / TC_BN;
+  const int kbs2 = (int)(g.seg2 / TC_BK);
+  CUtensorMap ma2 = make_map(s.d_beta_bf16_t, s.npw, 2 * g.seg2, g.pitch2, TC_BM);
+  CUtensorMap mb2 = make_map(B2, 2 * nb, 2 * g.seg2, g.pitch2, TC_BN);
+  TcArgs a2{};
+  a2.M = (int)s.npw; a2.N = 2 * nb; a2.kb_seg = kbs2; a2.terms = terms;
+  a2.kb_per_split = terms * kbs2; a2.hpsi = hpsi; a2.ldh = ldh; a2.nb = nb;
+  a2.err = device_error_word(s);
+  launch_tc(1, ma2, mb2, a2, gm2, gn2, 1, st);
 }
 
 }  // namespace pwh

@@ -65,7 +65,7 @@ void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2*
     nonlocal_fp64(s, nb, psi, ldp, hpsi, ldh, s.stream);
   } else {
     local_kinetic<float>(s, nb, psi, ldp, hpsi, ldh, s.stream);
-    nonlocal_mixed(s, nb, psi, ldp, hpsi, ldh, s.stream);
+    nonlocal_mixed(s, nb, psi, ldp, hpsi, ldh, s.stream, precision == PWH_MIXED_FAST ? 1 : 3);
   }
 }
 

@@ -26,7 +26,8 @@ System::~System() {
   void* ptrs[] = {d_int_to_pub, d_kin, d_stick_off, d_stick_of, d_zpos, d_stick_col,
                   d_stick_y, d_col_x, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
-                  ws_fft.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p};
+                  ws_fft.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
+                  ws_tc.p, d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -221,6 +222,14 @@ __global__ void k_beta_gather(const double2* __restrict__ src, int64_t npw, int 
 
 void prepare_tc_projectors(System& s);  // tensor-core operand copies (gemm_tc.cu)
 
+int* device_error_word(System& s) {
+  if (!s.d_err) {
+    PWH_CUDA(cudaMalloc((void**)&s.d_err, sizeof(int)));
+    PWH_CUDA(cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream));
+  }
+  return s.d_err;
+}
+
 }  // namespace pwh
 
 using namespace pwh;
@@ -234,7 +243,7 @@ pwh_status pwh_create_system(const pwh_system_desc* desc, pwh_system** out) {
     PWH_CHECK_ARG(desc && out, "null argument");
     *out = nullptr;
     PWH_CHECK_ARG(std::isfinite(desc->ecut_ha) && desc->ecut_ha > 0, "ecut_ha must be > 0");
-    PWH_CHECK_ARG(desc->precision == PWH_FP64 || desc->precision == PWH_MIXED,
+    PWH_CHECK_ARG(desc->precision >= PWH_FP64 && desc->precision <= PWH_MIXED_FAST,
                   "unknown precision");
     for (int d = 0; d < 3; ++d)
       PWH_CHECK_ARG(desc->fft[d] >= 0, "negative FFT size");
@@ -251,6 +260,7 @@ pwh_status pwh_create_system(const pwh_system_desc* desc, pwh_system** out) {
       build_basis(s, desc->fft);
       upload_basis(s);
       build_fft_plans(s);
+      device_error_word(s);
     } catch (...) {
       delete h;
       throw;
@@ -369,8 +379,22 @@ pwh_status pwh_set_projectors(pwh_system* sys, int32_t nproj, const void* beta,
 pwh_status pwh_set_precision(pwh_system* sys, int32_t precision) {
   return guarded([&] {
     PWH_CHECK_ARG(sys, "null system");
-    PWH_CHECK_ARG(precision == PWH_FP64 || precision == PWH_MIXED, "unknown precision");
+    PWH_CHECK_ARG(precision >= PWH_FP64 && precision <= PWH_MIXED_FAST, "unknown precision");
     sys->s.precision = precision;
+  });
+}
+
+pwh_status pwh_sync(pwh_system* sys) {
+  return guarded([&] {
+    PWH_CHECK_ARG(sys, "null system");
+    System& s = sys->s;
+    PWH_CUDA(cudaStreamSynchronize(s.stream));
+    int e = 0;
+    PWH_CUDA(cudaMemcpy(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+      PWH_CUDA(cudaMemset(s.d_err, 0, sizeof(int)));
+      throw Error{(pwh_status)e, "a bounded device wait gave up (kernel returned early)"};
+    }
   });
 }
 
