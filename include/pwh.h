@@ -129,6 +129,29 @@ pwh_status pwh_apply_h_host(pwh_system* sys, int32_t nb, const void* psi_host,
 pwh_status pwh_apply_h_internal(pwh_system* sys, int32_t nb, const void* psi,
                                 int64_t ld_psi, void* hpsi, int64_t ld_hpsi);
 
+/* Allocation-free variant of the kinetic + local-potential part of H, for
+ * callers that cannot let a library allocate device memory: host codes that
+ * hand all device memory to their own pool at start-up, or that call from a
+ * point where the device-wide synchronisation cudaMalloc/cudaFree may cause is
+ * not acceptable.  The paper has no counterpart; it is an interface addition.
+ *
+ * hpsi = (1/2|k+G|^2 + V_LOC) psi in FP64, bands in the library's internal
+ * plane-wave order (as pwh_apply_h_internal, nonlocal term left out).  psi,
+ * hpsi: device complex128, column-major, ld >= npw, caller-owned.  No cudaMalloc,
+ * cudaFree or other allocating routine is called: the FFT stick buffer is a
+ * fixed 32 MiB device array inside the library, held on every GPU that loads
+ * the library until the process exits.  Bands are processed in batches that
+ * fit it; a system whose single band needs more than 32 MiB (N3 x nsticks x 16
+ * bytes) is rejected with PWH_ERR_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every entry a call reads it first writes, so nothing
+ * needs clearing); calls whose work overlaps on the GPU (different streams or
+ * systems, no ordering between them) race on it.  Asynchronous on the
+ * system's stream; requires pwh_set_potential (PWH_ERR_STATE otherwise). */
+pwh_status pwh_apply_local_noalloc(pwh_system* sys, int32_t nb, const void* psi,
+                                   int64_t ld_psi, void* hpsi, int64_t ld_hpsi);
+
 /* Copy the permutation from internal (stick-major) to public order into host
  * int_to_pub[npw]: internal plane wave i is public plane wave int_to_pub[i]. */
 pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);

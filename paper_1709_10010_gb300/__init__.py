@@ -55,6 +55,7 @@ SIGNATURES = {
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
+    "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_last_error": (ctypes.c_char_p, []),
 }
 
@@ -217,6 +218,14 @@ class System:
         p, ldp = _band_ptr(psi, self.npw)
         h, ldh = _band_ptr(hpsi, self.npw)
         _check(lib().pwh_apply_h_internal(self._h, int(psi.shape[0]), p, ldp, h, ldh))
+        return hpsi
+
+    def apply_local_noalloc(self, psi, hpsi):
+        """(kinetic + local potential) psi in FP64, internal order, into the
+        caller's hpsi; the library allocates nothing during the call."""
+        p, ldp = _band_ptr(psi, self.npw)
+        h, ldh = _band_ptr(hpsi, self.npw)
+        _check(lib().pwh_apply_local_noalloc(self._h, int(psi.shape[0]), p, ldp, h, ldh))
         return hpsi
 
     def apply_h_host(self, psi: np.ndarray, hpsi: np.ndarray | None = None) -> np.ndarray:

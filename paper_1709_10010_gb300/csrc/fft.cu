@@ -26,6 +26,8 @@
 // a separate permutation.  Twiddles e^{2 pi i t/N} come from a host FP64 table.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -411,4 +413,84 @@ template void local_kinetic<double>(System&, int, const double2*, int64_t, doubl
 template void local_kinetic<float>(System&, int, const double2*, int64_t, double2*, int64_t,
                                    cudaStream_t);
 
+// ------------------------------------------- allocation-free entry point ----
+// Scratch for pwh_apply_local_noalloc: the stick buffer of the FFT passes lives
+// in this fixed device array instead of a cudaMalloc'ed workspace.  Every GPU
+// that loads the library holds it until the process exits.
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+static void* noalloc_scratch_address() {
+  static std::mutex mu;
+  static void* addr[128] = {};
+  int dev = -1;
+  PWH_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) throw Error{PWH_ERR_ARG, "device ordinal out of range"};
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    PWH_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = p;
+  }
+  return addr[dev];
+}
+
+static void local_kinetic_noalloc(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
+                                  int64_t ldh) {
+  using T = double;
+  const int64_t wband = (int64_t)s.n3 * s.nsticks;
+  const size_t per = (size_t)wband * sizeof(cx<T>);
+  if (per > kNoallocScratchBytes)
+    throw Error{PWH_ERR_ARG, "pwh_apply_local_noalloc: one band needs a " + std::to_string(per) +
+                                 "-byte stick buffer (N3 x nsticks x 16), above the " +
+                                 std::to_string(kNoallocScratchBytes) + "-byte static scratch"};
+  cx<T>* W = (cx<T>*)noalloc_scratch_address();
+  const int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, kNoallocScratchBytes / per));
+  const cx<T>* tw = s.d_tw64;
+  const int spb = stick_block(s.n3);
+  const size_t zsmem = ((size_t)spb * (s.n3 + 1) + s.n3) * sizeof(cx<T>) + s.n3 * sizeof(int16_t);
+  const size_t budget = 200 * 1024;
+  int rows = s.n2;
+  while (rows > 1 && plane_smem<T>(s, rows) > budget) rows = (rows + 1) / 2;
+  const size_t psmem = plane_smem<T>(s, rows);
+  if (psmem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
+  PWH_CUDA(cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  PWH_CUDA(cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  PWH_CUDA(cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  cudaStream_t st = s.stream;
+  for (int b0 = 0; b0 < nb; b0 += batch) {
+    int bb = std::min(batch, nb - b0);
+    dim3 gz((s.nsticks + spb - 1) / spb, bb);
+    k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
+                                       s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
+    PWH_LAUNCH_CHECK();
+    dim3 gp(s.n3, bb);
+    k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
+                                        s.d_col_x, s.d_v64, s.plan[0], s.plan[1], tw, s.d_perm, rows);
+    PWH_LAUNCH_CHECK();
+    k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
+                                       s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
+                                       hpsi + (size_t)b0 * ldh, ldh, spb);
+    PWH_LAUNCH_CHECK();
+  }
+}
+
 }  // namespace pwh
+
+extern "C" pwh_status pwh_apply_local_noalloc(pwh_system* sys, int32_t nb, const void* psi,
+                                               int64_t ld_psi, void* hpsi, int64_t ld_hpsi) {
+  using namespace pwh;
+  return guarded([&] {
+    PWH_CHECK_ARG(sys, "null system");
+    System& s = sys->s;
+    PWH_CHECK_ARG(nb >= 0, "nb < 0");
+    if (nb == 0) return;
+    PWH_CHECK_ARG(psi && hpsi, "null band pointer");
+    PWH_CHECK_ARG(ld_psi >= s.npw && ld_hpsi >= s.npw, "leading dimension < npw");
+    if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
+    local_kinetic_noalloc(s, nb, (const double2*)psi, ld_psi, (double2*)hpsi, ld_hpsi);
+  });
+}
