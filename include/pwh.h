@@ -156,6 +156,58 @@ pwh_status pwh_apply_local_noalloc(pwh_system* sys, int32_t nb, const void* psi,
  * int_to_pub[npw]: internal plane wave i is public plane wave int_to_pub[i]. */
 pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);
 
+/* ------------------------------------------------------------ eigensolver --
+ * Block Davidson for the lowest nb eigenpairs of H: the iterative
+ * diagonalisation with subspace diagonalisation of O_ij = <psi_i|O|psi_j>
+ * (Sec. "New parallelization levels"), a Davidson-like algorithm [Davidson
+ * 1975] (Sec. "Dynamic perturbations", optical absorption).  Each iteration:
+ * Rayleigh-Ritz on span(V) (FP64 device Jacobi), Ritz vectors X and residuals
+ * R = HX - X diag(theta), convergence when every ||r_n||_2 <= tol, new
+ * directions t_n = K (.) r_n for the unconverged bands (K: Teter-Payne-Allan,
+ * Phys. Rev. B 40, 12255 (1989), with x = (1/2|k+G|^2) / E_ref and
+ * E_ref = <x_n|T|x_n> the kinetic energy of the Ritz vector), projected out of
+ * V twice and orthonormalised by two Cholesky-QR passes (columns whose norm fell below 1e-10 of their norm before
+ * the projection, or whose unit-diagonal Cholesky pivot is below 1e-12, are
+ * dropped), restart to V = X when the subspace would exceed m_max. */
+typedef enum {
+  PWH_PRECOND_TPA = 0,   /* Teter-Payne-Allan diagonal preconditioner */
+  PWH_PRECOND_MLP = 1,   /* TPA times exp(learned correction), see pwh_set_mlp */
+  PWH_PRECOND_NONE = 2   /* t_n = r_n */
+} pwh_precond;
+
+typedef struct {
+  int32_t nb;                /* eigenpairs wanted, 1..1024, <= npw */
+  int32_t max_iter;          /* iteration cap (>= 1) */
+  int32_t max_subspace_mult; /* m_max = max_subspace_mult * nb (>= 2, m_max <= 4096) */
+  int32_t precond;           /* pwh_precond */
+  int32_t mixed;             /* 0: FP64 throughout.  1: first iterate with the
+                                reduced-precision H of the system's precision
+                                (PWH_MIXED if the system is PWH_FP64) until
+                                max ||r|| <= switch_tol, then restart from the
+                                Ritz vectors with the FP64 H */
+  int32_t reserved;
+  double tol;                /* FP64 residual target (Hartree), > 0 */
+  double switch_tol;         /* mixed phase target, >= tol */
+} pwh_davidson_opts;
+
+typedef struct {
+  int32_t iters;             /* Rayleigh-Ritz steps taken */
+  int32_t n_apply;           /* band applications of H (all precisions) */
+  int32_t n_apply_fp64;      /* of which in FP64 */
+  int32_t switch_iter;       /* iteration of the hand-over to FP64, -1 if none */
+  double t_total_s, t_mixed_s, t_fp64_s;  /* wall time, seconds */
+  double max_resid;          /* final max ||r_n||_2 */
+} pwh_davidson_stats;
+
+/* psi_io: DEVICE complex128, nb columns of length npw (ld_psi >= npw, public
+ * order): starting bands in (linearly independent), eigenvectors out.
+ * eig: HOST double[nb], ascending.  stats may be NULL.  Synchronous; runs on
+ * the system's stream.  Returns PWH_ERR_NOT_CONVERGED at max_iter (results
+ * still written), PWH_ERR_NONFINITE if a residual norm is not finite,
+ * PWH_ERR_TIMEOUT if a bounded device wait gave up. */
+pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
+                              int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
+
 /* Synchronize the system's stream and report device-side failures: returns
  * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave
  * up since the last call, so that its results must be discarded. */

@@ -13,7 +13,8 @@ eigenpairs of a Hermitian operator, step by step:
    eigenpairs (theta, c), ascending; X = V c, HX = HV c, R = HX - X diag(theta).
 3. Converged when ||r_n||_2 <= tol for every band n < nb.
 4. For the unconverged bands, t_n = K_n (.) r_n with the Teter-Payne-Allan
-   preconditioner K (Teter, Payne, Allan, Phys. Rev. B 40, 12255 (1989)).
+   preconditioner K (Teter, Payne, Allan, Phys. Rev. B 40, 12255 (1989)),
+   its reference energy the kinetic energy <x_n|T|x_n> of the Ritz vector.
 5. If the subspace would exceed m_max columns, restart with V = X, HV = HX.
 6. Project T against V twice (classical Gram-Schmidt), drop columns whose norm
    fell below 1e-10 of the norm before projection, orthonormalise by Cholesky-QR
@@ -30,12 +31,13 @@ import dataclasses
 import numpy as np
 
 
-def tpa_factor(kinetic: np.ndarray, r: np.ndarray) -> np.ndarray:
-    """Teter-Payne-Allan diagonal K for residual columns r (npw, k).
+def tpa_factor(kinetic: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Teter-Payne-Allan diagonal K for the bands X (npw, k), unit norm.
 
-    x = T_G / E_ref with E_ref = <r|T|r>/<r|r> per column, and
+    x = T_G / E_ref with E_ref = <x_n|T|x_n>/<x_n|x_n> the kinetic energy of the
+    band being corrected (the reference energy of the published method), and
     K(x) = (27 + 18x + 12x^2 + 8x^3) / (27 + 18x + 12x^2 + 8x^3 + 16x^4)."""
-    w = np.abs(r) ** 2
+    w = np.abs(X) ** 2
     eref = (kinetic[:, None] * w).sum(axis=0) / w.sum(axis=0)
     x = kinetic[:, None] / eref[None, :]
     p = 27.0 + 18.0 * x + 12.0 * x ** 2 + 8.0 * x ** 3
@@ -121,7 +123,7 @@ def davidson(apply_h, kinetic, X0, nb, tol=1e-10, max_iter=200, m_max=None,
                                   converged=bool(rn.max() <= tol), history=history)
         U = np.nonzero(rn > tol)[0]
         Ru = R[:, U]
-        T = tpa_factor(kinetic, Ru) * Ru if precond == "tpa" else Ru.copy()
+        T = tpa_factor(kinetic, X[:, U]) * Ru if precond == "tpa" else Ru.copy()
         if V.shape[1] + len(U) > m_max:
             V, HV = X, HX
         t0 = np.linalg.norm(T, axis=0)

@@ -33,6 +33,24 @@ class SystemDesc(ctypes.Structure):
                 ("fft", _c_i32 * 3), ("precision", _c_i32), ("stream", _c_p)]
 
 
+class DavidsonOpts(ctypes.Structure):
+    _fields_ = [("nb", _c_i32), ("max_iter", _c_i32), ("max_subspace_mult", _c_i32),
+                ("precond", _c_i32), ("mixed", _c_i32), ("reserved", _c_i32),
+                ("tol", _c_d), ("switch_tol", _c_d)]
+
+
+class DavidsonStats(ctypes.Structure):
+    _fields_ = [("iters", _c_i32), ("n_apply", _c_i32), ("n_apply_fp64", _c_i32),
+                ("switch_iter", _c_i32), ("t_total_s", _c_d), ("t_mixed_s", _c_d),
+                ("t_fp64_s", _c_d), ("max_resid", _c_d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PRECOND = {"tpa": 0, "mlp": 1, "none": 2}
+
+
 class PwhError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -55,6 +73,8 @@ SIGNATURES = {
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
+    "pwh_davidson_solve": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
+                                    ctypes.POINTER(DavidsonStats)]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_last_error": (ctypes.c_char_p, []),
 }
@@ -237,3 +257,23 @@ class System:
         _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
                                       hpsi.ctypes.data_as(_c_p)))
         return hpsi
+
+    # ---------------------------------------------------------- eigensolver
+    def davidson(self, psi, tol=1e-8, max_iter=200, mult=3, precond="tpa", mixed=False,
+                 switch_tol=1e-5, check=True):
+        """Lowest nb = psi.shape[0] eigenpairs; psi (nb, npw) CUDA complex128
+        holds the starting bands and receives the eigenvectors.  Returns
+        (eigenvalues as numpy, stats dict, status)."""
+        p, ld = _band_ptr(psi, self.npw)
+        nb = int(psi.shape[0])
+        o = DavidsonOpts(nb=nb, max_iter=int(max_iter), max_subspace_mult=int(mult),
+                         precond=PRECOND[precond], mixed=int(bool(mixed)), reserved=0,
+                         tol=float(tol), switch_tol=float(max(switch_tol, tol)))
+        st = DavidsonStats()
+        eig = np.zeros(nb, dtype=np.float64)
+        status = lib().pwh_davidson_solve(self._h, ctypes.byref(o), p, ld,
+                                          eig.ctypes.data_as(_c_p), ctypes.byref(st))
+        if check and status not in (0,):
+            _check(status)
+        return eig, st.as_dict(), status
+

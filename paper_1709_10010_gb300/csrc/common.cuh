@@ -85,6 +85,9 @@ template <typename T> struct DevBuf {
   size_t n = 0;
 };
 
+struct DavWs;
+void free_davidson_ws(DavWs* w);
+
 struct System {
   // description
   double lattice[9];
@@ -138,6 +141,7 @@ struct System {
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
   int* d_err = nullptr;             // device error word (bounded waits that gave up)
+  DavWs* dav = nullptr;             // eigensolver workspace
   int fft_batch = 32;               // bands per FFT batch (bounded by workspace)
 
   ~System();

@@ -1,0 +1,386 @@
+// Block Davidson eigensolver for the lowest nb eigenpairs of H (the iterative
+// diagonalisation with subspace diagonalisation of Sec. "New parallelization
+// levels"; "Davidson-like algorithm [Davidson 1975]", Sec. "Dynamic
+// perturbations", optical absorption).  All vectors stay on the device in the
+// library's internal plane-wave order; the host only reads the nb residual
+// norms and the number of accepted new directions once per iteration.
+//
+// Iteration (V orthonormal, HV = H V, m columns):
+//   Hs = V^H HV (new columns only, then Hermitised)          GEMM + hermitize
+//   (theta, c) = lowest nb eigenpairs of Hs                   device Jacobi (FP64)
+//   X = V c, HX = HV c, R = HX - X theta, ||r_n||             GEMM + k_residual
+//   stop when max_n ||r_n|| <= tol
+//   t_n = K_n (.) r_n for unconverged n (Teter-Payne-Allan K,   k_precond
+//         reference energy <x_n|T|x_n>)
+//   restart V = X, HV = HX when m would exceed m_max
+//   T -= V (V^H T) twice; Cholesky-QR twice with drops       GEMM + k_cholqr
+//   V <- [V T], HV <- [HV, H T]                              H|psi>
+// Mixed mode runs the same loop with the reduced-precision H until
+// max ||r|| <= switch_tol, then restarts from the Ritz vectors with the FP64 H
+// (the FP64 phase recomputes every residual in FP64).
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "davidson.cuh"
+#include "dense.cuh"
+#include "gemm.cuh"
+
+namespace pwh {
+
+struct DavWs {
+  DevBuf<char> vec;    // V, HV (npw x mmax each), X, HX, R, Tw (npw x nb each)
+  DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
+  DenseWs dense;
+  double* h_rn = nullptr;  // pinned host mirrors
+  int* h_idx = nullptr;
+  ~DavWs() {
+    if (vec.p) cudaFree(vec.p);
+    if (small.p) cudaFree(small.p);
+    if (h_rn) cudaFreeHost(h_rn);
+    if (h_idx) cudaFreeHost(h_idx);
+  }
+};
+
+void free_davidson_ws(DavWs* w) { delete w; }
+
+// ----------------------------------------------------------------- kernels --
+// R = HX - X theta per band; rn[b] = ||r_b||, eref[b] = <x|T|x>/<x|x> (the
+// band's kinetic energy, the reference energy of the TPA preconditioner).
+__global__ void k_residual(const double2* __restrict__ X, const double2* __restrict__ HX,
+                           int64_t ld, int64_t npw, const double* __restrict__ theta,
+                           const double* __restrict__ kin, double2* __restrict__ R,
+                           double* __restrict__ rn, double* __restrict__ eref) {
+  const int b = blockIdx.x;
+  const double th = theta[b];
+  const double2* x = X + (size_t)b * ld;
+  const double2* hx = HX + (size_t)b * ld;
+  double2* r = R + (size_t)b * ld;
+  double s2 = 0.0, xt = 0.0, x2 = 0.0;
+  for (int64_t i = threadIdx.x; i < npw; i += blockDim.x) {
+    const double2 xi = x[i];
+    double2 v = make_double2(hx[i].x - th * xi.x, hx[i].y - th * xi.y);
+    r[i] = v;
+    s2 += v.x * v.x + v.y * v.y;
+    const double a = xi.x * xi.x + xi.y * xi.y;
+    x2 += a;
+    xt += kin[i] * a;
+  }
+  __shared__ double red[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    xt += __shfl_xor_sync(0xffffffffu, xt, o);
+    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = s2;
+    red[1][threadIdx.x >> 5] = xt;
+    red[2][threadIdx.x >> 5] = x2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0, d = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      c += red[1][w];
+      d += red[2][w];
+    }
+    rn[b] = sqrt(a);
+    eref[b] = (d > 0 && c > 0) ? c / d : 1.0;
+  }
+}
+
+// T[:, j] = K(T_G / eref) (.) R[:, idx[j]] (K = 1 when tpa == 0); t0[j] = ||t_j||.
+__global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw,
+                          const int* __restrict__ idx, const double* __restrict__ eref,
+                          const double* __restrict__ kin, int tpa, double2* __restrict__ T,
+                          int64_t ldt, double* __restrict__ t0) {
+  const int j = blockIdx.x;
+  const int src = idx[j];
+  const double2* r = R + (size_t)src * ld;
+  double2* t = T + (size_t)j * ldt;
+  const double e = eref[src];
+  double s2 = 0.0;
+  for (int64_t i = threadIdx.x; i < npw; i += blockDim.x) {
+    double k = 1.0;
+    if (tpa) {
+      double x = kin[i] / e;
+      double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+      k = p / (p + 16.0 * x * x * x * x);
+    }
+    double2 v = make_double2(k * r[i].x, k * r[i].y);
+    t[i] = v;
+    s2 += v.x * v.x + v.y * v.y;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+    t0[j] = sqrt(a);
+  }
+}
+
+__global__ void k_copy_cols(const double2* __restrict__ src, int64_t lds, double2* __restrict__ dst,
+                            int64_t ldd, int64_t npw, int k) {
+  int64_t tot = npw * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t % npw, j = t / npw;
+    dst[j * ldd + i] = src[j * lds + i];
+  }
+}
+
+__global__ void k_perm_in(const double2* __restrict__ src, int64_t lds, int64_t npw, int nb,
+                          const int32_t* __restrict__ i2p, double2* __restrict__ dst, int64_t ldd) {
+  int64_t tot = npw * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t % npw, b = t / npw;
+    dst[b * ldd + i] = src[b * lds + i2p[i]];
+  }
+}
+
+__global__ void k_perm_out(const double2* __restrict__ src, int64_t lds, int64_t npw, int nb,
+                           const int32_t* __restrict__ i2p, double2* __restrict__ dst, int64_t ldd) {
+  int64_t tot = npw * nb;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = t % npw, b = t / npw;
+    dst[b * ldd + i2p[i]] = src[b * lds + i];
+  }
+}
+
+static int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (n + 255) / 256)); }
+
+// ------------------------------------------------------------------ solver --
+struct Layout {
+  double2 *V, *HV, *X, *HX, *R, *Tw;
+  double2 *Hs, *C, *Wc, *S, *Tr;
+  double *theta, *rn, *eref, *t0;
+  int *idx, *kk;
+};
+
+static Layout carve(System& s, DavWs& w, int nb, int mmax) {
+  const int64_t npw = s.npw;
+  const size_t nvec = (size_t)npw * (2 * (size_t)mmax + 4 * (size_t)nb);
+  ensure(w.vec, nvec * sizeof(double2));
+  const size_t nc = (size_t)mmax * mmax + (size_t)mmax * nb + (size_t)mmax * nb + 2 * (size_t)nb * nb;
+  const size_t nd = 4 * (size_t)nb;
+  ensure(w.small, nc * sizeof(double2) + nd * sizeof(double) + (2 * (size_t)nb + 8) * sizeof(int) + 256);
+  Layout L;
+  double2* p = (double2*)w.vec.p;
+  L.V = p; p += (size_t)npw * mmax;
+  L.HV = p; p += (size_t)npw * mmax;
+  L.X = p; p += (size_t)npw * nb;
+  L.HX = p; p += (size_t)npw * nb;
+  L.R = p; p += (size_t)npw * nb;
+  L.Tw = p;
+  double2* q = (double2*)w.small.p;
+  L.Hs = q; q += (size_t)mmax * mmax;
+  L.C = q; q += (size_t)mmax * nb;
+  L.Wc = q; q += (size_t)mmax * nb;
+  L.S = q; q += (size_t)nb * nb;
+  L.Tr = q; q += (size_t)nb * nb;
+  double* d = (double*)q;
+  L.theta = d; L.rn = d + nb; L.eref = d + 2 * nb; L.t0 = d + 3 * nb;
+  L.idx = (int*)(d + 4 * nb);
+  L.kk = L.idx + nb;
+  if (!w.h_rn) {
+    PWH_CUDA(cudaMallocHost((void**)&w.h_rn, 8192 * sizeof(double)));
+    PWH_CUDA(cudaMallocHost((void**)&w.h_idx, 8192 * sizeof(int)));
+  }
+  return L;
+}
+
+// Orthonormalise T (npw x k, ld npw, in place) by two Cholesky-QR passes; the
+// first also drops columns whose norm fell below drop_rel * t0.  Returns the
+// number of surviving columns (now the first ones of T).
+static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const double* t0,
+                   double drop_rel, cudaStream_t st) {
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  const int64_t npw = s.npw;
+  cgemm<double>(s, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
+  cholqr_factor(w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
+  cgemm<double>(s, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
+  cgemm<double>(s, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
+  cholqr_factor(w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
+  cgemm<double>(s, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
+  PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4096, L.kk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PWH_CUDA(cudaStreamSynchronize(st));
+  return w.h_idx[4096];
+}
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void check_err(System& s) {
+  int e = 0;
+  PWH_CUDA(cudaMemcpy(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    PWH_CUDA(cudaMemset(s.d_err, 0, sizeof(int)));
+    throw Error{(pwh_status)e, "a bounded device wait gave up inside the eigensolver"};
+  }
+}
+
+pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, int64_t ldpsi,
+                          double* eig, pwh_davidson_stats* stats) {
+  const int nb = o.nb;
+  const int mmax = o.max_subspace_mult * nb;
+  const int64_t npw = s.npw;
+  if (!s.dav) s.dav = new DavWs();
+  DavWs& w = *s.dav;
+  Layout L = carve(s, w, nb, mmax);
+  cudaStream_t st = s.stream;
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+  const int tpa = o.precond == PWH_PRECOND_TPA ? 1 : 0;
+  pwh_davidson_stats S{};
+  S.switch_iter = -1;
+  const double t_start = now_s();
+  double t_phase = t_start;
+  int phase_prec = o.mixed ? (s.precision == PWH_FP64 ? PWH_MIXED : s.precision) : PWH_FP64;
+
+  auto applyH = [&](const double2* in, double2* out, int k) {
+    apply_internal(s, k, in, npw, out, npw, phase_prec);
+    S.n_apply += k;
+    if (phase_prec == PWH_FP64) S.n_apply_fp64 += k;
+  };
+
+  // starting block: public -> internal order, orthonormalise, apply H
+  k_perm_in<<<grid1d(npw * nb), 256, 0, st>>>(psi, ldpsi, npw, nb, s.d_int_to_pub, L.V, npw);
+  PWH_LAUNCH_CHECK();
+  int k0 = cholqr2(s, w, L, L.V, nb, nullptr, 0.0, st);
+  if (k0 < nb) throw Error{PWH_ERR_ARG, "starting bands are linearly dependent"};
+  applyH(L.V, L.HV, nb);
+  int m = nb;
+  int hs_valid = 0;  // leading columns of Hs that match the current V, HV
+  pwh_status result = PWH_ERR_NOT_CONVERGED;
+  double maxr = 0.0;
+  auto restart_from_ritz = [&](bool recompute_hx) {
+    k_copy_cols<<<grid1d(npw * nb), 256, 0, st>>>(L.X, npw, L.V, npw, npw, nb);
+    PWH_LAUNCH_CHECK();
+    if (recompute_hx) {
+      applyH(L.V, L.HV, nb);
+    } else {
+      k_copy_cols<<<grid1d(npw * nb), 256, 0, st>>>(L.HX, npw, L.HV, npw, npw, nb);
+      PWH_LAUNCH_CHECK();
+    }
+    m = nb;
+    hs_valid = 0;
+  };
+  for (int it = 1;; ++it) {
+    // Rayleigh-Ritz on span(V): new columns of Hs, then its lowest nb eigenpairs
+    cgemm<double>(s, true, m, m - hs_valid, (int)npw, one, L.V, npw, L.HV + (size_t)hs_valid * npw,
+                  npw, zero, L.Hs + (size_t)hs_valid * mmax, mmax, st);
+    hermitize(L.Hs, mmax, hs_valid, m, st);
+    hs_valid = m;
+    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st);
+    cgemm<double>(s, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
+    cgemm<double>(s, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
+    k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
+    PWH_LAUNCH_CHECK();
+    PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PWH_CUDA(cudaStreamSynchronize(st));
+    check_err(s);
+    S.iters = it;
+    maxr = 0.0;
+    bool finite = true;
+    for (int b = 0; b < nb; ++b) {
+      if (!std::isfinite(w.h_rn[b])) finite = false;
+      maxr = std::max(maxr, w.h_rn[b]);
+    }
+    if (!finite) {
+      result = PWH_ERR_NONFINITE;
+      break;
+    }
+    if (phase_prec != PWH_FP64 && maxr <= o.switch_tol) {
+      // hand over to FP64: restart from the Ritz vectors with the FP64 operator
+      const double t = now_s();
+      S.t_mixed_s = t - t_phase;
+      t_phase = t;
+      S.switch_iter = it;
+      phase_prec = PWH_FP64;
+      restart_from_ritz(true);
+      continue;
+    }
+    if (phase_prec == PWH_FP64 && maxr <= o.tol) {
+      result = PWH_OK;
+      break;
+    }
+    if (it >= o.max_iter) break;
+    // bands still above this phase's target get a new direction
+    const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
+    int k = 0;
+    for (int b = 0; b < nb; ++b)
+      if (w.h_rn[b] > thr) w.h_idx[k++] = b;
+    PWH_CUDA(cudaMemcpyAsync(L.idx, w.h_idx, k * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (m + k > mmax) restart_from_ritz(false);
+    double2* T = L.V + (size_t)m * npw;
+    k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa, T, npw, L.t0);
+    PWH_LAUNCH_CHECK();
+    for (int pass = 0; pass < 2; ++pass) {
+      cgemm<double>(s, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
+      cgemm<double>(s, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
+    }
+    const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st);
+    if (kn == 0) {
+      restart_from_ritz(false);
+      continue;
+    }
+    applyH(T, L.HV + (size_t)m * npw, kn);
+    m += kn;
+  }
+  // outputs: eigenvalues (host), eigenvectors (public order, caller's buffer)
+  PWH_CUDA(cudaMemcpyAsync(eig, L.theta, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  k_perm_out<<<grid1d(npw * nb), 256, 0, st>>>(L.X, npw, npw, nb, s.d_int_to_pub, psi, ldpsi);
+  PWH_LAUNCH_CHECK();
+  PWH_CUDA(cudaStreamSynchronize(st));
+  check_err(s);
+  const double t_end = now_s();
+  if (S.switch_iter >= 0)
+    S.t_fp64_s = t_end - t_phase;
+  else if (o.mixed)
+    S.t_mixed_s = t_end - t_phase;
+  else
+    S.t_fp64_s = t_end - t_phase;
+  S.t_total_s = t_end - t_start;
+  S.max_resid = maxr;
+  if (stats) *stats = S;
+  return result;
+}
+
+}  // namespace pwh
+
+using namespace pwh;
+
+extern "C" pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts,
+                                         void* psi_io, int64_t ld_psi, double* eig,
+                                         pwh_davidson_stats* stats) {
+  pwh_status st = PWH_OK;
+  pwh_status g = guarded([&] {
+    PWH_CHECK_ARG(sys && opts && psi_io && eig, "null argument");
+    System& s = sys->s;
+    const pwh_davidson_opts& o = *opts;
+    PWH_CHECK_ARG(o.nb >= 1 && o.nb <= 1024, "nb out of range [1, 1024]");
+    PWH_CHECK_ARG(o.nb <= s.npw, "nb larger than the number of plane waves");
+    PWH_CHECK_ARG(o.max_subspace_mult >= 2 && (int64_t)o.max_subspace_mult * o.nb <= 4096,
+                  "max_subspace_mult must be >= 2 and m_max <= 4096");
+    PWH_CHECK_ARG(o.max_iter >= 1, "max_iter < 1");
+    PWH_CHECK_ARG(std::isfinite(o.tol) && o.tol > 0, "tol must be > 0");
+    PWH_CHECK_ARG(!o.mixed || (std::isfinite(o.switch_tol) && o.switch_tol >= o.tol),
+                  "switch_tol must be >= tol");
+    PWH_CHECK_ARG(o.precond == PWH_PRECOND_TPA || o.precond == PWH_PRECOND_NONE ||
+                      o.precond == PWH_PRECOND_MLP,
+                  "unknown preconditioner");
+    PWH_CHECK_ARG(ld_psi >= s.npw, "ld_psi < npw");
+    if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
+    st = davidson_solve(s, o, (double2*)psi_io, ld_psi, eig, stats);
+    if (st == PWH_ERR_NOT_CONVERGED) set_error("Davidson stopped at max_iter before tol");
+    if (st == PWH_ERR_NONFINITE) set_error("non-finite residual norm");
+  });
+  return g != PWH_OK ? g : st;
+}

@@ -1,0 +1,31 @@
+// Small dense FP64 kernels of the Davidson subspace (dense.cu).
+#pragma once
+#include "common.cuh"
+
+namespace pwh {
+
+struct DenseWs {
+  DevBuf<char> jac, chol;
+  void* ctl = nullptr;  // barrier words and flags of the Jacobi launch
+  ~DenseWs() {
+    if (jac.p) cudaFree(jac.p);
+    if (chol.p) cudaFree(chol.p);
+    if (ctl) cudaFree(ctl);
+  }
+};
+
+// Lowest nk eigenpairs of the n x n Hermitian H (ld = ldh, read only):
+// theta[0..nk) ascending (device), C (n x nk, ld = n, device).
+void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
+                 double* theta, double2* C, cudaStream_t st);
+
+// Complete columns [m0, m) of a Hermitian matrix computed as V^H HV[:, m0:m].
+void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);
+
+// Tr (k x k) such that T Tr has orthonormal first *kk columns (device int),
+// from the Gram matrix S = T^H T; t0 (optional) = column norms before the
+// projection that produced T, for the relative drop test.
+void cholqr_factor(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
+                   double2* Tr, int* kk, cudaStream_t st);
+
+}  // namespace pwh

@@ -23,6 +23,7 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 
 System::~System() {
   if (stream) cudaStreamSynchronize(stream);
+  free_davidson_ws(dav);
   void* ptrs[] = {d_int_to_pub, d_kin, d_stick_off, d_stick_of, d_zpos, d_stick_col,
                   d_stick_y, d_col_x, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,

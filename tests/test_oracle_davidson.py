@@ -70,14 +70,18 @@ def test_residual_bound_holds_midway():
 
 def test_tpa_factor_limits():
     """K(0) = 1, K decreasing, and K(x) ~ 1/(2x) for large x = T_G/E_ref, with
-    E_ref = <r|T|r>/<r|r> (here 0.5)."""
+    E_ref = <x|T|x> the band's kinetic energy (here 0.5)."""
     T = np.array([0.0, 1.0, 1e4, 3.0])
-    r = np.array([[1.0], [1.0], [0.0], [0.0]], dtype=complex)
-    K = od.tpa_factor(T, r)[:, 0]
+    X = np.array([[1.0], [1.0], [0.0], [0.0]], dtype=complex) / np.sqrt(2)
+    K = od.tpa_factor(T, X)[:, 0]
     assert abs(K[0] - 1.0) < 1e-15
     x = T / 0.5
     assert abs(K[2] * 2 * x[2] - 1.0) < 1e-3
     assert K[0] > K[1] > K[3] > K[2]
+    # at x = 1 the published rational function gives 65/81
+    T1 = np.array([0.5, 0.5])
+    X1 = np.array([[1.0], [1.0]], dtype=complex) / np.sqrt(2)
+    assert abs(od.tpa_factor(T1, X1)[0, 0] - 65.0 / 81.0) < 1e-15
 
 
 def test_cholqr_drops_dependent_columns():
