@@ -166,9 +166,9 @@ pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);
  * directions t_n = K (.) r_n for the unconverged bands (K: Teter-Payne-Allan,
  * Phys. Rev. B 40, 12255 (1989), with x = (1/2|k+G|^2) / E_ref and
  * E_ref = <x_n|T|x_n> the kinetic energy of the Ritz vector), projected out of
- * V twice and orthonormalised by two Cholesky-QR passes (columns whose norm fell below 1e-10 of their norm before
- * the projection, or whose unit-diagonal Cholesky pivot is below 1e-12, are
- * dropped), restart to V = X when the subspace would exceed m_max. */
+ * V twice and orthonormalised by two Cholesky-QR passes (columns whose norm
+ * fell below 1e-10 of their norm before the projection, or whose unit-diagonal
+ * Cholesky pivot is below 1e-12, are dropped), restart to V = X when the subspace would exceed m_max. */
 typedef enum {
   PWH_PRECOND_TPA = 0,   /* Teter-Payne-Allan diagonal preconditioner */
   PWH_PRECOND_MLP = 1,   /* TPA times exp(learned correction), see pwh_set_mlp */

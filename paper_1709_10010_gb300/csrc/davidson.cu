@@ -159,7 +159,7 @@ static int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t
 // ------------------------------------------------------------------ solver --
 struct Layout {
   double2 *V, *HV, *X, *HX, *R, *Tw;
-  double2 *Hs, *C, *Wc, *S, *Tr;
+  double2 *Hs, *Qk, *C, *Wc, *S, *Tr;
   double *theta, *rn, *eref, *t0;
   int *idx, *kk;
 };
@@ -168,7 +168,7 @@ static Layout carve(System& s, DavWs& w, int nb, int mmax) {
   const int64_t npw = s.npw;
   const size_t nvec = (size_t)npw * (2 * (size_t)mmax + 4 * (size_t)nb);
   ensure(w.vec, nvec * sizeof(double2));
-  const size_t nc = (size_t)mmax * mmax + (size_t)mmax * nb + (size_t)mmax * nb + 2 * (size_t)nb * nb;
+  const size_t nc = 2 * (size_t)mmax * mmax + (size_t)mmax * nb + (size_t)mmax * nb + 2 * (size_t)nb * nb;
   const size_t nd = 4 * (size_t)nb;
   ensure(w.small, nc * sizeof(double2) + nd * sizeof(double) + (2 * (size_t)nb + 8) * sizeof(int) + 256);
   Layout L;
@@ -181,6 +181,7 @@ static Layout carve(System& s, DavWs& w, int nb, int mmax) {
   L.Tw = p;
   double2* q = (double2*)w.small.p;
   L.Hs = q; q += (size_t)mmax * mmax;
+  L.Qk = q; q += (size_t)mmax * mmax;
   L.C = q; q += (size_t)mmax * nb;
   L.Wc = q; q += (size_t)mmax * nb;
   L.S = q; q += (size_t)nb * nb;
@@ -199,19 +200,34 @@ static Layout carve(System& s, DavWs& w, int nb, int mmax) {
 // Orthonormalise T (npw x k, ld npw, in place) by two Cholesky-QR passes; the
 // first also drops columns whose norm fell below drop_rel * t0.  Returns the
 // number of surviving columns (now the first ones of T).
+static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
+                  const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
+                  double2* C, int64_t ldc, cudaStream_t st);
+
 static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const double* t0,
-                   double drop_rel, cudaStream_t st) {
+                   double drop_rel, cudaStream_t st, int prec = PWH_FP64) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
   const int64_t npw = s.npw;
-  cgemm<double>(s, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
+  sgemm(s, prec, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
   cholqr_factor(w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
-  cgemm<double>(s, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
-  cgemm<double>(s, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
+  sgemm(s, prec, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
+  sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
   cholqr_factor(w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
-  cgemm<double>(s, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
+  sgemm(s, prec, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
   PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4096, L.kk, sizeof(int), cudaMemcpyDeviceToHost, st));
   PWH_CUDA(cudaStreamSynchronize(st));
   return w.h_idx[4096];
+}
+
+// Subspace GEMMs: FP64 in the FP64 phase, FP32 arithmetic on FP64 storage in
+// the reduced-precision phase.
+static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
+                  const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
+                  double2* C, int64_t ldc, cudaStream_t st) {
+  if (prec == PWH_FP64)
+    cgemm<double>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  else
+    cgemm_f32(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 static double now_s() {
@@ -264,6 +280,9 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     k_copy_cols<<<grid1d(npw * nb), 256, 0, st>>>(L.X, npw, L.V, npw, npw, nb);
     PWH_LAUNCH_CHECK();
     if (recompute_hx) {
+      // entering the FP64 phase: make the basis orthonormal to FP64 precision
+      const int kx = cholqr2(s, w, L, L.V, nb, nullptr, 0.0, st, PWH_FP64);
+      if (kx < nb) throw Error{PWH_ERR_NONFINITE, "Ritz vectors lost rank at the FP64 hand-over"};
       applyH(L.V, L.HV, nb);
     } else {
       k_copy_cols<<<grid1d(npw * nb), 256, 0, st>>>(L.HX, npw, L.HV, npw, npw, nb);
@@ -274,13 +293,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   };
   for (int it = 1;; ++it) {
     // Rayleigh-Ritz on span(V): new columns of Hs, then its lowest nb eigenpairs
-    cgemm<double>(s, true, m, m - hs_valid, (int)npw, one, L.V, npw, L.HV + (size_t)hs_valid * npw,
-                  npw, zero, L.Hs + (size_t)hs_valid * mmax, mmax, st);
+    sgemm(s, phase_prec, true, m, m - hs_valid, (int)npw, one, L.V, npw,
+          L.HV + (size_t)hs_valid * npw, npw, zero, L.Hs + (size_t)hs_valid * mmax, mmax, st);
     hermitize(L.Hs, mmax, hs_valid, m, st);
+    // the leading hs_valid x hs_valid block was diagonalised last time: start there
+    const int warm = hs_valid;
     hs_valid = m;
-    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st);
-    cgemm<double>(s, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
-    cgemm<double>(s, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
+    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm);
+    sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
+    sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
     PWH_LAUNCH_CHECK();
     PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -323,10 +344,10 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa, T, npw, L.t0);
     PWH_LAUNCH_CHECK();
     for (int pass = 0; pass < 2; ++pass) {
-      cgemm<double>(s, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
-      cgemm<double>(s, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
+      sgemm(s, phase_prec, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
+      sgemm(s, phase_prec, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
     }
-    const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st);
+    const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st, phase_prec);
     if (kn == 0) {
       restart_from_ritz(false);
       continue;

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "gemm.cuh"
 
 namespace pwh {
 
@@ -81,109 +82,112 @@ __device__ __forceinline__ int rr_player(int j, int r, int n) {
 
 __device__ __forceinline__ double cabs2(double2 z) { return z.x * z.x + z.y * z.y; }
 
-// Jacobi on A (n x n Hermitian, column-major ld = n, destroyed), eigenvectors
-// accumulated in Q (n x n).  Two buffers each (ping-pong): A0/A1, Q0/Q1.  n is
-// padded to even np with a dummy index that never rotates.  Per pair the
-// rotation J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] zeroes A_pq.  Stops when
-// the largest |A_pq| seen in a sweep is <= tol * max|A_ii| or after max_sweeps.
+// Parallel cyclic Jacobi on A (n x n Hermitian, column-major ld = n; ping-pong
+// buffers A[0]/A[1], Q[0]/Q[1]; A[0] and Q[0] hold the start, Q[0] being the
+// basis the start is expressed in).  n is padded to even np with a dummy index
+// that never rotates.  In each round of the round-robin every pair (p, q)
+// gets the rotation J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] that zeroes
+// A_pq; the np/2 rotations are disjoint, so A' = J^H A J and Q' = Q J are
+// formed element-wise in one pass.  Every block recomputes all rotations of
+// the round in shared memory from A's diagonal and upper pairs (cheap), so a
+// round needs a single grid barrier, and every block sees the same largest
+// |A_pq| of the sweep: the sweep loop stops in lockstep once it is
+// <= tol * max|A_ii|.
 struct JacobiArgs {
   double2* A[2];
   double2* Q[2];
-  double2* rot;   // per pair: (c, 0) and (s cos phi, s sin phi) -> 2 entries
-  int* pairs;     // per pair: p, q
-  unsigned long long* offmax;  // per sweep, as ordered bits of a non-negative double
   int n, np, max_sweeps;
   double tol;
-  int* out_buf;   // index (0/1) of the buffers holding the result, sweeps used
+  int* out_buf;   // buffer index (0/1) holding the result, sweeps used
   GridBar gb;
 };
 
 __global__ void k_jacobi(JacobiArgs a) {
+  extern __shared__ __align__(16) unsigned char jsm[];
   const int n = a.n, np = a.np;
+  // 16-byte entries first so that every table is naturally aligned for any np
+  double2* jpart = (double2*)jsm;                    // np: J[partner(x)][x]
+  double* jself = (double*)(jpart + np);             // np: J[x][x]
+  int* partner = (int*)(jself + np);                 // np
+  __shared__ double s_off[32], s_dmax[32];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   int cur = 0;
-  // Q = I
-  for (int t = tid; t < n * n; t += nth) {
-    int i = t % n, j = t / n;
-    a.Q[0][t] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-  }
-  if (tid == 0) *a.offmax = 0ull;
-  if (!grid_sync(a.gb)) return;
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
+    double sweep_off = 0.0, dmax = 0.0;
     for (int r = 0; r < np - 1; ++r) {
       const double2* A = a.A[cur];
-      // phase 1: rotation of every pair
-      for (int i = tid; i < np / 2; i += nth) {
+      double off = 0.0, dm = 0.0;
+      for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
         int p = rr_player(i, r, np), q = rr_player(np - 1 - i, r, np);
         if (p > q) { int t = p; p = q; q = t; }
         double c = 1.0, sr = 0.0, si = 0.0;
         if (q < n) {
-          double2 apq = A[(size_t)q * n + p];
-          double g = sqrt(cabs2(apq));
-          double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
+          const double2 apq = A[(size_t)q * n + p];
+          const double g = sqrt(cabs2(apq));
+          const double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
+          dm = fmax(dm, fmax(fabs(app), fabs(aqq)));
           if (g > 0.0) {
-            // record the largest off-diagonal modulus of this sweep
-            atomicMax(a.offmax, (unsigned long long)__double_as_longlong(g));
-            double zeta = (aqq - app) / (2.0 * g);
-            double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            off = fmax(off, g);
+            const double zeta = (aqq - app) / (2.0 * g);
+            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
             c = 1.0 / sqrt(1.0 + t * t);
-            double s = t * c;
-            sr = s * apq.x / g;
-            si = s * apq.y / g;
+            const double sn = t * c;
+            sr = sn * apq.x / g;
+            si = sn * apq.y / g;
           }
+        } else if (p < n) {
+          dm = fmax(dm, fabs(A[(size_t)p * n + p].x));
         }
-        a.pairs[2 * i] = p;
-        a.pairs[2 * i + 1] = q;
-        a.rot[2 * i] = make_double2(c, 0.0);
-        a.rot[2 * i + 1] = make_double2(sr, si);
+        partner[p] = q;
+        partner[q] = p;
+        jself[p] = c;
+        jself[q] = c;
+        jpart[p] = make_double2(-sr, si);  // J[q][p] = -s e^{-i phi}
+        jpart[q] = make_double2(sr, si);   // J[p][q] =  s e^{+i phi}
       }
-      if (!grid_sync(a.gb)) return;
-      // phase 2: A' = J^H A J, Q' = Q J.  Column j of J has two entries:
-      // J[j][j] and J[pj][j].
+      for (int o = 16; o > 0; o >>= 1) {
+        off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+        dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        s_off[threadIdx.x >> 5] = off;
+        s_dmax[threadIdx.x >> 5] = dm;
+      }
+      __syncthreads();
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sweep_off = fmax(sweep_off, s_off[w]);
+        dm = fmax(dm, s_dmax[w]);
+      }
+      dmax = dm;
       const double2* Qc = a.Q[cur];
       double2* An = a.A[cur ^ 1];
       double2* Qn = a.Q[cur ^ 1];
-      for (int t = tid; t < 2 * n * n; t += nth) {
-        const bool isq = t >= n * n;
-        const int e = isq ? t - n * n : t;
+      const int nn = n * n;
+      for (int t = tid; t < 2 * nn; t += nth) {
+        const bool isq = t >= nn;
+        const int e = isq ? t - nn : t;
         const int i = e % n, j = e / n;
-        // locate pair slots of i and j: position of a player in round r
-        auto slot = [&](int x, int& partner, double2& jxx, double2& jpx) {
-          // find position: players rotate; position j of player x
-          int pos;
-          if (x == 0) pos = 0;
-          else pos = 1 + ((x - 1 - r) % (np - 1) + (np - 1)) % (np - 1);
-          int pi = pos < np / 2 ? pos : np - 1 - pos;
-          int p = a.pairs[2 * pi], q = a.pairs[2 * pi + 1];
-          double c = a.rot[2 * pi].x;
-          double2 s = a.rot[2 * pi + 1];  // s e^{i phi}
-          jxx = make_double2(c, 0.0);
-          if (x == p) {
-            partner = q;
-            jpx = make_double2(-s.x, s.y);  // J[q][p] = -s e^{-i phi}
-          } else {
-            partner = p;
-            jpx = s;                         // J[p][q] = s e^{i phi}
-          }
-        };
-        int pj, pi_;
-        double2 jjj, jpj, jii, jpi;
-        slot(j, pj, jjj, jpj);
+        const int pj = partner[j];
+        const double cj = jself[j];
+        const double2 jpj = jpart[j];
         if (!isq) {
-          slot(i, pi_, jii, jpi);
-          // (A J)[x][j] = A[x][j] J_jj + A[x][pj] J_pj,j   (pj may be the dummy)
-          auto AJ = [&](int x) {
-            double2 v = mul<double>(A[(size_t)j * n + x], jjj);
-            if (pj < n) v = add<double>(v, mul<double>(A[(size_t)pj * n + x], jpj));
-            return v;
-          };
-          double2 v = mul<double>(make_double2(jii.x, -jii.y), AJ(i));
-          if (pi_ < n) v = add<double>(v, mul<double>(make_double2(jpi.x, -jpi.y), AJ(pi_)));
+          const int pi = partner[i];
+          const double ci = jself[i];
+          const double2 jpi = jpart[i];
+          // (A J)[x][j] = A[x][j] J_jj + A[x][pj] J_pj,j ; A' = J^H (A J)
+          double2 aij = scl<double>(A[(size_t)j * n + i], cj);
+          if (pj < n) aij = add<double>(aij, mul<double>(A[(size_t)pj * n + i], jpj));
+          double2 v = scl<double>(aij, ci);
+          if (pi < n) {
+            double2 apj = scl<double>(A[(size_t)j * n + pi], cj);
+            if (pj < n) apj = add<double>(apj, mul<double>(A[(size_t)pj * n + pi], jpj));
+            v = add<double>(v, mul<double>(make_double2(jpi.x, -jpi.y), apj));
+          }
           An[(size_t)j * n + i] = v;
         } else {
-          double2 v = mul<double>(Qc[(size_t)j * n + i], jjj);
+          double2 v = scl<double>(Qc[(size_t)j * n + i], cj);
           if (pj < n) v = add<double>(v, mul<double>(Qc[(size_t)pj * n + i], jpj));
           Qn[(size_t)j * n + i] = v;
         }
@@ -191,14 +195,10 @@ __global__ void k_jacobi(JacobiArgs a) {
       cur ^= 1;
       if (!grid_sync(a.gb)) return;
     }
-    // convergence: largest off-diagonal rotated away during this sweep
-    double off = __longlong_as_double((long long)*(volatile unsigned long long*)a.offmax);
-    double dmax = 0.0;
-    for (int i = 0; i < n; ++i) dmax = fmax(dmax, fabs(a.A[cur][(size_t)i * n + i].x));
-    if (!grid_sync(a.gb)) return;
-    if (tid == 0) *a.offmax = 0ull;
-    if (!grid_sync(a.gb)) return;
-    if (off <= a.tol * fmax(dmax, 1e-300)) { ++sweep; break; }
+    if (sweep_off <= a.tol * fmax(dmax, 1e-300)) {
+      ++sweep;
+      break;
+    }
   }
   if (tid == 0) {
     a.out_buf[0] = cur;
@@ -207,11 +207,13 @@ __global__ void k_jacobi(JacobiArgs a) {
 }
 
 // Sort the diagonal ascending and gather the lowest nk eigenpairs:
-// theta[k], C[:, k] (n x nk, ld = n).  One block.
+// theta[k], C[:, k] (n x nk, ld = n).  Also keeps the full eigenvector matrix
+// in Qkeep (ld = ldk) for a warm start of the next call.  One block.
 __global__ void k_jacobi_select(const double2* __restrict__ A0, const double2* __restrict__ A1,
                                 const double2* __restrict__ Q0, const double2* __restrict__ Q1,
                                 const int* __restrict__ buf, int n, int nk,
-                                double* __restrict__ theta, double2* __restrict__ C) {
+                                double* __restrict__ theta, double2* __restrict__ C,
+                                double2* __restrict__ Qkeep, int64_t ldk) {
   const double2* A = buf[0] ? A1 : A0;
   const double2* Q = buf[0] ? Q1 : Q0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -225,6 +227,22 @@ __global__ void k_jacobi_select(const double2* __restrict__ A0, const double2* _
       theta[rank] = di;
       for (int r = 0; r < n; ++r) C[(size_t)rank * n + r] = Q[(size_t)i * n + r];
     }
+    if (Qkeep)
+      for (int r = 0; r < n; ++r) Qkeep[(size_t)rank * ldk + r] = Q[(size_t)i * n + r];
+  }
+}
+
+// Q0 = blockdiag(Qprev[0:m0, 0:m0], I) (n x n, ld n).
+__global__ void k_warm_basis(const double2* __restrict__ Qprev, int64_t ldp, int m0, int n,
+                             double2* __restrict__ Q0) {
+  int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+    if (i < m0 && j < m0) v = Qprev[(size_t)j * ldp + i];
+    else if (i < m0 || j < m0) v = make_double2(0.0, 0.0);
+    Q0[t] = v;
   }
 }
 
@@ -343,43 +361,55 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
 
 // ---------------------------------------------------------------- host -----
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
-                 double* theta, double2* C, cudaStream_t st) {
+                 double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
+                 int warm_m0) {
+  if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
   const int np = n + (n & 1);
-  // buffers
-  size_t nn = (size_t)n * n;
-  ensure(w.jac, (4 * nn + (size_t)np) * sizeof(double2) + (size_t)np * sizeof(int) + 64);
+  const size_t nn = (size_t)n * n;
+  ensure(w.jac, 4 * nn * sizeof(double2) + 64);
   double2* A0 = (double2*)w.jac.p;
   double2* A1 = A0 + nn;
   double2* Q0 = A1 + nn;
   double2* Q1 = Q0 + nn;
-  double2* rot = Q1 + nn;
-  int* pairs = (int*)(rot + np);
-  if (!w.ctl) {
-    PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
-    PWH_CUDA(cudaMemsetAsync(w.ctl, 0, 64, st));
-  }
+  if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
   unsigned* ctl = (unsigned*)w.ctl;
   PWH_CUDA(cudaMemsetAsync(ctl, 0, 64, st));
-  PWH_CUDA(cudaMemcpy2DAsync(A0, n * sizeof(double2), H, ldh * sizeof(double2),
-                             n * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
+  const int gq = (int)std::min<int64_t>(1024, ((int64_t)nn + 255) / 256);
+  if (warm_m0 > 0 && Qkeep) {
+    // start from the previous eigenbasis: A = Q0^H H Q0, Q = Q0
+    k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q0);
+    PWH_LAUNCH_CHECK();
+    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+    cgemm<double>(s, false, n, n, n, one, H, ldh, Q0, n, zero, A1, n, st);
+    cgemm<double>(s, true, n, n, n, one, Q0, n, A1, n, zero, A0, n, st);
+    hermitize(A0, n, 0, n, st);
+  } else {
+    PWH_CUDA(cudaMemcpy2DAsync(A0, n * sizeof(double2), H, ldh * sizeof(double2),
+                               n * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
+    k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);
+    PWH_LAUNCH_CHECK();
+  }
   JacobiArgs a;
   a.A[0] = A0; a.A[1] = A1; a.Q[0] = Q0; a.Q[1] = Q1;
-  a.rot = rot; a.pairs = pairs;
-  a.offmax = (unsigned long long*)(ctl + 4);
   a.n = n; a.np = np; a.max_sweeps = 40; a.tol = 1e-13;
   a.out_buf = (int*)(ctl + 8);
   a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
-  // one cooperative grid sized to the work, all blocks resident
+  const size_t smem = (size_t)(np + 2) * sizeof(int) + (size_t)np * (sizeof(double) + sizeof(double2)) + 16;
+  static bool attr = false;
+  if (!attr) {
+    PWH_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
   int dev = 0, nsm = 0, per_sm = 0;
   PWH_CUDA(cudaGetDevice(&dev));
   PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, 0));
-  int want = (int)std::max<int64_t>(1, std::min<int64_t>((2 * (int64_t)nn + 255) / 256, nsm));
-  int blocks = std::max(1, std::min(want, nsm * std::max(per_sm, 1)));
+  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem));
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((2 * (int64_t)nn + 1023) / 1024, nsm));
+  const int blocks = std::max(1, std::min(want, nsm * std::max(per_sm, 1)));
   void* args[] = {&a};
-  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, blocks, 256, args, 0, st));
-  k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, a.out_buf, n, nk, theta, C);
+  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, blocks, 256, args, smem, st));
+  k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, a.out_buf, n, nk, theta, C, Qkeep, ldk);
   PWH_LAUNCH_CHECK();
 }
 

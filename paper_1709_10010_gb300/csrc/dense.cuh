@@ -14,10 +14,16 @@ struct DenseWs {
   }
 };
 
+constexpr int kJacobiMaxN = 4096;
+
 // Lowest nk eigenpairs of the n x n Hermitian H (ld = ldh, read only):
-// theta[0..nk) ascending (device), C (n x nk, ld = n, device).
+// theta[0..nk) ascending (device), C (n x nk, ld = n, device).  Qkeep
+// (optional, ld = ldk) receives all n eigenvectors sorted by eigenvalue; with
+// warm_m0 > 0 it must hold the previous call's eigenvectors of the leading
+// warm_m0 x warm_m0 block of H, and the iteration starts in that basis.
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
-                 double* theta, double2* C, cudaStream_t st);
+                 double* theta, double2* C, cudaStream_t st, double2* Qkeep = nullptr,
+                 int64_t ldk = 0, int warm_m0 = 0);
 
 // Complete columns [m0, m) of a Hermitian matrix computed as V^H HV[:, m0:m].
 void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);

@@ -20,12 +20,15 @@ namespace pwh {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-template <typename T, bool CONJ_A>
-__global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<T>* __restrict__ A,
-                                               int64_t lda, const cx<T>* __restrict__ B,
-                                               int64_t ldb, cx<T>* __restrict__ C, int64_t ldc,
-                                               cx<T> alpha, cx<T> beta, int kchunk,
-                                               cx<T>* __restrict__ part) {
+// TS: storage type of A, B, C and the split-K partials; T: compute type
+// (operands are rounded to T when staged in shared memory, products are
+// accumulated in T).
+template <typename TS, typename T, bool CONJ_A>
+__global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<TS>* __restrict__ A,
+                                               int64_t lda, const cx<TS>* __restrict__ B,
+                                               int64_t ldb, cx<TS>* __restrict__ C, int64_t ldc,
+                                               cx<TS> alpha, cx<TS> beta, int kchunk,
+                                               cx<TS>* __restrict__ part) {
   __shared__ cx<T> As[GBK][GBM + 1];
   __shared__ cx<T> Bs[GBK][GBN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -45,14 +48,17 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<T>*
       if (!CONJ_A) {
         int m = t % GBM, k = t / GBM;
         int gm = m0 + m, gk = k0 + k;
-        if (gm < M && gk < ke) v = A[(size_t)gk * lda + gm];
+        if (gm < M && gk < ke) {
+          cx<TS> z = A[(size_t)gk * lda + gm];
+          v = mk<T>((T)z.x, (T)z.y);
+        }
         As[k][m] = v;
       } else {
         int k = t % GBK, m = t / GBK;
         int gm = m0 + m, gk = k0 + k;
         if (gm < M && gk < ke) {
-          v = A[(size_t)gm * lda + gk];
-          v.y = -v.y;
+          cx<TS> z = A[(size_t)gm * lda + gk];
+          v = mk<T>((T)z.x, -(T)z.y);
         }
         As[k][m] = v;
       }
@@ -61,7 +67,10 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<T>*
       int k = t % GBK, n = t / GBK;
       int gn = n0 + n, gk = k0 + k;
       cx<T> v = mk<T>(0, 0);
-      if (gn < N && gk < ke) v = B[(size_t)gn * ldb + gk];
+      if (gn < N && gk < ke) {
+        cx<TS> z = B[(size_t)gn * ldb + gk];
+        v = mk<T>((T)z.x, (T)z.y);
+      }
       Bs[k][n] = v;
     }
     __syncthreads();
@@ -90,11 +99,12 @@ __global__ void __launch_bounds__(256) k_cgemm(int M, int N, int K, const cx<T>*
     for (int j = 0; j < 4; ++j) {
       int gm = m0 + tx + 16 * i, gn = n0 + ty + 16 * j;
       if (gm < M && gn < N) {
+        const cx<TS> a = mk<TS>((TS)acc[i][j].x, (TS)acc[i][j].y);
         if (part) {
-          part[((size_t)blockIdx.z * N + gn) * M + gm] = acc[i][j];
+          part[((size_t)blockIdx.z * N + gn) * M + gm] = a;
         } else {
-          cx<T> r = mul<T>(alpha, acc[i][j]);
-          if (beta.x != (T)0 || beta.y != (T)0) r = add<T>(r, mul<T>(beta, C[(size_t)gn * ldc + gm]));
+          cx<TS> r = mul<TS>(alpha, a);
+          if (beta.x != (TS)0 || beta.y != (TS)0) r = add<TS>(r, mul<TS>(beta, C[(size_t)gn * ldc + gm]));
           C[(size_t)gn * ldc + gm] = r;
         }
       }
@@ -119,10 +129,10 @@ __global__ void k_splitk_reduce(int M, int N, int nsplit, const cx<T>* __restric
   }
 }
 
-template <typename T>
-void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
-           const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
-           const double* rowscale) {
+template <typename TS, typename T>
+static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha, const cx<TS>* A,
+                       int64_t lda, const cx<TS>* B, int64_t ldb, cx<TS> beta, cx<TS>* C,
+                       int64_t ldc, cudaStream_t st, const double* rowscale) {
   if (M <= 0 || N <= 0) return;
   const int gm = (M + GBM - 1) / GBM, gn = (N + GBN - 1) / GBN;
   const int tiles = gm * gn;
@@ -132,7 +142,6 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
     nsplit = std::min((2 * 152 + tiles - 1) / tiles, std::max(1, K / 256));
     nsplit = std::max(1, std::min(nsplit, 64));
   }
-  if (rowscale && nsplit == 1) nsplit = 1;  // the reduce kernel applies the row scale
   int kchunk = (K + nsplit - 1) / nsplit;
   kchunk = ((kchunk + GBK - 1) / GBK) * GBK;
   nsplit = std::max(1, (K + kchunk - 1) / kchunk);
@@ -141,23 +150,38 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
     kchunk = 0;
   }
   const bool use_part = nsplit > 1 || rowscale != nullptr;
-  cx<T>* part = nullptr;
+  cx<TS>* part = nullptr;
   if (use_part) {
-    ensure(s.ws_split, (size_t)nsplit * M * N * sizeof(cx<T>));
-    part = (cx<T>*)s.ws_split.p;
+    ensure(s.ws_split, (size_t)nsplit * M * N * sizeof(cx<TS>));
+    part = (cx<TS>*)s.ws_split.p;
   }
   dim3 grid(gm, gn, nsplit);
   if (conjA)
-    k_cgemm<T, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kchunk, part);
+    k_cgemm<TS, T, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kchunk,
+                                                part);
   else
-    k_cgemm<T, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kchunk, part);
+    k_cgemm<TS, T, false><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta,
+                                                 kchunk, part);
   PWH_LAUNCH_CHECK();
   if (use_part) {
     int64_t tot = (int64_t)M * N;
     int blocks = (int)std::min<int64_t>(4096, (tot + 255) / 256);
-    k_splitk_reduce<T><<<blocks, 256, 0, st>>>(M, N, nsplit, part, C, ldc, alpha, beta, rowscale);
+    k_splitk_reduce<TS><<<blocks, 256, 0, st>>>(M, N, nsplit, part, C, ldc, alpha, beta, rowscale);
     PWH_LAUNCH_CHECK();
   }
+}
+
+template <typename T>
+void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
+           const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
+           const double* rowscale) {
+  cgemm_impl<T, T>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
+}
+
+void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+               int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+               cudaStream_t st) {
+  cgemm_impl<double, float>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, nullptr);
 }
 
 template void cgemm<double>(System&, bool, int, int, int, double2, const double2*, int64_t,

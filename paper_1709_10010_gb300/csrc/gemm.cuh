@@ -12,4 +12,10 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
            const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
            const double* rowscale = nullptr);
 
+// Same with FP64 (complex128) storage and FP32 arithmetic: operands rounded to
+// FP32 in shared memory, FP32 accumulation, result widened to FP64.
+void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+               int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+               cudaStream_t st);
+
 }  // namespace pwh
