@@ -208,6 +208,35 @@ typedef struct {
 pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                               int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
 
+/* -------------------------------------------------------------- measurement --
+ * Per-family kernel timing: with timing on, the library brackets the launches
+ * of each kernel family with CUDA events on the system's stream and
+ * accumulates their durations (adds an event pair per launch).  Turning it on
+ * or off synchronizes the stream and clears the totals. */
+typedef struct {
+  char name[32];     /* family: fft_z_inverse_fp64|fp32, fft_plane_fp64|fp32,
+                        fft_z_forward_fp64|fp32, tc_gemm_becp, tc_gemm_backproj,
+                        cgemm_fp64, cgemm_fp32, jacobi_fp64, cholqr_fp64 */
+  int64_t launches;  /* timed launches (bracketed groups) */
+  double total_ms;   /* summed device time */
+  double flops;      /* algorithmic floating-point operations of those launches
+                        (nominal 5 N log2 N per length-N complex FFT, 8 MNK per
+                        complex GEMM, 2 MNK per real tensor-core GEMM, 40 m^2
+                        per Jacobi round); 0 where not counted (cholqr) */
+  double bytes;      /* algorithmic device-memory bytes of those launches */
+} pwh_kernel_time;
+
+pwh_status pwh_set_kernel_timing(pwh_system* sys, int32_t on);
+
+/* Synchronize and copy up to max_out family totals into out; *count receives
+ * the number of families. */
+pwh_status pwh_get_kernel_times(pwh_system* sys, pwh_kernel_time* out, int32_t max_out,
+                                int32_t* count);
+
+/* Number of kernels this library has launched in the process so far (host
+ * counter, all systems). */
+pwh_status pwh_launch_count(int64_t* count);
+
 /* Synchronize the system's stream and report device-side failures: returns
  * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave
  * up since the last call, so that its results must be discarded. */

@@ -51,6 +51,11 @@ class DavidsonStats(ctypes.Structure):
 PRECOND = {"tpa": 0, "mlp": 1, "none": 2}
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _c_i64), ("total_ms", _c_d),
+                ("flops", _c_d), ("bytes", _c_d)]
+
+
 class PwhError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -73,6 +78,9 @@ SIGNATURES = {
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
+    "pwh_set_kernel_timing": (_c_i32, [_c_p, _c_i32]),
+    "pwh_get_kernel_times": (_c_i32, [_c_p, _c_p, _c_i32, ctypes.POINTER(_c_i32)]),
+    "pwh_launch_count": (_c_i32, [ctypes.POINTER(_c_i64)]),
     "pwh_davidson_solve": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
                                     ctypes.POINTER(DavidsonStats)]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
@@ -100,6 +108,13 @@ def lib():
 def _check(status: int):
     if status != 0:
         raise PwhError(status, lib().pwh_last_error().decode())
+
+
+def launch_count() -> int:
+    """Kernels launched by libpwh in this process so far."""
+    c = _c_i64()
+    _check(lib().pwh_launch_count(ctypes.byref(c)))
+    return int(c.value)
 
 
 def _torch():
@@ -214,6 +229,18 @@ class System:
     def set_precision(self, precision):
         p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         _check(lib().pwh_set_precision(self._h, p))
+
+    def set_kernel_timing(self, on: bool):
+        _check(lib().pwh_set_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_times(self) -> dict:
+        """{family: dict(launches, ms, flops, bytes)} accumulated while timing is on."""
+        arr = (KernelTime * 32)()
+        n = _c_i32()
+        _check(lib().pwh_get_kernel_times(self._h, arr, 32, ctypes.byref(n)))
+        return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
+                                       "flops": float(arr[i].flops), "bytes": float(arr[i].bytes)}
+                for i in range(min(n.value, 32))}
 
     def sync(self):
         """Wait for the stream; raises PwhError(PWH_ERR_TIMEOUT) if a bounded

@@ -34,7 +34,14 @@ struct Error {
     }                                                                                   \
   } while (0)
 
-#define PWH_LAUNCH_CHECK() PWH_CUDA(cudaGetLastError())
+// Every kernel launch site ends with PWH_LAUNCH_CHECK(): it checks the launch
+// and counts it (pwh_launch_count).
+void note_launch();
+#define PWH_LAUNCH_CHECK()          \
+  do {                              \
+    ::pwh::note_launch();           \
+    PWH_CUDA(cudaGetLastError());   \
+  } while (0)
 
 // ------------------------------------------------------------- complex ------
 template <typename T> struct cplx;
@@ -87,6 +94,28 @@ template <typename T> struct DevBuf {
 
 struct DavWs;
 void free_davidson_ws(DavWs* w);
+
+// Optional per-family kernel timing with CUDA events on the system's stream.
+enum KernelFamily {
+  KF_FFT_ZINV64 = 0, KF_FFT_PLANE64, KF_FFT_ZFWD64, KF_FFT_ZINV32, KF_FFT_PLANE32, KF_FFT_ZFWD32,
+  KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_COUNT
+};
+extern const char* const kKernelFamilyName[KF_COUNT];
+
+struct KernelTimer {
+  bool on = false;
+  double ms[KF_COUNT] = {};
+  long long n[KF_COUNT] = {};
+  double flops[KF_COUNT] = {};  // algorithmic work of the timed launches
+  double bytes[KF_COUNT] = {};
+  struct Pending { int fam; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get();
+  void resolve();  // waits for the recorded events, accumulates, recycles
+  void reset();
+  ~KernelTimer();
+};
 
 struct System {
   // description
@@ -142,6 +171,7 @@ struct System {
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
   int* d_err = nullptr;             // device error word (bounded waits that gave up)
   DavWs* dav = nullptr;             // eigensolver workspace
+  KernelTimer timer;
   int fft_batch = 32;               // bands per FFT batch (bounded by workspace)
 
   ~System();
@@ -155,6 +185,30 @@ template <typename T> void ensure(DevBuf<T>& b, size_t n) {
   PWH_CUDA(cudaMalloc((void**)&b.p, n * sizeof(T)));
   b.n = n;
 }
+
+// Brackets the launches of one kernel family with events when timing is on.
+struct TimedScope {
+  System& s;
+  int fam;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  TimedScope(System& s_, int fam_, cudaStream_t st_, double flops = 0, double bytes = 0)
+      : s(s_), fam(fam_), st(st_) {
+    if (s.timer.on) {
+      a = s.timer.get();
+      cudaEventRecord(a, st);
+      s.timer.flops[fam] += flops;
+      s.timer.bytes[fam] += bytes;
+    }
+  }
+  ~TimedScope() {
+    if (a) {
+      cudaEvent_t b = s.timer.get();
+      cudaEventRecord(b, st);
+      s.timer.pending.push_back({fam, a, b});
+    }
+  }
+};
 
 // --------------------------------------------------------- entry helpers ----
 template <typename F> pwh_status guarded(F&& f) {

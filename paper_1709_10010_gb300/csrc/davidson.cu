@@ -209,10 +209,10 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
   const int64_t npw = s.npw;
   sgemm(s, prec, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
-  cholqr_factor(w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
+  cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
   sgemm(s, prec, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
   sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
-  cholqr_factor(w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
+  cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
   sgemm(s, prec, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
   PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4096, L.kk, sizeof(int), cudaMemcpyDeviceToHost, st));
   PWH_CUDA(cudaStreamSynchronize(st));
@@ -305,8 +305,18 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
     PWH_LAUNCH_CHECK();
     PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (s.timer.on)
+      PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4100, jacobi_sweeps_word(w.dense), sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
     PWH_CUDA(cudaStreamSynchronize(st));
     check_err(s);
+    if (s.timer.on) {
+      // Jacobi work: sweeps x (m-1) rounds x m^2 elements x 40 FP64 operations
+      const double sw = w.h_idx[4100];
+      s.timer.flops[KF_JACOBI] += sw * (m - 1) * 40.0 * (double)m * m;
+      s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 4.0 * 16.0 * (double)m * m;
+    }
+    s.timer.resolve();
     S.iters = it;
     maxr = 0.0;
     bool finite = true;

@@ -408,7 +408,12 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   const int want = (int)std::max<int64_t>(1, std::min<int64_t>((2 * (int64_t)nn + 1023) / 1024, nsm));
   const int blocks = std::max(1, std::min(want, nsm * std::max(per_sm, 1)));
   void* args[] = {&a};
-  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, blocks, 256, args, smem, st));
+  {
+    // work recorded after the launch, once the number of sweeps is known
+    TimedScope ts(s, KF_JACOBI, st);
+    PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, blocks, 256, args, smem, st));
+    note_launch();
+  }
   k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, a.out_buf, n, nk, theta, C, Qkeep, ldk);
   PWH_LAUNCH_CHECK();
 }
@@ -421,10 +426,11 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {
   PWH_LAUNCH_CHECK();
 }
 
-void cholqr_factor(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
-                   double2* Tr, int* kk, cudaStream_t st) {
+void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
+                   double drop_rel, double2* Tr, int* kk, cudaStream_t st) {
   if (k > 1024) throw Error{PWH_ERR_ARG, "block of more than 1024 new directions"};
   ensure(w.chol, (size_t)k * k * sizeof(double2));
+  TimedScope ts(s, KF_CHOLQR, st);
   k_cholqr<<<1, 1024, 0, st>>>(S, k, t0, drop_rel, 1e-12, (double2*)w.chol.p, Tr, kk);
   PWH_LAUNCH_CHECK();
 }

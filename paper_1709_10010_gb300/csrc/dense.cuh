@@ -25,13 +25,16 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep = nullptr,
                  int64_t ldk = 0, int warm_m0 = 0);
 
+// Device word holding the number of sweeps of the last jacobi_eigh.
+inline int* jacobi_sweeps_word(DenseWs& w) { return (int*)w.ctl + 9; }
+
 // Complete columns [m0, m) of a Hermitian matrix computed as V^H HV[:, m0:m].
 void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);
 
 // Tr (k x k) such that T Tr has orthonormal first *kk columns (device int),
 // from the Gram matrix S = T^H T; t0 (optional) = column norms before the
 // projection that produced T, for the relative drop test.
-void cholqr_factor(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
-                   double2* Tr, int* kk, cudaStream_t st);
+void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
+                   double drop_rel, double2* Tr, int* kk, cudaStream_t st);
 
 }  // namespace pwh

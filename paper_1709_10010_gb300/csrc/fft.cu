@@ -391,20 +391,39 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
     attr_done[ti] = true;
   }
   const T* V = sizeof(T) == 8 ? (const T*)s.d_v64 : (const T*)s.d_v32;
+  const bool dp = sizeof(T) == 8;
+  // algorithmic work per band (nominal 5 N log2 N flops per complex transform of
+  // length N; bytes each pass must move at minimum)
+  auto l2 = [](int n) { return std::log2((double)n); };
+  const double cz = sizeof(cx<T>), ncol = s.ncols;
+  const double fz = 5.0 * s.n3 * l2(s.n3) * s.nsticks;                      // z pass
+  const double fp = 2.0 * s.n3 * (ncol * 5.0 * s.n2 * l2(s.n2) + s.n2 * 5.0 * s.n1 * l2(s.n1));
+  const double bw = cz * (double)s.nsticks * s.n3;                          // one W slice
+  const double bv = sizeof(T) * (double)s.n1 * s.n2 * s.n3;                 // V, once per launch
   for (int b0 = 0; b0 < nb; b0 += batch) {
     int bb = std::min(batch, nb - b0);
     dim3 gz((s.nsticks + spb - 1) / spb, bb);
-    k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
-                                       s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
-    PWH_LAUNCH_CHECK();
+    {
+      TimedScope ts(s, dp ? KF_FFT_ZINV64 : KF_FFT_ZINV32, st, bb * fz, bb * (16.0 * s.npw + bw));
+      k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
+                                         s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
+      PWH_LAUNCH_CHECK();
+    }
     dim3 gp(s.n3, bb);
-    k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
-                                        s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
-    PWH_LAUNCH_CHECK();
-    k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
-                                       s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
-                                       hpsi + (size_t)b0 * ldh, ldh, spb);
-    PWH_LAUNCH_CHECK();
+    {
+      TimedScope ts(s, dp ? KF_FFT_PLANE64 : KF_FFT_PLANE32, st, bb * fp, bb * 2.0 * bw + bv);
+      k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
+                                          s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
+      PWH_LAUNCH_CHECK();
+    }
+    {
+      TimedScope ts(s, dp ? KF_FFT_ZFWD64 : KF_FFT_ZFWD32, st, bb * fz,
+                    bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw));
+      k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
+                                         s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
+                                         hpsi + (size_t)b0 * ldh, ldh, spb);
+      PWH_LAUNCH_CHECK();
+    }
   }
 }
 

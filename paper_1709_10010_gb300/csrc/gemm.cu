@@ -156,6 +156,8 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
     part = (cx<TS>*)s.ws_split.p;
   }
   dim3 grid(gm, gn, nsplit);
+  TimedScope ts(s, sizeof(T) == 8 ? KF_GEMM_FP64 : KF_GEMM_FP32, st, 8.0 * M * N * (double)K,
+                sizeof(cx<TS>) * ((double)M * K + (double)K * N + 2.0 * M * N));
   if (conjA)
     k_cgemm<TS, T, true><<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, kchunk,
                                                 part);

@@ -456,8 +456,13 @@ void prepare_tc_projectors(System& s) {
   PWH_LAUNCH_CHECK();
 }
 
-static void launch_tc(int mode, const CUtensorMap& ma, const CUtensorMap& mb, TcArgs a, int gm,
-                      int gn, int gz, cudaStream_t st) {
+static void launch_tc(System& s, int mode, const CUtensorMap& ma, const CUtensorMap& mb, TcArgs a,
+                      int gm, int gn, int gz, cudaStream_t st) {
+  // algorithmic work: the real GEMM M x N x (terms x K) the launch performs
+  const double kk = (double)a.terms * a.kb_seg * TC_BK;
+  TimedScope ts(s, mode == 0 ? KF_TC_BECP : KF_TC_BACK, st, 2.0 * a.M * (double)a.N * kk,
+                2.0 * ((double)a.M + a.N) * kk + (mode == 0 ? 4.0 * gz * (double)a.M * a.N
+                                                            : 32.0 * a.M * (a.N / 2)));
   static bool attr = false;
   if (!attr) {
     PWH_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
@@ -514,7 +519,7 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
   TcArgs a1{};
   a1.M = 2 * P; a1.N = 2 * nb; a1.kb_seg = kbs1; a1.terms = terms; a1.kb_per_split = kper;
   a1.part = (float*)s.ws_split.p; a1.err = device_error_word(s);
-  launch_tc(0, ma1, mb1, a1, gm1, gn1, split, st);
+  launch_tc(s, 0, ma1, mb1, a1, gm1, gn1, split, st);
   int rb = (int)std::min<int64_t>(1024, ((int64_t)P * nb + 255) / 256);
   if (s.d_diag) {
     k_becp_reduce<<<rb, 256, 0, st>>>((const float*)s.ws_split.p, split, P, nb, s.d_ddiag, becp);
@@ -539,7 +544,7 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
   a2.M = (int)s.npw; a2.N = 2 * nb; a2.kb_seg = kbs2; a2.terms = terms;
   a2.kb_per_split = terms * kbs2; a2.hpsi = hpsi; a2.ldh = ldh; a2.nb = nb;
   a2.err = device_error_word(s);
-  launch_tc(1, ma2, mb2, a2, gm2, gn2, 1, st);
+  launch_tc(s, 1, ma2, mb2, a2, gm2, gn2, 1, st);
 }
 
 }  // namespace pwh

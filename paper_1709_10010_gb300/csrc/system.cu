@@ -10,6 +10,7 @@
 // Internal order: lexicographic (m1, m2, m3), so that every z-stick (fixed
 // m1, m2) is a contiguous run and sticks sharing m1 form one x-column.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -20,6 +21,56 @@ namespace pwh {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+const char* const kKernelFamilyName[KF_COUNT] = {
+    "fft_z_inverse_fp64", "fft_plane_fp64", "fft_z_forward_fp64", "fft_z_inverse_fp32",
+    "fft_plane_fp32", "fft_z_forward_fp32", "tc_gemm_becp", "tc_gemm_backproj", "cgemm_fp64",
+    "cgemm_fp32", "jacobi_fp64", "cholqr_fp64"};
+
+cudaEvent_t KernelTimer::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void KernelTimer::resolve() {
+  for (auto& p : pending) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+      ms[p.fam] += t;
+      n[p.fam] += 1;
+    }
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+void KernelTimer::reset() {
+  resolve();
+  for (int i = 0; i < KF_COUNT; ++i) {
+    ms[i] = 0;
+    n[i] = 0;
+    flops[i] = 0;
+    bytes[i] = 0;
+  }
+}
+
+KernelTimer::~KernelTimer() {
+  for (auto& p : pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
 
 System::~System() {
   if (stream) cudaStreamSynchronize(stream);
@@ -323,6 +374,7 @@ pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_devi
     }
     k_potential_layout<<<1024, 256, 0, s.stream>>>(src, s.n1, s.n2, s.n3, 1.0 / (double)tot,
                                                   s.d_v64, s.d_v32);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     if (tmp) {
       cudaStreamSynchronize(s.stream);
@@ -360,6 +412,7 @@ pwh_status pwh_set_projectors(pwh_system* sys, int32_t nproj, const void* beta,
     }
     k_beta_gather<<<2048, 256, 0, s.stream>>>(src, s.npw, nproj, s.d_int_to_pub, s.d_beta64,
                                              s.d_beta32);
+    note_launch();
     cudaError_t e = cudaGetLastError();
     s.d_diag = d_is_diag != 0;
     size_t dn = s.d_diag ? (size_t)nproj * sizeof(double) : (size_t)nproj * nproj * sizeof(double2);
@@ -382,6 +435,44 @@ pwh_status pwh_set_precision(pwh_system* sys, int32_t precision) {
     PWH_CHECK_ARG(sys, "null system");
     PWH_CHECK_ARG(precision >= PWH_FP64 && precision <= PWH_MIXED_FAST, "unknown precision");
     sys->s.precision = precision;
+  });
+}
+
+pwh_status pwh_set_kernel_timing(pwh_system* sys, int32_t on) {
+  return guarded([&] {
+    PWH_CHECK_ARG(sys, "null system");
+    PWH_CUDA(cudaStreamSynchronize(sys->s.stream));
+    sys->s.timer.reset();
+    sys->s.timer.on = on != 0;
+  });
+}
+
+pwh_status pwh_get_kernel_times(pwh_system* sys, pwh_kernel_time* out, int32_t max_out,
+                                int32_t* count) {
+  return guarded([&] {
+    PWH_CHECK_ARG(sys && count && (out || max_out == 0), "null argument");
+    PWH_CUDA(cudaStreamSynchronize(sys->s.stream));
+    sys->s.timer.resolve();
+    int c = 0;
+    for (int f = 0; f < KF_COUNT; ++f) {
+      if (c < max_out) {
+        std::memset(out[c].name, 0, sizeof(out[c].name));
+        std::strncpy(out[c].name, kKernelFamilyName[f], sizeof(out[c].name) - 1);
+        out[c].launches = sys->s.timer.n[f];
+        out[c].total_ms = sys->s.timer.ms[f];
+        out[c].flops = sys->s.timer.flops[f];
+        out[c].bytes = sys->s.timer.bytes[f];
+      }
+      ++c;
+    }
+    *count = c;
+  });
+}
+
+pwh_status pwh_launch_count(int64_t* count) {
+  return guarded([&] {
+    PWH_CHECK_ARG(count, "null argument");
+    *count = g_launches.load();
   });
 }
 
