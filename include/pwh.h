@@ -237,6 +237,20 @@ pwh_status pwh_get_kernel_times(pwh_system* sys, pwh_kernel_time* out, int32_t m
  * counter, all systems). */
 pwh_status pwh_launch_count(int64_t* count);
 
+/* Subspace diagonalisation (the dense eigensolve of the O_ij matrices, Sec.
+ * "New parallelization levels"), as used by pwh_davidson_solve: the lowest nk
+ * eigenpairs of the n x n Hermitian H (DEVICE complex128, column-major, ld >=
+ * n, only read).  theta: DEVICE double[nk] ascending; C: DEVICE complex128
+ * n x nk (ld = n), orthonormal eigenvectors.  Q (optional, DEVICE, ld = ldq >= n)
+ * receives all n eigenvectors sorted by eigenvalue; with warm > 0, Q must hold
+ * on entry the eigenvectors of the leading warm x warm block of H (a previous
+ * call's output) and the iteration starts in that basis.  Parallel cyclic
+ * Jacobi: sweeps in FP32 to FP32 convergence, the accumulated basis made
+ * unitary in FP64 (Newton-Schulz), then FP64 sweeps until
+ * max|A_ij| <= 1e-13 max|A_ii|.  Asynchronous on the system's stream; n <= 4096. */
+pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t ldh, int32_t nk,
+                             double* theta, void* C, void* Q, int64_t ldq, int32_t warm);
+
 /* Synchronize the system's stream and report device-side failures: returns
  * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave
  * up since the last call, so that its results must be discarded. */

@@ -78,6 +78,8 @@ SIGNATURES = {
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
+    "pwh_subspace_eigh": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_i32, _c_p, _c_p, _c_p, _c_i64,
+                                   _c_i32]),
     "pwh_set_kernel_timing": (_c_i32, [_c_p, _c_i32]),
     "pwh_get_kernel_times": (_c_i32, [_c_p, _c_p, _c_i32, ctypes.POINTER(_c_i32)]),
     "pwh_launch_count": (_c_i32, [ctypes.POINTER(_c_i64)]),
@@ -241,6 +243,25 @@ class System:
         return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].total_ms),
                                        "flops": float(arr[i].flops), "bytes": float(arr[i].bytes)}
                 for i in range(min(n.value, 32))}
+
+    def subspace_eigh(self, H, nk, Q=None, warm=0):
+        """Lowest nk eigenpairs of a Hermitian matrix given as an (n, n) CUDA
+        complex128 tensor Ht with Ht[j, i] = H[i, j] (column-major H).  Returns
+        (theta, C) CUDA tensors, C of shape (nk, n) holding eigenvectors as
+        rows.  Q: optional (n_max, n_max) tensor (row j = eigenvector j) that
+        receives all n eigenvectors; with warm > 0 it must hold on entry the
+        eigenvectors of the leading warm x warm block."""
+        torch = _torch()
+        n = int(H.shape[0])
+        Hc = H.contiguous()
+        theta = torch.empty(nk, dtype=torch.float64, device=H.device)
+        C = torch.empty((nk, n), dtype=torch.complex128, device=H.device)
+        qp = ctypes.c_void_p(Q.data_ptr()) if Q is not None else None
+        ldq = int(Q.shape[1]) if Q is not None else 0
+        _check(lib().pwh_subspace_eigh(self._h, n, ctypes.c_void_p(Hc.data_ptr()), n, int(nk),
+                                       ctypes.c_void_p(theta.data_ptr()),
+                                       ctypes.c_void_p(C.data_ptr()), qp, ldq, int(warm)))
+        return theta, C
 
     def sync(self):
         """Wait for the stream; raises PwhError(PWH_ERR_TIMEOUT) if a bounded

@@ -104,6 +104,7 @@ extern const char* const kKernelFamilyName[KF_COUNT];
 
 struct KernelTimer {
   bool on = false;
+  int depth = 0;  // nested scopes are attributed to the outermost family
   double ms[KF_COUNT] = {};
   long long n[KF_COUNT] = {};
   double flops[KF_COUNT] = {};  // algorithmic work of the timed launches
@@ -192,16 +193,21 @@ struct TimedScope {
   int fam;
   cudaStream_t st;
   cudaEvent_t a = nullptr;
+  bool counted = false;
   TimedScope(System& s_, int fam_, cudaStream_t st_, double flops = 0, double bytes = 0)
       : s(s_), fam(fam_), st(st_) {
     if (s.timer.on) {
-      a = s.timer.get();
-      cudaEventRecord(a, st);
-      s.timer.flops[fam] += flops;
-      s.timer.bytes[fam] += bytes;
+      counted = true;
+      if (s.timer.depth++ == 0) {
+        a = s.timer.get();
+        cudaEventRecord(a, st);
+        s.timer.flops[fam] += flops;
+        s.timer.bytes[fam] += bytes;
+      }
     }
   }
   ~TimedScope() {
+    if (counted) --s.timer.depth;
     if (a) {
       cudaEvent_t b = s.timer.get();
       cudaEventRecord(b, st);

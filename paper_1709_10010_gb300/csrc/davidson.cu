@@ -311,10 +311,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     PWH_CUDA(cudaStreamSynchronize(st));
     check_err(s);
     if (s.timer.on) {
-      // Jacobi work: sweeps x (m-1) rounds x m^2 elements x 40 FP64 operations
+      // FP64 work of the eigensolve: polish sweeps x (m-1) rounds x 20 m^2
+      // operations, plus the Newton-Schulz step and Q^H H Q (4 complex GEMMs)
       const double sw = w.h_idx[4100];
-      s.timer.flops[KF_JACOBI] += sw * (m - 1) * 40.0 * (double)m * m;
-      s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 4.0 * 16.0 * (double)m * m;
+      s.timer.flops[KF_JACOBI] += sw * (m - 1) * 20.0 * (double)m * m + 32.0 * (double)m * m * m;
+      s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 3.0 * 16.0 * (double)m * m;
     }
     s.timer.resolve();
     S.iters = it;

@@ -83,119 +83,184 @@ __device__ __forceinline__ int rr_player(int j, int r, int n) {
 __device__ __forceinline__ double cabs2(double2 z) { return z.x * z.x + z.y * z.y; }
 
 // Parallel cyclic Jacobi on A (n x n Hermitian, column-major ld = n; ping-pong
-// buffers A[0]/A[1], Q[0]/Q[1]; A[0] and Q[0] hold the start, Q[0] being the
-// basis the start is expressed in).  n is padded to even np with a dummy index
-// that never rotates.  In each round of the round-robin every pair (p, q)
-// gets the rotation J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] that zeroes
-// A_pq; the np/2 rotations are disjoint, so A' = J^H A J and Q' = Q J are
-// formed element-wise in one pass.  Every block recomputes all rotations of
-// the round in shared memory from A's diagonal and upper pairs (cheap), so a
-// round needs a single grid barrier, and every block sees the same largest
-// |A_pq| of the sweep: the sweep loop stops in lockstep once it is
-// <= tol * max|A_ii|.
-struct JacobiArgs {
-  double2* A[2];
-  double2* Q[2];
+// buffers A[0]/A[1], Q[0]/Q[1]; A[0] holds the start and Q[0] the basis it is
+// expressed in).  n is padded to even np with a dummy index that never
+// rotates.  In round r of the round-robin the np/2 disjoint pairs (p, q) each
+// get the rotation J = [[c, s], [-conj(s), c]] (c real, s = |s| e^{i phi})
+// that zeroes A_pq, and A' = J^H A J, Q' = Q J are formed in one pass: a work
+// item is a 2 x 2 block of A (rows of pair k, columns of pair l, k <= l by
+// Hermitian symmetry; the mirror block is written too) or one row of Q
+// against one pair.  Every block recomputes the round's rotations in shared
+// memory, so a round costs one grid barrier.  After each sweep block 0 scans
+// the off-diagonal of the current A; the sweeps stop in lockstep once
+// max|A_ij| <= tol * max|A_ii|.
+template <typename T>
+struct JacobiArgsT {
+  cx<T>* A[2];
+  cx<T>* Q[2];
   int n, np, max_sweeps;
   double tol;
   int* out_buf;   // buffer index (0/1) holding the result, sweeps used
+  int* conv;      // per-sweep convergence flag written by block 0
   GridBar gb;
 };
 
-__global__ void k_jacobi(JacobiArgs a) {
+template <typename T>
+__global__ void k_jacobi(JacobiArgsT<T> a) {
   extern __shared__ __align__(16) unsigned char jsm[];
-  const int n = a.n, np = a.np;
-  // 16-byte entries first so that every table is naturally aligned for any np
-  double2* jpart = (double2*)jsm;                    // np: J[partner(x)][x]
-  double* jself = (double*)(jpart + np);             // np: J[x][x]
-  int* partner = (int*)(jself + np);                 // np
-  __shared__ double s_off[32], s_dmax[32];
+  const int n = a.n, np = a.np, P = np / 2;
+  cx<T>* srot = (cx<T>*)jsm;          // P: s of pair k
+  T* crot = (T*)(srot + P);           // P: c of pair k
+  int* pp = (int*)(crot + P);         // P: p of pair k
+  int* pq = pp + P;                   // P: q of pair k
+  __shared__ double s_red[2][32];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
-  int cur = 0;
-  int sweep = 0;
+  int cur = 0, sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
-    double sweep_off = 0.0, dmax = 0.0;
     for (int r = 0; r < np - 1; ++r) {
-      const double2* A = a.A[cur];
-      double off = 0.0, dm = 0.0;
-      for (int i = threadIdx.x; i < np / 2; i += blockDim.x) {
-        int p = rr_player(i, r, np), q = rr_player(np - 1 - i, r, np);
+      const cx<T>* A = a.A[cur];
+      for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        int p = rr_player(k, r, np), q = rr_player(np - 1 - k, r, np);
         if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, sr = 0.0, si = 0.0;
+        T c = 1, sr = 0, si = 0;
         if (q < n) {
-          const double2 apq = A[(size_t)q * n + p];
-          const double g = sqrt(cabs2(apq));
-          const double app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
-          dm = fmax(dm, fmax(fabs(app), fabs(aqq)));
-          if (g > 0.0) {
-            off = fmax(off, g);
-            const double zeta = (aqq - app) / (2.0 * g);
-            const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            c = 1.0 / sqrt(1.0 + t * t);
-            const double sn = t * c;
+          const cx<T> apq = A[(size_t)q * n + p];
+          // |A_pq| scaled against underflow: an inaccurate modulus would make
+          // the rotation non-unitary when zeta is O(1) (degenerate diagonal)
+          const T mx = fmax(fabs(apq.x), fabs(apq.y));
+          T g = 0;
+          if (mx > (T)0) {
+            const T ux = apq.x / mx, uy = apq.y / mx;
+            g = mx * sqrt(ux * ux + uy * uy);
+          }
+          const T app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
+          // an A_pq too small to change either diagonal entry is dropped
+          // without rotating (the 2 x 2 update below writes it as zero)
+          const bool negligible = (fabs(app) + (T)100 * g == fabs(app)) &&
+                                  (fabs(aqq) + (T)100 * g == fabs(aqq));
+          if (g > (T)0 && !negligible) {
+            const T zeta = (aqq - app) / (2 * g);
+            // tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
+            // (1/(2 zeta) once zeta^2 would overflow)
+            const T t = fabs(zeta) > (T)1e9 ? (T)0.5 / zeta
+                                            : (zeta >= 0 ? (T)1 : (T)-1) /
+                                                  (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+            c = (T)1 / sqrt((T)1 + t * t);
+            const T sn = t * c;
             sr = sn * apq.x / g;
             si = sn * apq.y / g;
           }
-        } else if (p < n) {
-          dm = fmax(dm, fabs(A[(size_t)p * n + p].x));
         }
-        partner[p] = q;
-        partner[q] = p;
-        jself[p] = c;
-        jself[q] = c;
-        jpart[p] = make_double2(-sr, si);  // J[q][p] = -s e^{-i phi}
-        jpart[q] = make_double2(sr, si);   // J[p][q] =  s e^{+i phi}
+        pp[k] = p;
+        pq[k] = q;
+        crot[k] = c;
+        srot[k] = mk<T>(sr, si);
+      }
+      __syncthreads();
+      const cx<T>* Qc = a.Q[cur];
+      cx<T>* An = a.A[cur ^ 1];
+      cx<T>* Qn = a.Q[cur ^ 1];
+      const int nA = P * P, nQ = n * P;
+      for (int t = tid; t < nA + nQ; t += nth) {
+        if (t < nA) {
+          const int k = t % P, l = t / P;
+          if (k > l) continue;
+          const int pk = pp[k], qk = pq[k], pl = pp[l], ql = pq[l];
+          const bool vk = qk < n, vl = ql < n;  // pair carries a real second index
+          if (pk >= n || pl >= n) continue;     // (p is never the dummy: p < q)
+          const T ck = crot[k], cl = crot[l];
+          const cx<T> sk = srot[k], sl = srot[l];
+          const cx<T> z = mk<T>(0, 0);
+          const cx<T> a00 = A[(size_t)pl * n + pk];
+          const cx<T> a01 = vl ? A[(size_t)ql * n + pk] : z;
+          const cx<T> a10 = vk ? A[(size_t)pl * n + qk] : z;
+          const cx<T> a11 = (vk && vl) ? A[(size_t)ql * n + qk] : z;
+          const cx<T> msl = mk<T>(-sl.x, sl.y);  // -conj(s_l) = J[q][p]
+          // (A J) on the block: columns (pl, ql)
+          const cx<T> x00 = add<T>(scl<T>(a00, cl), mul<T>(a01, msl));
+          const cx<T> x01 = add<T>(mul<T>(a00, sl), scl<T>(a01, cl));
+          const cx<T> x10 = add<T>(scl<T>(a10, cl), mul<T>(a11, msl));
+          const cx<T> x11 = add<T>(mul<T>(a10, sl), scl<T>(a11, cl));
+          // J^H (A J): row pk = c_k x0 - s_k x1, row qk = conj(s_k) x0 + c_k x1
+          const cx<T> csk = mk<T>(sk.x, -sk.y);
+          cx<T> y00 = sub<T>(scl<T>(x00, ck), mul<T>(sk, x10));
+          cx<T> y01 = sub<T>(scl<T>(x01, ck), mul<T>(sk, x11));
+          cx<T> y10 = add<T>(mul<T>(csk, x00), scl<T>(x10, ck));
+          cx<T> y11 = add<T>(mul<T>(csk, x01), scl<T>(x11, ck));
+          if (k == l) {
+            // rotated 2 x 2 diagonal block: real diagonal, zeroed pair element
+            An[(size_t)pk * n + pk] = mk<T>(y00.x, 0);
+            if (vk) {
+              An[(size_t)qk * n + qk] = mk<T>(y11.x, 0);
+              An[(size_t)qk * n + pk] = mk<T>(0, 0);
+              An[(size_t)pk * n + qk] = mk<T>(0, 0);
+            }
+          } else {
+            An[(size_t)pl * n + pk] = y00;
+            An[(size_t)pk * n + pl] = mk<T>(y00.x, -y00.y);
+            if (vl) {
+              An[(size_t)ql * n + pk] = y01;
+              An[(size_t)pk * n + ql] = mk<T>(y01.x, -y01.y);
+            }
+            if (vk) {
+              An[(size_t)pl * n + qk] = y10;
+              An[(size_t)qk * n + pl] = mk<T>(y10.x, -y10.y);
+            }
+            if (vk && vl) {
+              An[(size_t)ql * n + qk] = y11;
+              An[(size_t)qk * n + ql] = mk<T>(y11.x, -y11.y);
+            }
+          }
+        } else {
+          const int e = t - nA;
+          const int i = e % n, l = e / n;
+          const int pl = pp[l], ql = pq[l];
+          if (pl >= n) continue;
+          const T cl = crot[l];
+          const cx<T> sl = srot[l];
+          const cx<T> q0 = Qc[(size_t)pl * n + i];
+          if (ql < n) {
+            const cx<T> q1 = Qc[(size_t)ql * n + i];
+            Qn[(size_t)pl * n + i] = add<T>(scl<T>(q0, cl), mul<T>(q1, mk<T>(-sl.x, sl.y)));
+            Qn[(size_t)ql * n + i] = add<T>(mul<T>(q0, sl), scl<T>(q1, cl));
+          } else {
+            Qn[(size_t)pl * n + i] = q0;
+          }
+        }
+      }
+      cur ^= 1;
+      if (!grid_sync(a.gb)) return;
+    }
+    // convergence of the current matrix, decided by block 0 for everyone
+    if (blockIdx.x == 0) {
+      const cx<T>* A = a.A[cur];
+      double off = 0.0, dm = 0.0;
+      for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int i = t % n, j = t / n;
+        const cx<T> v = A[t];
+        if (i == j) dm = fmax(dm, fabs((double)v.x));
+        else if (i < j) off = fmax(off, sqrt((double)v.x * v.x + (double)v.y * v.y));
       }
       for (int o = 16; o > 0; o >>= 1) {
         off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
         dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
       }
       if ((threadIdx.x & 31) == 0) {
-        s_off[threadIdx.x >> 5] = off;
-        s_dmax[threadIdx.x >> 5] = dm;
+        s_red[0][threadIdx.x >> 5] = off;
+        s_red[1][threadIdx.x >> 5] = dm;
       }
       __syncthreads();
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        sweep_off = fmax(sweep_off, s_off[w]);
-        dm = fmax(dm, s_dmax[w]);
-      }
-      dmax = dm;
-      const double2* Qc = a.Q[cur];
-      double2* An = a.A[cur ^ 1];
-      double2* Qn = a.Q[cur ^ 1];
-      const int nn = n * n;
-      for (int t = tid; t < 2 * nn; t += nth) {
-        const bool isq = t >= nn;
-        const int e = isq ? t - nn : t;
-        const int i = e % n, j = e / n;
-        const int pj = partner[j];
-        const double cj = jself[j];
-        const double2 jpj = jpart[j];
-        if (!isq) {
-          const int pi = partner[i];
-          const double ci = jself[i];
-          const double2 jpi = jpart[i];
-          // (A J)[x][j] = A[x][j] J_jj + A[x][pj] J_pj,j ; A' = J^H (A J)
-          double2 aij = scl<double>(A[(size_t)j * n + i], cj);
-          if (pj < n) aij = add<double>(aij, mul<double>(A[(size_t)pj * n + i], jpj));
-          double2 v = scl<double>(aij, ci);
-          if (pi < n) {
-            double2 apj = scl<double>(A[(size_t)j * n + pi], cj);
-            if (pj < n) apj = add<double>(apj, mul<double>(A[(size_t)pj * n + pi], jpj));
-            v = add<double>(v, mul<double>(make_double2(jpi.x, -jpi.y), apj));
-          }
-          An[(size_t)j * n + i] = v;
-        } else {
-          double2 v = scl<double>(Qc[(size_t)j * n + i], cj);
-          if (pj < n) v = add<double>(v, mul<double>(Qc[(size_t)pj * n + i], jpj));
-          Qn[(size_t)j * n + i] = v;
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+          s_red[0][0] = fmax(s_red[0][0], s_red[0][w]);
+          s_red[1][0] = fmax(s_red[1][0], s_red[1][w]);
         }
+        *(volatile int*)a.conv = s_red[0][0] <= a.tol * fmax(s_red[1][0], 1e-300) ? 1 : 0;
       }
-      cur ^= 1;
-      if (!grid_sync(a.gb)) return;
     }
-    if (sweep_off <= a.tol * fmax(dmax, 1e-300)) {
+    if (!grid_sync(a.gb)) return;
+    if (*(volatile int*)a.conv) {
       ++sweep;
       break;
     }
@@ -230,6 +295,15 @@ __global__ void k_jacobi_select(const double2* __restrict__ A0, const double2* _
     if (Qkeep)
       for (int r = 0; r < n; ++r) Qkeep[(size_t)rank * ldk + r] = Q[(size_t)i * n + r];
   }
+}
+
+// dst (FP64) = the FP32 buffer (b0 or b1) holding the result.
+__global__ void k_select_buf(const float2* __restrict__ b0, const float2* __restrict__ b1,
+                             const int* __restrict__ buf, int64_t n2, double2* __restrict__ dst) {
+  const float2* b = buf[0] ? b1 : b0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = make_double2((double)b[t].x, (double)b[t].y);
 }
 
 // Q0 = blockdiag(Qprev[0:m0, 0:m0], I) (n x n, ld n).
@@ -360,61 +434,134 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
 }
 
 // ---------------------------------------------------------------- host -----
-void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
-                 double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
-                 int warm_m0) {
-  if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
-  const int np = n + (n & 1);
-  const size_t nn = (size_t)n * n;
-  ensure(w.jac, 4 * nn * sizeof(double2) + 64);
-  double2* A0 = (double2*)w.jac.p;
-  double2* A1 = A0 + nn;
-  double2* Q0 = A1 + nn;
-  double2* Q1 = Q0 + nn;
-  if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
-  unsigned* ctl = (unsigned*)w.ctl;
-  PWH_CUDA(cudaMemsetAsync(ctl, 0, 64, st));
-  const int gq = (int)std::min<int64_t>(1024, ((int64_t)nn + 255) / 256);
-  if (warm_m0 > 0 && Qkeep) {
-    // start from the previous eigenbasis: A = Q0^H H Q0, Q = Q0
-    k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q0);
-    PWH_LAUNCH_CHECK();
-    const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
-    cgemm<double>(s, false, n, n, n, one, H, ldh, Q0, n, zero, A1, n, st);
-    cgemm<double>(s, true, n, n, n, one, Q0, n, A1, n, zero, A0, n, st);
-    hermitize(A0, n, 0, n, st);
-  } else {
-    PWH_CUDA(cudaMemcpy2DAsync(A0, n * sizeof(double2), H, ldh * sizeof(double2),
-                               n * sizeof(double2), n, cudaMemcpyDeviceToDevice, st));
-    k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);
-    PWH_LAUNCH_CHECK();
+// FP32 <-> FP64 copies and the Newton-Schulz step of the host routine.
+__global__ void k_c64_to_c32(const double2* __restrict__ a, int64_t lda, int n, float2* __restrict__ b) {
+  int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    double2 z = a[(size_t)j * lda + i];
+    b[t] = make_float2((float)z.x, (float)z.y);
   }
-  JacobiArgs a;
+}
+__global__ void k_c32_to_c64(const float2* __restrict__ a, int64_t n2, double2* __restrict__ b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2;
+       t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = make_double2((double)a[t].x, (double)a[t].y);
+}
+// B = (3 I - G) / 2
+__global__ void k_ns_rhs(const double2* __restrict__ G, int n, double2* __restrict__ B) {
+  int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(t % n), j = (int)(t / n);
+    double2 g = G[t];
+    B[t] = make_double2((i == j ? 1.5 : 0.0) - 0.5 * g.x, -0.5 * g.y);
+  }
+}
+
+template <typename T>
+static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0, cx<T>* Q1, int n,
+                          double tol, int max_sweeps, int* out_buf, cudaStream_t st) {
+  const int np = n + (n & 1);
+  unsigned* ctl = (unsigned*)w.ctl;
+  PWH_CUDA(cudaMemsetAsync(ctl, 0, 3 * sizeof(unsigned), st));  // barrier words
+  JacobiArgsT<T> a;
   a.A[0] = A0; a.A[1] = A1; a.Q[0] = Q0; a.Q[1] = Q1;
-  a.n = n; a.np = np; a.max_sweeps = 40; a.tol = 1e-13;
-  a.out_buf = (int*)(ctl + 8);
+  a.n = n; a.np = np; a.max_sweeps = max_sweeps; a.tol = tol;
+  a.out_buf = out_buf;
+  a.conv = (int*)(ctl + 12);
   a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
-  const size_t smem = (size_t)(np + 2) * sizeof(int) + (size_t)np * (sizeof(double) + sizeof(double2)) + 16;
-  static bool attr = false;
-  if (!attr) {
-    PWH_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
+  const int P = np / 2;
+  const size_t smem = (size_t)P * (sizeof(cx<T>) + sizeof(T) + 2 * sizeof(int)) + 16;
+  static bool attr[2] = {false, false};
+  const int ti = sizeof(T) == 8 ? 0 : 1;
+  if (!attr[ti]) {
+    PWH_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr[ti] = true;
   }
   int dev = 0, nsm = 0, per_sm = 0;
   PWH_CUDA(cudaGetDevice(&dev));
   PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, smem));
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((2 * (int64_t)nn + 1023) / 1024, nsm));
+  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T>, 256, smem));
+  const int64_t items = (int64_t)P * P + (int64_t)n * P;
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((items + 511) / 512, nsm));
   const int blocks = std::max(1, std::min(want, nsm * std::max(per_sm, 1)));
   void* args[] = {&a};
-  {
-    // work recorded after the launch, once the number of sweeps is known
-    TimedScope ts(s, KF_JACOBI, st);
-    PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi, blocks, 256, args, smem, st));
-    note_launch();
+  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi<T>, blocks, 256, args, smem, st));
+  note_launch();
+}
+
+void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
+                 double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
+                 int warm_m0) {
+  if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
+  const size_t nn = (size_t)n * n;
+  // FP64: A0, A1, Q0, Q1, G;  FP32: a0, a1, q0, q1
+  ensure(w.jac, 5 * nn * sizeof(double2) + 4 * nn * sizeof(float2) + 256);
+  double2* A0 = (double2*)w.jac.p;
+  double2* A1 = A0 + nn;
+  double2* Q0 = A1 + nn;
+  double2* Q1 = Q0 + nn;
+  double2* G = Q1 + nn;
+  float2* a0 = (float2*)(G + nn);
+  float2* a1 = a0 + nn;
+  float2* q0 = a1 + nn;
+  float2* q1 = q0 + nn;
+  if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
+  unsigned* ctl = (unsigned*)w.ctl;
+  PWH_CUDA(cudaMemsetAsync(ctl, 0, 64, st));
+  int* out_buf = (int*)(ctl + 8);  // FP64 stage: result buffer index, sweeps
+  const int gq = (int)std::min<int64_t>(1024, ((int64_t)nn + 255) / 256);
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  TimedScope ts(s, KF_JACOBI, st);
+  // ---- stage 1 (FP32): rotate the start to near-diagonal
+  const bool warm = warm_m0 > 0 && Qkeep;
+  if (warm) {
+    // start in the previous eigenbasis: A = Qw^H H Qw (FP32 arithmetic suffices)
+    k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q1);
+    PWH_LAUNCH_CHECK();
+    cgemm_f32(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
+    cgemm_f32(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
+    k_c64_to_c32<<<gq, 256, 0, st>>>(A1, n, n, a0);
+  } else {
+    k_c64_to_c32<<<gq, 256, 0, st>>>(H, ldh, n, a0);
   }
-  k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, a.out_buf, n, nk, theta, C, Qkeep, ldk);
+  PWH_LAUNCH_CHECK();
+  k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity, reused below
+  PWH_LAUNCH_CHECK();
+  k_c64_to_c32<<<gq, 256, 0, st>>>(Q0, n, n, q0);
+  PWH_LAUNCH_CHECK();
+  int* ob32 = (int*)(ctl + 10);  // FP32 stage: result buffer index, sweeps
+  launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 2e-6, 30, ob32, st);
+  // the FP32 eigenvectors sit in q0 or q1 (ob32[0]): widen them to FP64
+  k_select_buf<<<gq, 256, 0, st>>>(q0, q1, ob32, (int64_t)nn, Q0);
+  PWH_LAUNCH_CHECK();
+  // ---- stage 2 (FP64): exact unitary basis, A = Q^H H Q
+  double2* Q = Q0;
+  if (warm) {
+    cgemm_f32(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
+    Q = A0;
+  }
+  // Newton-Schulz to the nearest unitary: Q <- Q (3I - Q^H Q)/2, once in FP32
+  // arithmetic, once in FP64
+  double2* Qo = (Q == Q0) ? A0 : Q0;
+  cgemm_f32(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
+  k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
+  PWH_LAUNCH_CHECK();
+  cgemm_f32(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
+  cgemm<double>(s, true, n, n, n, one, Qo, n, Qo, n, zero, G, n, st);
+  k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
+  PWH_LAUNCH_CHECK();
+  cgemm<double>(s, false, n, n, n, one, Qo, n, A1, n, zero, Q1, n, st);   // Q1: unitary basis
+  cgemm<double>(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
+  cgemm<double>(s, true, n, n, n, one, Q1, n, G, n, zero, A0, n, st);    // A0 = Q^H H Q
+  hermitize(A0, n, 0, n, st);
+  PWH_CUDA(cudaMemcpyAsync(Q0, Q1, nn * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  // ---- stage 3 (FP64): polish sweeps on the nearly diagonal matrix
+  launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 12, out_buf, st);
+  k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, out_buf, n, nk, theta, C, Qkeep, ldk);
   PWH_LAUNCH_CHECK();
 }
 
@@ -436,3 +583,22 @@ void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double*
 }
 
 }  // namespace pwh
+
+extern "C" pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t ldh,
+                                        int32_t nk, double* theta, void* C, void* Q, int64_t ldq,
+                                        int32_t warm) {
+  using namespace pwh;
+  return guarded([&] {
+    PWH_CHECK_ARG(sys && H && theta && C, "null argument");
+    PWH_CHECK_ARG(n >= 1 && n <= kJacobiMaxN, "n out of range");
+    PWH_CHECK_ARG(nk >= 1 && nk <= n, "nk out of range");
+    PWH_CHECK_ARG(ldh >= n, "ldh < n");
+    PWH_CHECK_ARG(!Q || ldq >= n, "ldq < n");
+    PWH_CHECK_ARG(warm >= 0 && warm <= n && (warm == 0 || Q), "warm needs Q and 0 <= warm <= n");
+    System& s = sys->s;
+    static thread_local DenseWs* ws = nullptr;
+    if (!ws) ws = new DenseWs();
+    jacobi_eigh(s, *ws, (const double2*)H, ldh, n, nk, theta, (double2*)C, s.stream, (double2*)Q,
+                ldq, warm);
+  });
+}
