@@ -185,7 +185,12 @@ typedef struct {
                                 (PWH_MIXED if the system is PWH_FP64) until
                                 max ||r|| <= switch_tol, then restart from the
                                 Ritz vectors with the FP64 H */
-  int32_t reserved;
+  int32_t jd_inner;          /* mixed solves only: >0 turns the FP64 phase into
+                                Jacobi-Davidson steps, each band's correction
+                                equation (I-XX^H)(H-theta)(I-XX^H) t = -r solved
+                                by jd_inner preconditioned CG steps with the
+                                reduced-precision H, then V = [X, T] and an
+                                FP64 Rayleigh-Ritz; 0 = plain Davidson */
   double tol;                /* FP64 residual target (Hartree), > 0 */
   double switch_tol;         /* mixed phase target, >= tol */
 } pwh_davidson_opts;

@@ -35,7 +35,7 @@ class SystemDesc(ctypes.Structure):
 
 class DavidsonOpts(ctypes.Structure):
     _fields_ = [("nb", _c_i32), ("max_iter", _c_i32), ("max_subspace_mult", _c_i32),
-                ("precond", _c_i32), ("mixed", _c_i32), ("reserved", _c_i32),
+                ("precond", _c_i32), ("mixed", _c_i32), ("jd_inner", _c_i32),
                 ("tol", _c_d), ("switch_tol", _c_d)]
 
 
@@ -308,14 +308,14 @@ class System:
 
     # ---------------------------------------------------------- eigensolver
     def davidson(self, psi, tol=1e-8, max_iter=200, mult=3, precond="tpa", mixed=False,
-                 switch_tol=1e-5, check=True):
+                 switch_tol=1e-5, jd_inner=0, check=True):
         """Lowest nb = psi.shape[0] eigenpairs; psi (nb, npw) CUDA complex128
         holds the starting bands and receives the eigenvectors.  Returns
         (eigenvalues as numpy, stats dict, status)."""
         p, ld = _band_ptr(psi, self.npw)
         nb = int(psi.shape[0])
         o = DavidsonOpts(nb=nb, max_iter=int(max_iter), max_subspace_mult=int(mult),
-                         precond=PRECOND[precond], mixed=int(bool(mixed)), reserved=0,
+                         precond=PRECOND[precond], mixed=int(bool(mixed)), jd_inner=int(jd_inner),
                          tol=float(tol), switch_tol=float(max(switch_tol, tol)))
         st = DavidsonStats()
         eig = np.zeros(nb, dtype=np.float64)

@@ -31,6 +31,7 @@ namespace pwh {
 
 struct DavWs {
   DevBuf<char> vec;    // V, HV (npw x mmax each), X, HX, R, Tw (npw x nb each)
+  DevBuf<char> cg;     // Jacobi-Davidson PCG: r, z, p, q (npw x nb each), scalars
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
   DenseWs dense;
   double* h_rn = nullptr;  // pinned host mirrors
@@ -124,6 +125,10 @@ __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw
   }
 }
 
+__global__ void k_sqrt(double* __restrict__ a, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = sqrt(fmax(a[i], 0.0));
+}
+
 __global__ void k_copy_cols(const double2* __restrict__ src, int64_t lds, double2* __restrict__ dst,
                             int64_t ldd, int64_t npw, int k) {
   int64_t tot = npw * k;
@@ -154,6 +159,97 @@ __global__ void k_perm_out(const double2* __restrict__ src, int64_t lds, int64_t
   }
 }
 
+// ---------------------------------------- Jacobi-Davidson correction (PCG) --
+// Column j works on band idx[j].  All per-column scalars live on the device.
+// r = -R[:, idx[j]], t = 0
+__global__ void k_cg_init(const double2* __restrict__ R, int64_t ld, int64_t npw,
+                          const int* __restrict__ idx, double2* __restrict__ r,
+                          double2* __restrict__ t) {
+  const int j = blockIdx.y;
+  const double2* src = R + (size_t)idx[j] * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    r[(size_t)j * npw + i] = make_double2(-v.x, -v.y);
+    t[(size_t)j * npw + i] = make_double2(0.0, 0.0);
+  }
+}
+// z = K(T_G / eref[idx[j]]) (.) r  (Teter-Payne-Allan diagonal)
+__global__ void k_cg_precond(const double2* __restrict__ r, int64_t npw, const int* __restrict__ idx,
+                             const double* __restrict__ eref, const double* __restrict__ kin,
+                             double2* __restrict__ z) {
+  const int j = blockIdx.y;
+  const double e = eref[idx[j]];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = kin[i] / e;
+    const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+    const double k = p / (p + 16.0 * x * x * x * x);
+    const double2 v = r[(size_t)j * npw + i];
+    z[(size_t)j * npw + i] = make_double2(k * v.x, k * v.y);
+  }
+}
+// out[j] = Re <a_j, b_j>, one block per column (fixed-order reduction)
+__global__ void k_col_dot(const double2* __restrict__ a, const double2* __restrict__ b, int64_t npw,
+                          double* __restrict__ out) {
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < npw; i += blockDim.x) {
+    const double2 x = a[(size_t)j * npw + i], y = b[(size_t)j * npw + i];
+    acc += x.x * y.x + x.y * y.y;
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a2 += red[w];
+    out[j] = a2;
+  }
+}
+// q -= theta[idx[j]] p
+__global__ void k_cg_shift(double2* __restrict__ q, const double2* __restrict__ p, int64_t npw,
+                           const int* __restrict__ idx, const double* __restrict__ theta) {
+  const int j = blockIdx.y;
+  const double th = theta[idx[j]];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)j * npw + i;
+    const double2 a = q[o], b = p[o];
+    q[o] = make_double2(a.x - th * b.x, a.y - th * b.y);
+  }
+}
+// alpha = rho / <p,q> (0 where <p,q> <= 0: the column stops);  t += alpha p,
+// r -= alpha q
+__global__ void k_cg_step(double2* __restrict__ t, double2* __restrict__ r,
+                          const double2* __restrict__ p, const double2* __restrict__ q, int64_t npw,
+                          const double* __restrict__ rho, const double* __restrict__ pq) {
+  const int j = blockIdx.y;
+  const double alpha = (pq[j] > 0.0 && rho[j] > 0.0) ? rho[j] / pq[j] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)j * npw + i;
+    const double2 pv = p[o], qv = q[o];
+    t[o].x += alpha * pv.x;
+    t[o].y += alpha * pv.y;
+    r[o].x -= alpha * qv.x;
+    r[o].y -= alpha * qv.y;
+  }
+}
+// p = z + (rho_new / rho_old) p
+__global__ void k_cg_dir(double2* __restrict__ p, const double2* __restrict__ z, int64_t npw,
+                         const double* __restrict__ rho_new, const double* __restrict__ rho_old) {
+  const int j = blockIdx.y;
+  const double beta = rho_old[j] > 0.0 ? rho_new[j] / rho_old[j] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const size_t o = (size_t)j * npw + i;
+    const double2 zv = z[o], pv = p[o];
+    p[o] = make_double2(zv.x + beta * pv.x, zv.y + beta * pv.y);
+  }
+}
+
 static int grid1d(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (n + 255) / 256)); }
 
 // ------------------------------------------------------------------ solver --
@@ -163,6 +259,65 @@ struct Layout {
   double *theta, *rn, *eref, *t0;
   int *idx, *kk;
 };
+
+// P v = v - X (X^H v) on k columns (FP32 arithmetic, FP64 storage); W: nb x k.
+static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
+                  const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
+                  double2* C, int64_t ldc, cudaStream_t st);
+static void project_out(System& s, const double2* X, int nb, double2* v, int k, double2* W,
+                        cudaStream_t st) {
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
+  const int64_t npw = s.npw;
+  sgemm(s, PWH_MIXED, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
+  sgemm(s, PWH_MIXED, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
+}
+
+// Approximate solution t (npw x k) of (I-XX^H)(H-theta_j)(I-XX^H) t_j = -r_j
+// for the bands idx[0..k), by `iters` steps of CG preconditioned with the TPA
+// diagonal, H applied in reduced precision.
+static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const double2* R,
+                          const int* idx, int k, const double* theta, const double* eref,
+                          int iters, int prec, double2* t, double2* Wc, int* n_apply,
+                          cudaStream_t st) {
+  const int64_t npw = s.npw;
+  ensure(w.cg, (size_t)4 * npw * k * sizeof(double2) + 8 * (size_t)k * sizeof(double) + 256);
+  double2* r = (double2*)w.cg.p;
+  double2* z = r + (size_t)npw * k;
+  double2* p = z + (size_t)npw * k;
+  double2* q = p + (size_t)npw * k;
+  double* rho[2] = {(double*)(q + (size_t)npw * k), (double*)(q + (size_t)npw * k) + k};
+  double* pq = rho[1] + k;
+  const dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (npw + 255) / 256)), k);
+  k_cg_init<<<g2, 256, 0, st>>>(R, npw, npw, idx, r, t);
+  PWH_LAUNCH_CHECK();
+  k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
+  PWH_LAUNCH_CHECK();
+  project_out(s, X, nb, z, k, Wc, st);
+  PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  k_col_dot<<<k, 256, 0, st>>>(r, z, npw, rho[0]);
+  PWH_LAUNCH_CHECK();
+  int cur = 0;
+  for (int it = 0; it < iters; ++it) {
+    apply_internal(s, k, p, npw, q, npw, prec);
+    *n_apply += k;
+    k_cg_shift<<<g2, 256, 0, st>>>(q, p, npw, idx, theta);
+    PWH_LAUNCH_CHECK();
+    project_out(s, X, nb, q, k, Wc, st);
+    k_col_dot<<<k, 256, 0, st>>>(p, q, npw, pq);
+    PWH_LAUNCH_CHECK();
+    k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[cur], pq);
+    PWH_LAUNCH_CHECK();
+    if (it + 1 == iters) break;
+    k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
+    PWH_LAUNCH_CHECK();
+    project_out(s, X, nb, z, k, Wc, st);
+    k_col_dot<<<k, 256, 0, st>>>(r, z, npw, rho[cur ^ 1]);
+    PWH_LAUNCH_CHECK();
+    k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[cur ^ 1], rho[cur]);
+    PWH_LAUNCH_CHECK();
+    cur ^= 1;
+  }
+}
 
 static Layout carve(System& s, DavWs& w, int nb, int mmax) {
   const int64_t npw = s.npw;
@@ -350,10 +505,25 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     for (int b = 0; b < nb; ++b)
       if (w.h_rn[b] > thr) w.h_idx[k++] = b;
     PWH_CUDA(cudaMemcpyAsync(L.idx, w.h_idx, k * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (m + k > mmax) restart_from_ritz(false);
+    // Jacobi-Davidson steps in the FP64 phase, and in the reduced-precision
+    // phase once its residuals are within 100x of the hand-over target
+    const bool jd = o.mixed && o.jd_inner > 0 &&
+                    (phase_prec == PWH_FP64 || maxr <= 100.0 * o.switch_tol);
+    if (jd || m + k > mmax) restart_from_ritz(false);
     double2* T = L.V + (size_t)m * npw;
-    k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa, T, npw, L.t0);
-    PWH_LAUNCH_CHECK();
+    if (jd) {
+      // Jacobi-Davidson step: corrections from the reduced-precision operator
+      const int red = s.precision == PWH_FP64 ? PWH_MIXED : s.precision;
+      jd_correction(s, w, L.X, nb, L.R, L.idx, k, L.theta, L.eref, o.jd_inner, red, T, L.Wc,
+                    &S.n_apply, st);
+      k_col_dot<<<k, 256, 0, st>>>(T, T, npw, L.t0);
+      PWH_LAUNCH_CHECK();
+      k_sqrt<<<1, 256, 0, st>>>(L.t0, k);
+      PWH_LAUNCH_CHECK();
+    } else {
+      k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa, T, npw, L.t0);
+      PWH_LAUNCH_CHECK();
+    }
     for (int pass = 0; pass < 2; ++pass) {
       sgemm(s, phase_prec, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
       sgemm(s, phase_prec, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);

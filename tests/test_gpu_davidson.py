@@ -38,16 +38,17 @@ SMALL = [
 
 
 @pytest.mark.parametrize("kw,nb", SMALL)
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_jd"])
 def test_davidson_matches_dense_eigh(torch, kw, nb, mode):
     cell, b, v, beta, D = case(**kw)
     H = oh.dense_h(b, v, beta, D)
     ex = np.linalg.eigvalsh(H)[:nb]
-    s = system(cell, v, beta, D, precision="mixed" if mode == "mixed" else "fp64")
+    s = system(cell, v, beta, D, precision="fp64" if mode == "fp64" else "mixed")
     psi0 = syn.initial_bands(3, b.npw, nb)
     psi = torch.from_numpy(psi0).cuda()
     tol = 1e-10 if mode == "fp64" else 1e-9
-    eig, st, status = s.davidson(psi, tol=tol, mixed=(mode == "mixed"), switch_tol=1e-5)
+    eig, st, status = s.davidson(psi, tol=tol, mixed=(mode != "fp64"), switch_tol=1e-5,
+                                 jd_inner=10 if mode == "mixed_jd" else 0)
     assert status == 0 and st["max_resid"] <= tol
     bar = 1e-10 if mode == "fp64" else 1e-8
     assert np.abs(eig - ex).max() <= bar, (eig - ex)
@@ -55,7 +56,7 @@ def test_davidson_matches_dense_eigh(torch, kw, nb, mode):
     assert np.abs(X.conj() @ X.T - np.eye(nb)).max() < 1e-10
     r = np.linalg.norm(H @ X.T - X.T * eig[None, :], axis=0)
     assert r.max() <= 2 * tol
-    if mode == "mixed":
+    if mode != "fp64":
         assert st["switch_iter"] >= 1 and st["n_apply"] > st["n_apply_fp64"]
 
 
@@ -68,10 +69,11 @@ def test_davidson_small_workload_vs_oracle(torch):
     assert b.npw == 1503
     nb = cfg["nb"]
     ex = np.linalg.eigvalsh(oh.dense_h(b, v, beta, D))[:nb]
-    for mode in ("fp64", "mixed"):
-        s = system(cell, v, beta, D, precision="mixed" if mode == "mixed" else "fp64")
+    for mode in ("fp64", "mixed", "mixed_jd"):
+        s = system(cell, v, beta, D, precision="fp64" if mode == "fp64" else "mixed")
         psi = torch.from_numpy(syn.initial_bands(0, b.npw, nb)).cuda()
-        eig, st, status = s.davidson(psi, tol=1e-8, mixed=(mode == "mixed"))
+        eig, st, status = s.davidson(psi, tol=1e-8, mixed=(mode != "fp64"),
+                                     jd_inner=10 if mode == "mixed_jd" else 0)
         assert status == 0
         assert np.abs(eig - ex).max() <= 1e-8
         # residual recomputed by the oracle's FP64 operator
