@@ -213,6 +213,54 @@ typedef struct {
 pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                               int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
 
+/* ----------------------------------------------------- learned preconditioner --
+ * Not in the paper.  A 4 -> 64 -> 64 -> 1 SiLU network corrects the TPA
+ * diagonal per (shell of equal |k+G|, band): K = K_TPA * exp(clip(s, -3, 3)),
+ * s = MLP(f1..f4) with, for shell g and band n (Ritz value theta, residual
+ * norm |r|, kinetic energy E = <x|T|x>, mean potential vbar, x = T_g / E):
+ *   f1 = log(x + 0.05), f2 = (theta - vbar)/E, f3 = clip(log10|r|, -12, 2),
+ *   f4 = (T_g + vbar - theta)/(T_g + E).
+ * Parameter blob (FP32, pwh_mlp_num_params floats): W1 (64x4 row-major), b1,
+ * W2 (64x64), b2, W3 (64), b3, then min f1..f4 and max f1..f4 of the training
+ * data; outside that box the preconditioner uses plain TPA (s = 0).
+ * All array arguments below are DEVICE pointers unless stated. */
+pwh_status pwh_mlp_num_params(int32_t* n);
+
+/* s[r] = MLP(feats[4r .. 4r+3]) for r < rows (FP32). */
+pwh_status pwh_mlp_forward(pwh_system* sys, const float* params, const float* feats, int64_t rows,
+                           float* s_out);
+
+/* loss = sum_r w_r (s_r - y_r)^2 / wsum and grad_out = d loss / d params (the
+ * first 4545 entries of the blob), by reverse-mode differentiation. */
+pwh_status pwh_mlp_loss_grad(pwh_system* sys, const float* params, const float* feats,
+                             const float* y, const float* w, int64_t rows, double wsum,
+                             float* grad_out, float* loss_out);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; step counts
+ * from 1) on the 4545 network parameters; m, v: moment buffers. */
+pwh_status pwh_mlp_adam(pwh_system* sys, float* params, const float* grad, float* m, float* v,
+                        int32_t step, float lr);
+
+/* Training rows from one point of a Davidson trajectory: X (nb Ritz vectors),
+ * HX = H X (FP64), theta (HOST double[nb]) and the converged bands Xstar, all
+ * complex128 npw x nb in public order.  Row n*nshell + g: feats (4 floats),
+ * target y = log d - log K_TPA minus the band's weighted mean and weight w,
+ * where d = -<r,e>_g/<r,r>_g maps the residual r = HX - X theta onto the
+ * exact correction e = Xstar Xstar^H x - x on shell g (w = <r,r>_g/<r,r>;
+ * rows with d <= 0 get w = 0).  Synchronous. */
+pwh_status pwh_mlp_training_rows(pwh_system* sys, int32_t nb, const void* X, const void* HX,
+                                 const double* theta, const void* Xstar, float* feats, float* y,
+                                 float* w);
+
+/* Install the parameter blob (HOST pointer, n = pwh_mlp_num_params) used by
+ * PWH_PRECOND_MLP. */
+pwh_status pwh_set_mlp(pwh_system* sys, const float* blob, int32_t n);
+
+/* Shell decomposition (HOST outputs, any may be NULL except nshell): shell
+ * index of every public plane wave and 1/2|k+G|^2 of every shell. */
+pwh_status pwh_get_shells(const pwh_system* sys, int32_t* nshell, int32_t* shell_of_pw,
+                          double* shell_kinetic);
+
 /* -------------------------------------------------------------- measurement --
  * Per-family kernel timing: with timing on, the library brackets the launches
  * of each kernel family with CUDA events on the system's stream and

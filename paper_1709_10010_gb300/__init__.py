@@ -80,6 +80,13 @@ SIGNATURES = {
     "pwh_sync": (_c_i32, [_c_p]),
     "pwh_subspace_eigh": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_i32, _c_p, _c_p, _c_p, _c_i64,
                                    _c_i32]),
+    "pwh_mlp_num_params": (_c_i32, [ctypes.POINTER(_c_i32)]),
+    "pwh_mlp_forward": (_c_i32, [_c_p, _c_p, _c_p, _c_i64, _c_p]),
+    "pwh_mlp_loss_grad": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_i64, _c_d, _c_p, _c_p]),
+    "pwh_mlp_adam": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_i32, ctypes.c_float]),
+    "pwh_mlp_training_rows": (_c_i32, [_c_p, _c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p]),
+    "pwh_set_mlp": (_c_i32, [_c_p, _c_p, _c_i32]),
+    "pwh_get_shells": (_c_i32, [_c_p, ctypes.POINTER(_c_i32), _c_p, _c_p]),
     "pwh_set_kernel_timing": (_c_i32, [_c_p, _c_i32]),
     "pwh_get_kernel_times": (_c_i32, [_c_p, _c_p, _c_i32, ctypes.POINTER(_c_i32)]),
     "pwh_launch_count": (_c_i32, [ctypes.POINTER(_c_i64)]),
@@ -90,6 +97,8 @@ SIGNATURES = {
 }
 
 _lib = None
+MLP_PARAMS = 4545   # network parameters; the blob adds 8 feature-range floats
+MLP_BLOB = MLP_PARAMS + 8
 
 
 def lib():
@@ -305,6 +314,64 @@ class System:
         _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
                                       hpsi.ctypes.data_as(_c_p)))
         return hpsi
+
+    # ----------------------------------------------------- learned precond
+    def shells(self):
+        """(shell index of every public plane wave, kinetic energy of every shell)."""
+        n = _c_i32()
+        _check(lib().pwh_get_shells(self._h, ctypes.byref(n), None, None))
+        sh = np.empty(self.npw, dtype=np.int32)
+        T = np.empty(n.value, dtype=np.float64)
+        _check(lib().pwh_get_shells(self._h, ctypes.byref(n), sh.ctypes.data_as(_c_p),
+                                    T.ctypes.data_as(_c_p)))
+        return sh, T
+
+    def set_mlp(self, blob):
+        b = np.ascontiguousarray(blob, dtype=np.float32)
+        _check(lib().pwh_set_mlp(self._h, b.ctypes.data_as(_c_p), int(b.size)))
+
+    def mlp_forward(self, params, feats):
+        torch = _torch()
+        out = torch.empty(feats.shape[0], dtype=torch.float32, device=feats.device)
+        _check(lib().pwh_mlp_forward(self._h, ctypes.c_void_p(params.data_ptr()),
+                                     ctypes.c_void_p(feats.data_ptr()), int(feats.shape[0]),
+                                     ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def mlp_loss_grad(self, params, feats, y, w, wsum=None):
+        torch = _torch()
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feats.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feats.device)
+        wsum = float(w.double().sum().item()) if wsum is None else float(wsum)
+        _check(lib().pwh_mlp_loss_grad(self._h, ctypes.c_void_p(params.data_ptr()),
+                                       ctypes.c_void_p(feats.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       ctypes.c_void_p(w.data_ptr()), int(feats.shape[0]), wsum,
+                                       ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr())))
+        return loss, g
+
+    def mlp_adam(self, params, g, m, v, step, lr):
+        _check(lib().pwh_mlp_adam(self._h, ctypes.c_void_p(params.data_ptr()),
+                                  ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                                  ctypes.c_void_p(v.data_ptr()), int(step), float(lr)))
+
+    def mlp_training_rows(self, X, HX, theta, Xstar):
+        """Rows of (features, target, weight) from one trajectory point; X, HX,
+        Xstar: (nb, npw) CUDA complex128 (public order), theta: numpy (nb,)."""
+        torch = _torch()
+        nb = int(X.shape[0])
+        nsh = int(self.shells()[1].size)
+        F = torch.empty((nb * nsh, 4), dtype=torch.float32, device=X.device)
+        y = torch.empty(nb * nsh, dtype=torch.float32, device=X.device)
+        w = torch.empty(nb * nsh, dtype=torch.float32, device=X.device)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        for t in (X, HX, Xstar):
+            _band_ptr(t, self.npw)
+        _check(lib().pwh_mlp_training_rows(self._h, nb, ctypes.c_void_p(X.data_ptr()),
+                                           ctypes.c_void_p(HX.data_ptr()), th.ctypes.data_as(_c_p),
+                                           ctypes.c_void_p(Xstar.data_ptr()),
+                                           ctypes.c_void_p(F.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           ctypes.c_void_p(w.data_ptr())))
+        return F, y, w
 
     # ---------------------------------------------------------- eigensolver
     def davidson(self, psi, tol=1e-8, max_iter=200, mult=3, precond="tpa", mixed=False,

@@ -136,6 +136,9 @@ struct System {
   std::vector<int32_t> stick_off;  // nsticks+1, internal offsets
   std::vector<int32_t> stick_col, stick_y;  // column index, y grid index
   std::vector<int32_t> col_x;      // x grid index of each column
+  int nshell = 0;                  // shells of equal |k+G|^2 (public-order rule)
+  std::vector<int32_t> shell_pub;  // shell of each public plane wave
+  std::vector<double> Tshell_h;    // 1/2|k+G|^2 of each shell
 
   // device: maps and tables
   int32_t* d_int_to_pub = nullptr;
@@ -150,9 +153,12 @@ struct System {
   double2* d_tw64 = nullptr;        // twiddle tables, FP64
   float2* d_tw32 = nullptr;         // same, rounded to FP32
   int16_t* d_perm = nullptr;        // digit-reversal tables
+  int32_t* d_shell = nullptr;       // shell of each internal plane wave
+  double* d_Tshell = nullptr;       // nshell kinetic energies
 
   // potential (internal layout [i3][i2][i1], scaled by 1/(N1 N2 N3))
   bool have_v = false;
+  double vbar = 0.0;                // mean of V_LOC(r) over the grid
   double* d_v64 = nullptr;
   float* d_v32 = nullptr;
 
@@ -171,6 +177,8 @@ struct System {
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
   int* d_err = nullptr;             // device error word (bounded waits that gave up)
+  float* d_mlp = nullptr;           // learned-preconditioner parameters
+  bool have_mlp = false;
   DavWs* dav = nullptr;             // eigensolver workspace
   KernelTimer timer;
   int fft_batch = 32;               // bands per FFT batch (bounded by workspace)
@@ -245,6 +253,9 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
 int* device_error_word(System& s);
 void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                     int64_t ldh, int precision);
+void permute_public_to_internal(System& s, const double2* src, double2* dst, int nb);
+void mlp_factors(System& s, const int* idx, int k, const double* theta, const double* rn,
+                 const double* eref, float* out, cudaStream_t st);
 
 }  // namespace pwh
 

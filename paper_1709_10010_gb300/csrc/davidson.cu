@@ -32,6 +32,7 @@ namespace pwh {
 struct DavWs {
   DevBuf<char> vec;    // V, HV (npw x mmax each), X, HX, R, Tw (npw x nb each)
   DevBuf<char> cg;     // Jacobi-Davidson PCG: r, z, p, q (npw x nb each), scalars
+  DevBuf<char> mlp;    // learned-preconditioner factors (k x nshell)
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
   DenseWs dense;
   double* h_rn = nullptr;  // pinned host mirrors
@@ -92,11 +93,13 @@ __global__ void k_residual(const double2* __restrict__ X, const double2* __restr
   }
 }
 
-// T[:, j] = K(T_G / eref) (.) R[:, idx[j]] (K = 1 when tpa == 0); t0[j] = ||t_j||.
+// T[:, j] = K(T_G / eref) (.) R[:, idx[j]] (K = 1 when tpa == 0); with the
+// learned correction, K *= exp(s[j, shell(G)]).  t0[j] = ||t_j||.
 __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw,
                           const int* __restrict__ idx, const double* __restrict__ eref,
                           const double* __restrict__ kin, int tpa, double2* __restrict__ T,
-                          int64_t ldt, double* __restrict__ t0) {
+                          int64_t ldt, double* __restrict__ t0, const float* __restrict__ sfac,
+                          const int32_t* __restrict__ shell, int nshell) {
   const int j = blockIdx.x;
   const int src = idx[j];
   const double2* r = R + (size_t)src * ld;
@@ -110,6 +113,7 @@ __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw
       double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
       k = p / (p + 16.0 * x * x * x * x);
     }
+    if (sfac) k *= exp((double)sfac[(size_t)j * nshell + shell[i]]);
     double2 v = make_double2(k * r[i].x, k * r[i].y);
     t[i] = v;
     s2 += v.x * v.x + v.y * v.y;
@@ -521,7 +525,14 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       k_sqrt<<<1, 256, 0, st>>>(L.t0, k);
       PWH_LAUNCH_CHECK();
     } else {
-      k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa, T, npw, L.t0);
+      float* sfac = nullptr;
+      if (o.precond == PWH_PRECOND_MLP) {
+        ensure(w.mlp, (size_t)k * s.nshell * sizeof(float));
+        sfac = (float*)w.mlp.p;
+        mlp_factors(s, L.idx, k, L.theta, L.rn, L.eref, sfac, st);
+      }
+      k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa || sfac, T, npw, L.t0,
+                                   sfac, s.d_shell, s.nshell);
       PWH_LAUNCH_CHECK();
     }
     for (int pass = 0; pass < 2; ++pass) {
@@ -580,6 +591,8 @@ extern "C" pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opt
                   "unknown preconditioner");
     PWH_CHECK_ARG(ld_psi >= s.npw, "ld_psi < npw");
     if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
+    if (o.precond == PWH_PRECOND_MLP && !s.have_mlp)
+      throw Error{PWH_ERR_STATE, "PWH_PRECOND_MLP needs pwh_set_mlp first"};
     st = davidson_solve(s, o, (double2*)psi_io, ld_psi, eig, stats);
     if (st == PWH_ERR_NOT_CONVERGED) set_error("Davidson stopped at max_iter before tol");
     if (st == PWH_ERR_NONFINITE) set_error("non-finite residual norm");

@@ -79,7 +79,7 @@ System::~System() {
                   d_stick_y, d_col_x, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
-                  ws_tc.p, d_err};
+                  ws_tc.p, d_err, d_shell, d_Tshell, d_mlp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -157,6 +157,13 @@ static void build_basis(System& s, const int fft_req[3]) {
   s.npw = (int64_t)pw.size();
   s.miller.resize(3 * s.npw);
   s.kin_pub.resize(s.npw);
+  s.shell_pub.resize(s.npw);
+  s.Tshell_h.clear();
+  for (int64_t j = 0; j < s.npw; ++j) {
+    s.shell_pub[j] = (int32_t)pw[j].shell;
+    if ((int64_t)s.Tshell_h.size() <= pw[j].shell) s.Tshell_h.push_back(0.5 * pw[j].q2);
+  }
+  s.nshell = (int)s.Tshell_h.size();
   int mmax[3] = {0, 0, 0};
   for (int64_t j = 0; j < s.npw; ++j) {
     for (int d = 0; d < 3; ++d) {
@@ -237,6 +244,10 @@ static void upload_basis(System& s) {
   s.d_stick_col = upload(s.stick_col, st);
   s.d_stick_y = upload(s.stick_y, st);
   s.d_col_x = upload(s.col_x, st);
+  std::vector<int32_t> shell_int(s.npw);
+  for (int64_t i = 0; i < s.npw; ++i) shell_int[i] = s.shell_pub[s.int_to_pub[i]];
+  s.d_shell = upload(shell_int, st);
+  s.d_Tshell = upload(s.Tshell_h, st);
   // host vectors above die at scope end: wait for the copies
   PWH_CUDA(cudaStreamSynchronize(st));
 }
@@ -256,6 +267,21 @@ __global__ void k_potential_layout(const double* __restrict__ v, int n1, int n2,
     double x = v[((int64_t)i1 * n2 + i2) * n3 + i3] * scale;
     v64[t] = x;
     v32[t] = (float)x;
+  }
+}
+
+// sum of the (1/N^3-scaled) grid potential = mean V(r); one block, fixed order
+__global__ void k_grid_sum(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += v[i];
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = t;
   }
 }
 
@@ -380,6 +406,14 @@ pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_devi
       cudaStreamSynchronize(s.stream);
       cudaFree(tmp);
     }
+    PWH_CUDA(e);
+    double* dsum = nullptr;
+    PWH_CUDA(cudaMalloc((void**)&dsum, sizeof(double)));
+    k_grid_sum<<<1, 1024, 0, s.stream>>>(s.d_v64, tot, dsum);
+    note_launch();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&s.vbar, dsum, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(dsum);
     PWH_CUDA(e);
     s.have_v = true;
   });
