@@ -184,6 +184,7 @@ def run_ours(a):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("bench_timed")
     e0.record(stream)
     n_apply, stats = 0, []
     eig = None
@@ -193,6 +194,7 @@ def run_ours(a):
         n_apply += st["n_apply"]
         stats.append(st)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     elapsed = e0.elapsed_time(e1) / 1e3

@@ -32,14 +32,14 @@ def init_params(seed: int) -> np.ndarray:
 
 def harvest(system, psi0, snapshots=(2, 5, 10, 20), xstar=None, tol=1e-8):
     """Training rows from one system.  psi0: (nb, npw) CUDA complex128 starting
-    bands.  Returns (F, y, w) CUDA tensors."""
+    bands.  Returns (F, y, w) CUDA tensors.  Leaves the system's apply
+    precision at FP64."""
     import torch
     nb = int(psi0.shape[0])
     if xstar is None:
         xstar = psi0.clone()
         _, _, st = system.davidson(xstar, tol=tol, mixed=True, switch_tol=1e-3, jd_inner=20,
                                    check=False)
-    prec_saved = None
     Fs, ys, ws = [], [], []
     for it in snapshots:
         X = psi0.clone()
@@ -50,7 +50,6 @@ def harvest(system, psi0, snapshots=(2, 5, 10, 20), xstar=None, tol=1e-8):
         Fs.append(F)
         ys.append(y)
         ws.append(w)
-    del prec_saved
     return torch.cat(Fs), torch.cat(ys), torch.cat(ws)
 
 
@@ -77,3 +76,80 @@ def train(system, rows, steps=2000, lr=2e-3, seed=0, log_every=0):
     blob = np.concatenate([p.cpu().numpy(), lo, hi]).astype(np.float32)
     assert blob.size == MLP_BLOB
     return blob, hist
+
+
+def workload_cell(seed):
+    """A cell of the learned-preconditioner workload: cubic a ~ U(16, 20) bohr,
+    32-64 atoms, 40 Ry, s,p,d projectors (the shape of the 34k-plane-wave cell)."""
+    from . import synthetic as syn
+    rng = np.random.default_rng([int(seed), 3])
+    a = float(rng.uniform(16.0, 20.0))
+    natoms = int(rng.integers(32, 65))
+    return syn.make_cell(seed, a, natoms, 40.0, 2)
+
+
+def load_system(cell, precision="mixed"):
+    import paper_1709_10010_gb300 as pwh
+    from . import synthetic as syn
+    s = pwh.System.from_cell(cell, precision=precision)
+    s.set_potential(syn.potential_grid(cell, s.fft))
+    s.set_projectors(syn.projectors(cell, s.miller()), syn.d_diagonal(cell))
+    return s
+
+
+def main():
+    import argparse
+    import json
+    import time
+
+    import torch
+
+    from . import synthetic as syn
+    ap = argparse.ArgumentParser(description="train the learned preconditioner on GPU and "
+                                             "compare it with TPA on held-out cells")
+    ap.add_argument("--train", type=int, default=32)
+    ap.add_argument("--test", type=int, default=8)
+    ap.add_argument("--nb", type=int, default=128)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--out", default="mlp_blob.npy")
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    t0 = time.time()
+    parts = []
+    s = None
+    for seed in range(1000, 1000 + a.train):
+        s = load_system(workload_cell(seed))
+        psi0 = torch.from_numpy(syn.initial_bands(seed, s.npw, a.nb)).cuda()
+        parts.append(harvest(s, psi0, snapshots=(2, 5, 10)))
+    rows = tuple(torch.cat([p[i] for p in parts]) for i in range(3))
+    t_data = time.time() - t0
+    blob, hist = train(s, rows, steps=a.steps, lr=2e-3, log_every=500)
+    t_train = time.time() - t0 - t_data
+    np.save(a.out, blob)
+    res = []
+    for seed in range(2000, 2000 + a.test):
+        s = load_system(workload_cell(seed))
+        s.set_mlp(blob)
+        psi0 = torch.from_numpy(syn.initial_bands(seed, s.npw, a.nb)).cuda()
+        row = {"seed": seed, "npw": s.npw}
+        for pc in ("tpa", "mlp"):
+            for mode, kw in (("mixed", dict(mixed=True, switch_tol=1e-5, jd_inner=0)),
+                             ("mixed_jd", dict(mixed=True, switch_tol=1e-3, jd_inner=20))):
+                psi = psi0.clone()
+                torch.cuda.synchronize()
+                t = time.time()
+                eig, st, status = s.davidson(psi, tol=1e-8, precond=pc, check=False, **kw)
+                row[f"{pc}_{mode}"] = {"iters": st["iters"], "n_apply": st["n_apply"],
+                                       "time_s": time.time() - t, "status": status,
+                                       "resid": st["max_resid"], "eig0": float(eig[0])}
+                row.setdefault("eigs", {})[f"{pc}_{mode}"] = eig
+        row["max_dlambda_tpa_vs_mlp"] = float(np.abs(row["eigs"]["tpa_mixed"] - row["eigs"]["mlp_mixed"]).max())
+        del row["eigs"]
+        res.append(row)
+    summary = {"train_cells": a.train, "test_cells": a.test, "rows": int(rows[0].shape[0]),
+               "data_s": t_data, "train_s": t_train, "loss_history": hist, "held_out": res}
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
