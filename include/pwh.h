@@ -290,6 +290,20 @@ pwh_status pwh_get_kernel_times(pwh_system* sys, pwh_kernel_time* out, int32_t m
  * counter, all systems). */
 pwh_status pwh_launch_count(int64_t* count);
 
+/* Batched eigensolves of n independent systems (cells x k-points: the pool and
+ * image levels of Sec. "New parallelization levels"): a pool of nthreads host
+ * threads runs pwh_davidson_solve on every system, each on its own stream, so
+ * their kernels overlap on the GPU.  Arrays of length n: systems (distinct,
+ * each created with its own stream for overlap), opts, psi_io (DEVICE),
+ * ld_psi, eig (HOST double[nb_i]), stats (may be NULL), status_out (HOST).
+ * Returns PWH_OK when every solve did, else the first failing status (its
+ * message names the system). */
+pwh_status pwh_batch_davidson_solve(int32_t n, pwh_system* const* systems,
+                                    const pwh_davidson_opts* opts, void* const* psi_io,
+                                    const int64_t* ld_psi, double* const* eig,
+                                    pwh_davidson_stats* stats, pwh_status* status_out,
+                                    int32_t nthreads);
+
 /* Subspace diagonalisation (the dense eigensolve of the O_ij matrices, Sec.
  * "New parallelization levels"), as used by pwh_davidson_solve: the lowest nk
  * eigenpairs of the n x n Hermitian H (DEVICE complex128, column-major, ld >=

@@ -78,6 +78,7 @@ SIGNATURES = {
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
+    "pwh_batch_davidson_solve": (_c_i32, [_c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i32]),
     "pwh_subspace_eigh": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_i32, _c_p, _c_p, _c_p, _c_i64,
                                    _c_i32]),
     "pwh_mlp_num_params": (_c_i32, [ctypes.POINTER(_c_i32)]),
@@ -391,4 +392,30 @@ class System:
         if check and status not in (0,):
             _check(status)
         return eig, st.as_dict(), status
+
+
+def batch_davidson(systems, psis, tol=1e-8, max_iter=200, mult=3, precond="tpa", mixed=True,
+                   switch_tol=1e-3, jd_inner=20, nthreads=16):
+    """Solve many independent systems concurrently (pwh_batch_davidson_solve).
+    systems: list of System (each created with its own stream); psis: list of
+    (nb_i, npw_i) CUDA complex128 tensors (starting bands in, eigenvectors
+    out).  Returns (list of eigenvalue arrays, list of stats dicts, statuses)."""
+    n = len(systems)
+    hs = (_c_p * n)(*[s._h.value for s in systems])
+    opts = (DavidsonOpts * n)()
+    ptrs = (_c_p * n)()
+    lds = (_c_i64 * n)()
+    eigs = [np.zeros(int(p.shape[0]), dtype=np.float64) for p in psis]
+    eptr = (_c_p * n)(*[e.ctypes.data for e in eigs])
+    stats = (DavidsonStats * n)()
+    status = (_c_i32 * n)()
+    for i, (s, p) in enumerate(zip(systems, psis)):
+        ptr, ld = _band_ptr(p, s.npw)
+        ptrs[i] = ptr.value
+        lds[i] = ld
+        opts[i] = DavidsonOpts(nb=int(p.shape[0]), max_iter=int(max_iter), max_subspace_mult=int(mult),
+                               precond=PRECOND[precond], mixed=int(bool(mixed)), jd_inner=int(jd_inner),
+                               tol=float(tol), switch_tol=float(max(switch_tol, tol)))
+    st = lib().pwh_batch_davidson_solve(n, hs, opts, ptrs, lds, eptr, stats, status, int(nthreads))
+    return eigs, [stats[i].as_dict() for i in range(n)], [int(status[i]) for i in range(n)], st
 

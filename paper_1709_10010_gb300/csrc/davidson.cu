@@ -395,9 +395,10 @@ static double now_s() {
 
 static void check_err(System& s) {
   int e = 0;
-  PWH_CUDA(cudaMemcpy(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost));
+  PWH_CUDA(cudaMemcpyAsync(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+  PWH_CUDA(cudaStreamSynchronize(s.stream));
   if (e) {
-    PWH_CUDA(cudaMemset(s.d_err, 0, sizeof(int)));
+    PWH_CUDA(cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream));
     throw Error{(pwh_status)e, "a bounded device wait gave up inside the eigensolver"};
   }
 }
@@ -411,6 +412,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   DavWs& w = *s.dav;
   Layout L = carve(s, w, nb, mmax);
   cudaStream_t st = s.stream;
+  // grow every workspace the loop can need now, so that no allocation (and no
+  // device-wide synchronisation) happens inside the iterations
+  jacobi_reserve(w.dense, mmax, nb);
+  if (o.mixed && o.jd_inner > 0)
+    ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
   const int tpa = o.precond == PWH_PRECOND_TPA ? 1 : 0;
   pwh_davidson_stats S{};

@@ -15,6 +15,7 @@
 // returns.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 #include "dense.cuh"
@@ -475,12 +476,10 @@ static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0
   a.gb.err = device_error_word(s);
   const int P = np / 2;
   const size_t smem = (size_t)P * (sizeof(cx<T>) + sizeof(T) + 2 * sizeof(int)) + 16;
-  static bool attr[2] = {false, false};
-  const int ti = sizeof(T) == 8 ? 0 : 1;
-  if (!attr[ti]) {
-    PWH_CUDA(cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr[ti] = true;
-  }
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  });
   int dev = 0, nsm = 0, per_sm = 0;
   PWH_CUDA(cudaGetDevice(&dev));
   PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -563,6 +562,13 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 12, out_buf, st);
   k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, out_buf, n, nk, theta, C, Qkeep, ldk);
   PWH_LAUNCH_CHECK();
+}
+
+void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
+  const size_t nn = (size_t)nmax * nmax;
+  ensure(w.jac, 5 * nn * sizeof(double2) + 4 * nn * sizeof(float2) + 256);
+  ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
+  if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
 }
 
 void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {

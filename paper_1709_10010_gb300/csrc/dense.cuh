@@ -28,6 +28,10 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
 // Device word holding the number of sweeps of the last jacobi_eigh.
 inline int* jacobi_sweeps_word(DenseWs& w) { return (int*)w.ctl + 9; }
 
+// Grow the workspaces for subspaces up to nmax and Cholesky blocks up to kmax
+// (so that no allocation, hence no device-wide synchronisation, happens later).
+void jacobi_reserve(DenseWs& w, int nmax, int kmax);
+
 // Complete columns [m0, m) of a Hermitian matrix computed as V^H HV[:, m0:m].
 void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);
 

@@ -382,14 +382,12 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   while (rows > 1 && plane_smem<T>(s, rows) > budget) rows = (rows + 1) / 2;
   const size_t psmem = plane_smem<T>(s, rows);
   if (psmem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
-  static bool attr_done[2] = {false, false};
-  int ti = sizeof(T) == 8 ? 0 : 1;
-  if (!attr_done[ti]) {
-    PWH_CUDA(cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    PWH_CUDA(cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    PWH_CUDA(cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr_done[ti] = true;
-  }
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
   const T* V = sizeof(T) == 8 ? (const T*)s.d_v64 : (const T*)s.d_v32;
   const bool dp = sizeof(T) == 8;
   // algorithmic work per band (nominal 5 N log2 N flops per complex transform of

@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "gemm.cuh"
@@ -394,16 +395,17 @@ __global__ void k_d_to_f32(const double2* __restrict__ src, int64_t n, float2* _
 
 // ---------------------------------------------------------------- host -----
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  std::call_once(once, [] {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
-    PWH_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                              cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      throw Error{PWH_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  if (!fn) throw Error{PWH_ERR_CUDA, "cuTensorMapEncodeTiled unavailable"};
   return fn;
 }
 
@@ -463,12 +465,11 @@ static void launch_tc(System& s, int mode, const CUtensorMap& ma, const CUtensor
   TimedScope ts(s, mode == 0 ? KF_TC_BECP : KF_TC_BACK, st, 2.0 * a.M * (double)a.N * kk,
                 2.0 * ((double)a.M + a.N) * kk + (mode == 0 ? 4.0 * gz * (double)a.M * a.N
                                                             : 32.0 * a.M * (a.N / 2)));
-  static bool attr = false;
-  if (!attr) {
-    PWH_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    PWH_CUDA(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    attr = true;
-  }
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
   dim3 grid(gm, gn, gz);
   if (mode == 0)
     k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);

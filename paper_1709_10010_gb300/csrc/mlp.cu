@@ -12,6 +12,7 @@
 // then 8 floats of feature ranges (min f1..f4, max f1..f4) outside which the
 // preconditioner falls back to plain TPA (s = 0).
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <vector>
 
@@ -374,12 +375,11 @@ pwh_status pwh_mlp_loss_grad(pwh_system* sys, const float* params, const float* 
     PWH_CHECK_ARG(sys && params && feats && y && w && grad_out && loss_out, "null argument");
     PWH_CHECK_ARG(rows >= 1 && wsum > 0, "rows >= 1 and wsum > 0 required");
     System& s = sys->s;
-    static bool attr = false;
-    if (!attr) {
-      PWH_CUDA(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)grad_smem()));
-      attr = true;
-    }
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+      cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)grad_smem());
+    });
     PWH_CUDA(cudaMemsetAsync(grad_out, 0, kMlpParams * sizeof(float), s.stream));
     PWH_CUDA(cudaMemsetAsync(loss_out, 0, sizeof(float), s.stream));
     const int blocks = (int)((rows + GR - 1) / GR);

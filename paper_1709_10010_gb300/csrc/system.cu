@@ -412,7 +412,8 @@ pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_devi
     k_grid_sum<<<1, 1024, 0, s.stream>>>(s.d_v64, tot, dsum);
     note_launch();
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpy(&s.vbar, dsum, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&s.vbar, dsum, sizeof(double), cudaMemcpyDeviceToHost, s.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
     cudaFree(dsum);
     PWH_CUDA(e);
     s.have_v = true;
@@ -516,9 +517,10 @@ pwh_status pwh_sync(pwh_system* sys) {
     System& s = sys->s;
     PWH_CUDA(cudaStreamSynchronize(s.stream));
     int e = 0;
-    PWH_CUDA(cudaMemcpy(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost));
+    PWH_CUDA(cudaMemcpyAsync(&e, device_error_word(s), sizeof(int), cudaMemcpyDeviceToHost, s.stream));
+    PWH_CUDA(cudaStreamSynchronize(s.stream));
     if (e != 0) {
-      PWH_CUDA(cudaMemset(s.d_err, 0, sizeof(int)));
+      PWH_CUDA(cudaMemsetAsync(s.d_err, 0, sizeof(int), s.stream));
       throw Error{(pwh_status)e, "a bounded device wait gave up (kernel returned early)"};
     }
   });

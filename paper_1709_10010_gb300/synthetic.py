@@ -219,3 +219,24 @@ CONFIGS = {
 def config_cell(name: str, seed: int = 0) -> Cell:
     c = CONFIGS[name]
     return make_cell(seed, c["a"], c["natoms"], c["ecut_ry"], c["lmax"])
+
+
+# 2x2x2 Monkhorst-Pack grid (fractional): all eight (+-1/4, +-1/4, +-1/4)
+MP222 = [(sx * 0.25, sy * 0.25, sz * 0.25) for sx in (-1, 1) for sy in (-1, 1) for sz in (-1, 1)]
+
+
+def batched_workload(ncells: int = 32, seed: int = 0, ecut_ry: float = 30.0):
+    """Independent systems of the batched workload: ``ncells`` cubic cells with
+    edge ~ U(8, 14) bohr and 4-16 atoms (s,p,d projectors), 30 Ry, each at the
+    eight k-points of a 2x2x2 Monkhorst-Pack grid, 24-48 bands per cell.
+    Draws from ``default_rng([seed, 4])``: per cell edge, atom count, band count.
+    Returns a list of (cell, nb), cells at a k-point sharing the cell's atoms."""
+    rng = np.random.default_rng([int(seed), 4])
+    out = []
+    for c in range(ncells):
+        a = float(rng.uniform(8.0, 14.0))
+        natoms = int(rng.integers(4, 17))
+        nb = int(rng.integers(24, 49))
+        for k in MP222:
+            out.append((make_cell(10_000 + 100 * seed + c, a, natoms, ecut_ry, 2, kpoint=k), nb))
+    return out
