@@ -129,6 +129,17 @@ __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw
   }
 }
 
+// After a restart from Ritz vectors: Hs[0:nb, 0:nb] = diag(theta) and the kept
+// Jacobi basis of that block = identity (theta is ascending).
+__global__ void k_ritz_block(double2* __restrict__ Hs, int64_t ldh, double2* __restrict__ Qk,
+                             const double* __restrict__ theta, int nb) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nb * nb; t += gridDim.x * blockDim.x) {
+    const int i = t % nb, j = t / nb;
+    Hs[(size_t)j * ldh + i] = make_double2(i == j ? theta[i] : 0.0, 0.0);
+    Qk[(size_t)j * ldh + i] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
 __global__ void k_sqrt(double* __restrict__ a, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = sqrt(fmax(a[i], 0.0));
 }
@@ -364,12 +375,14 @@ static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 
                   double2* C, int64_t ldc, cudaStream_t st);
 
 static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const double* t0,
-                   double drop_rel, cudaStream_t st, int prec = PWH_FP64) {
+                   double drop_rel, cudaStream_t st, int prec = PWH_FP64,
+                   int prec_first = -1) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
   const int64_t npw = s.npw;
-  sgemm(s, prec, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
+  const int p1 = prec_first < 0 ? prec : prec_first;  // first pass may be cheaper
+  sgemm(s, p1, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
   cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
-  sgemm(s, prec, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
+  sgemm(s, p1, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
   sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
   cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
   sgemm(s, prec, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
@@ -519,7 +532,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // phase once its residuals are within 100x of the hand-over target
     const bool jd = o.mixed && o.jd_inner > 0 &&
                     (phase_prec == PWH_FP64 || maxr <= 100.0 * o.switch_tol);
-    if (jd || m + k > mmax) restart_from_ritz(false);
+    if (jd || m + k > mmax) {
+      restart_from_ritz(false);
+      if (jd) {
+        // V = X: the leading block of Hs is diag(theta), its eigenbasis the identity
+        k_ritz_block<<<64, 256, 0, st>>>(L.Hs, mmax, L.Qk, L.theta, nb);
+        PWH_LAUNCH_CHECK();
+        hs_valid = nb;
+      }
+    }
     double2* T = L.V + (size_t)m * npw;
     if (jd) {
       // Jacobi-Davidson step: corrections from the reduced-precision operator
@@ -541,9 +562,16 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
                                    sfac, s.d_shell, s.nshell);
       PWH_LAUNCH_CHECK();
     }
+    // project twice; with Jacobi-Davidson corrections (already orthogonal to X
+    // in reduced precision) the first pass runs in FP32 arithmetic and the
+    // second, in the phase's precision, removes what it left.  Both
+    // Cholesky-QR passes stay in the phase's precision: a reduced-precision
+    // T Tr would bring back components along V that nothing removes.
+    const int first = jd ? PWH_MIXED : phase_prec;
     for (int pass = 0; pass < 2; ++pass) {
-      sgemm(s, phase_prec, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
-      sgemm(s, phase_prec, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
+      const int pp = pass == 0 ? first : phase_prec;
+      sgemm(s, pp, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
+      sgemm(s, pp, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
     }
     const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st, phase_prec);
     if (kn == 0) {

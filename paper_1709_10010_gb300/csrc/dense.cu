@@ -106,7 +106,18 @@ struct JacobiArgsT {
   GridBar gb;
 };
 
-template <typename T>
+// All threads of all CTAs of the cluster (the whole grid when launched as one
+// cluster): hardware barrier with release/acquire ordering at cluster scope.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n"
+      "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// CLUSTER: the grid is one thread-block cluster and rounds are separated by
+// the hardware cluster barrier; otherwise by the bounded grid barrier of a
+// cooperative launch.
+template <typename T, bool CLUSTER>
 __global__ void k_jacobi(JacobiArgsT<T> a) {
   extern __shared__ __align__(16) unsigned char jsm[];
   const int n = a.n, np = a.np, P = np / 2;
@@ -231,7 +242,11 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
         }
       }
       cur ^= 1;
-      if (!grid_sync(a.gb)) return;
+      if (CLUSTER) {
+        cluster_sync_all();
+      } else if (!grid_sync(a.gb)) {
+        return;
+      }
     }
     // convergence of the current matrix, decided by block 0 for everyone
     if (blockIdx.x == 0) {
@@ -260,7 +275,11 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
         *(volatile int*)a.conv = s_red[0][0] <= a.tol * fmax(s_red[1][0], 1e-300) ? 1 : 0;
       }
     }
-    if (!grid_sync(a.gb)) return;
+    if (CLUSTER) {
+      cluster_sync_all();
+    } else if (!grid_sync(a.gb)) {
+      return;
+    }
     if (*(volatile int*)a.conv) {
       ++sweep;
       break;
@@ -477,18 +496,63 @@ static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0
   const int P = np / 2;
   const size_t smem = (size_t)P * (sizeof(cx<T>) + sizeof(T) + 2 * sizeof(int)) + 16;
   static std::once_flag attr_once;
+  static int cluster_size = 0;  // largest cluster (16 or 8) that fits, 0 if none
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_jacobi<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_jacobi<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 64 * 1024;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_jacobi<T, true>, &cfg) == cudaSuccess &&
+          nclusters >= 1) {
+        cluster_size = cs;
+        break;
+      }
+    }
+    cudaGetLastError();  // clear a refused query
   });
+  // Reduced precision, small size: one cluster, hardware barrier per round
+  // (beyond ~192 the per-thread share of each round outweighs the barrier)
+  if (sizeof(T) == 4 && n <= 192 && cluster_size > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster_size);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cluster_size;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    PWH_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi<T, true>, a));
+    note_launch();
+    return;
+  }
   int dev = 0, nsm = 0, per_sm = 0;
   PWH_CUDA(cudaGetDevice(&dev));
   PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T>, 256, smem));
+  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi<T, false>, 256, smem));
+  // FP32 stage: few blocks (the per-round barrier latency dominates);
+  // FP64 stage: every SM, the FP64 units are the limit
   const int64_t items = (int64_t)P * P + (int64_t)n * P;
-  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((items + 511) / 512, nsm));
+  const int64_t per_block = sizeof(T) == 8 ? 64 : 256;
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>((items + per_block - 1) / per_block, nsm));
   const int blocks = std::max(1, std::min(want, nsm * std::max(per_sm, 1)));
   void* args[] = {&a};
-  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi<T>, blocks, 256, args, smem, st));
+  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi<T, false>, blocks, 256, args, smem, st));
   note_launch();
 }
 
@@ -533,7 +597,9 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   k_c64_to_c32<<<gq, 256, 0, st>>>(Q0, n, n, q0);
   PWH_LAUNCH_CHECK();
   int* ob32 = (int*)(ctl + 10);  // FP32 stage: result buffer index, sweeps
-  launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 2e-6, 30, ob32, st);
+  // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
+  // convergence) usually finishes
+  launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 4e-7, 30, ob32, st);
   // the FP32 eigenvectors sit in q0 or q1 (ob32[0]): widen them to FP64
   k_select_buf<<<gq, 256, 0, st>>>(q0, q1, ob32, (int64_t)nn, Q0);
   PWH_LAUNCH_CHECK();

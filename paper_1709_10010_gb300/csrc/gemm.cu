@@ -137,9 +137,11 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
   const int gm = (M + GBM - 1) / GBM, gn = (N + GBN - 1) / GBN;
   const int tiles = gm * gn;
   // split the reduction when the output alone cannot fill the GPU
+  // (chunks of at least 32: small square products such as the eigensolver's
+  // n x n x n ones still spread over the GPU)
   int nsplit = 1;
-  if (tiles < 2 * 152 && K > 4 * GBK) {
-    nsplit = std::min((2 * 152 + tiles - 1) / tiles, std::max(1, K / 256));
+  if (tiles < 2 * 152 && K > 2 * GBK) {
+    nsplit = std::min((2 * 152 + tiles - 1) / tiles, std::max(1, K / 32));
     nsplit = std::max(1, std::min(nsplit, 64));
   }
   int kchunk = (K + nsplit - 1) / nsplit;
