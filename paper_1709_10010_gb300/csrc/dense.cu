@@ -367,15 +367,24 @@ __global__ void k_hermitize(double2* __restrict__ H, int64_t ld, int m0, int m) 
 // Column j survives when S_jj > 0, sqrt(S_jj) >= drop_rel * t0[j] (t0 may be
 // null) and its Cholesky pivot of the unit-diagonal matrix stays above
 // piv_tol.  Output: Tr (k x k, ld = k) whose first kk columns give T Tr with
-// orthonormal columns (other columns zero); *kk = number kept.  W: k x k
-// scratch.
+// orthonormal columns (other columns zero); *kk = number kept.  The lower
+// triangle lives in shared memory (packed by columns) when SMEM, else in the
+// k x k global scratch W.
+template <bool SMEM>
 __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __restrict__ t0,
-                         double drop_rel, double piv_tol, double2* __restrict__ W,
+                         double drop_rel, double piv_tol, double2* __restrict__ Wg,
                          double2* __restrict__ Tr, int* __restrict__ kk) {
+  extern __shared__ __align__(16) unsigned char chsm[];
   __shared__ int keep_s[1024];
   __shared__ int rank_s[1024];
   __shared__ double dinv_s[1024];
   __shared__ int nkeep_s;
+  __shared__ double piv_s;
+  double2* L = SMEM ? (double2*)chsm : Wg;
+  // element (i, j), i >= j, of the lower triangle
+  auto at = [&](int i, int j) -> double2& {
+    return SMEM ? L[(size_t)j * k - (size_t)j * (j - 1) / 2 + (i - j)] : L[(size_t)j * k + i];
+  };
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     double d = S[(size_t)j * k + j].x;
     bool keep = d > 0.0 && (!t0 || sqrt(d) >= drop_rel * t0[j]);
@@ -383,17 +392,16 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
     dinv_s[j] = keep ? 1.0 / sqrt(d) : 0.0;
   }
   __syncthreads();
-  // W = D^-1/2 S D^-1/2
+  // unit-diagonal scaling of the lower triangle
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    int i = t % k, j = t / k;
-    W[t] = scl<double>(S[t], dinv_s[i] * dinv_s[j]);
+    const int i = t % k, j = t / k;
+    if (i >= j) at(i, j) = scl<double>(S[t], dinv_s[i] * dinv_s[j]);
   }
   __syncthreads();
-  // right-looking Cholesky on the kept set (lower triangle of W becomes L)
+  // right-looking Cholesky on the kept set
   for (int j = 0; j < k; ++j) {
-    __shared__ double piv_s;
     if (threadIdx.x == 0) {
-      double piv = W[(size_t)j * k + j].x;
+      const double piv = at(j, j).x;
       if (keep_s[j] && !(piv > piv_tol)) keep_s[j] = 0;
       piv_s = keep_s[j] ? sqrt(piv) : 0.0;
     }
@@ -401,21 +409,18 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
     if (keep_s[j]) {
       const double lj = piv_s;
       for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
-        if (keep_s[i]) W[(size_t)j * k + i] = scl<double>(W[(size_t)j * k + i], 1.0 / lj);
+        if (keep_s[i]) at(i, j) = scl<double>(at(i, j), 1.0 / lj);
       __syncthreads();
-      // A_il -= L_ij conj(L_lj) for kept i >= l > j
-      for (int t = threadIdx.x; t < (k - j - 1) * (k - j - 1); t += blockDim.x) {
-        int i = j + 1 + t % (k - j - 1), l = j + 1 + t / (k - j - 1);
-        if (i >= l && keep_s[i] && keep_s[l]) {
-          double2 lij = W[(size_t)j * k + i], llj = W[(size_t)j * k + l];
-          W[(size_t)l * k + i] = sub<double>(W[(size_t)l * k + i], mulc<double>(lij, llj));
-        }
+      const int r = k - j - 1;
+      for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
+        const int i = j + 1 + t % r, l = j + 1 + t / r;
+        if (i >= l && keep_s[i] && keep_s[l])
+          at(i, l) = sub<double>(at(i, l), mulc<double>(at(i, j), at(l, j)));
       }
-      if (threadIdx.x == 0) W[(size_t)j * k + j] = make_double2(lj, 0.0);
+      if (threadIdx.x == 0) at(j, j) = make_double2(lj, 0.0);
     }
     __syncthreads();
   }
-  // compress kept indices
   if (threadIdx.x == 0) {
     int c = 0;
     for (int j = 0; j < k; ++j) rank_s[j] = keep_s[j] ? c++ : -1;
@@ -424,36 +429,30 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
   }
   __syncthreads();
   const int kp = nkeep_s;
-  // Tr = D^-1/2 L^-H: column c of Tr (c < kp) is D^-1/2 times row c of L^-1
-  // conjugated; solve L^H x = e_c by back substitution over kept indices.
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) Tr[t] = make_double2(0.0, 0.0);
   __syncthreads();
+  // Tr = D^-1/2 L^-H: column rank(j) solves L^H x = e_j by back substitution
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     if (!keep_s[j]) continue;
-    const int c = rank_s[j];
-    // x = L^-H e_c (upper triangular solve): x_i for kept i <= j (in rank order)
-    // Use Tr column c as storage (rows = original indices).
-    double2* x = Tr + (size_t)c * k;
+    double2* x = Tr + (size_t)rank_s[j] * k;
     for (int i = j; i >= 0; --i) {
       if (!keep_s[i]) continue;
       double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
       for (int l = i + 1; l <= j; ++l)
         if (keep_s[l]) {
-          // (L^H)_{il} = conj(L_li)
-          double2 lli = W[(size_t)i * k + l];
+          const double2 lli = at(l, i);  // (L^H)_{il} = conj(L_li)
           v = sub<double>(v, mul<double>(make_double2(lli.x, -lli.y), x[l]));
         }
-      x[i] = scl<double>(v, 1.0 / W[(size_t)i * k + i].x);
+      x[i] = scl<double>(v, 1.0 / at(i, i).x);
     }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < k * kp; t += blockDim.x) {
-    int i = t % k;
+    const int i = t % k;
     Tr[t] = scl<double>(Tr[t], dinv_s[i]);
   }
 }
 
-// ---------------------------------------------------------------- host -----
 // FP32 <-> FP64 copies and the Newton-Schulz step of the host routine.
 __global__ void k_c64_to_c32(const double2* __restrict__ a, int64_t lda, int n, float2* __restrict__ b) {
   int64_t tot = (int64_t)n * n;
@@ -648,9 +647,19 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {
 void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
                    double drop_rel, double2* Tr, int* kk, cudaStream_t st) {
   if (k > 1024) throw Error{PWH_ERR_ARG, "block of more than 1024 new directions"};
-  ensure(w.chol, (size_t)k * k * sizeof(double2));
+  // the packed lower triangle fits the shared memory up to k = 160
+  const size_t tri = (size_t)k * (k + 1) / 2 * sizeof(double2);
+  static std::once_flag attr_once;
+  std::call_once(attr_once, [] {
+    cudaFuncSetAttribute(k_cholqr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  });
   TimedScope ts(s, KF_CHOLQR, st);
-  k_cholqr<<<1, 1024, 0, st>>>(S, k, t0, drop_rel, 1e-12, (double2*)w.chol.p, Tr, kk);
+  if (tri <= 200 * 1024) {
+    k_cholqr<true><<<1, 1024, tri, st>>>(S, k, t0, drop_rel, 1e-12, nullptr, Tr, kk);
+  } else {
+    ensure(w.chol, (size_t)k * k * sizeof(double2));
+    k_cholqr<false><<<1, 1024, 0, st>>>(S, k, t0, drop_rel, 1e-12, (double2*)w.chol.p, Tr, kk);
+  }
   PWH_LAUNCH_CHECK();
 }
 
