@@ -26,10 +26,13 @@
 // a separate permutation.  Twiddles e^{2 pi i t/N} come from a host FP64 table.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
 #include "common.cuh"
+#include "fft_device.cuh"
+#include "fft_spec.cuh"
 
 namespace pwh {
 
@@ -85,89 +88,6 @@ void build_fft_plans(System& s) {
   PWH_CUDA(cudaMemcpy(s.d_tw64, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
   PWH_CUDA(cudaMemcpy(s.d_tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice));
   PWH_CUDA(cudaMemcpy(s.d_perm, perm.data(), perm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
-}
-
-// ---------------------------------------------------------- device FFT ------
-// sin/cos of 2 pi/3, 2 pi/5, 4 pi/5 (mathematical constants)
-#define PWH_S3 0.866025403784438646763723170753
-#define PWH_C5A 0.309016994374947424102293417183
-#define PWH_S5A 0.951056516295153572116439333379
-#define PWH_C5B (-0.809016994374947424102293417183)
-#define PWH_S5B 0.587785252292473129168705954639
-
-// z * (sg * i)
-template <typename T> __device__ __forceinline__ cx<T> rot(cx<T> z, T sg) {
-  return mk<T>(-sg * z.y, sg * z.x);
-}
-
-// In-register DFT of length R with sign sg (+1 inverse, -1 forward).
-template <typename T, int R> __device__ __forceinline__ void dft(cx<T>* a, T sg);
-
-template <typename T> __device__ __forceinline__ void dft2(cx<T>* a) {
-  cx<T> t = a[0];
-  a[0] = add<T>(t, a[1]);
-  a[1] = sub<T>(t, a[1]);
-}
-template <typename T, int R> __device__ __forceinline__ void dft(cx<T>* a, T sg) {
-  if constexpr (R == 2) {
-    dft2<T>(a);
-  } else if constexpr (R == 3) {
-    cx<T> t1 = add<T>(a[1], a[2]);
-    cx<T> t2 = rot<T>(sub<T>(a[1], a[2]), sg * (T)PWH_S3);
-    cx<T> m = sub<T>(a[0], scl<T>(t1, (T)0.5));
-    a[0] = add<T>(a[0], t1);
-    a[1] = add<T>(m, t2);
-    a[2] = sub<T>(m, t2);
-  } else if constexpr (R == 4) {
-    cx<T> s02 = add<T>(a[0], a[2]), d02 = sub<T>(a[0], a[2]);
-    cx<T> s13 = add<T>(a[1], a[3]), d13 = rot<T>(sub<T>(a[1], a[3]), sg);
-    a[0] = add<T>(s02, s13);
-    a[2] = sub<T>(s02, s13);
-    a[1] = add<T>(d02, d13);
-    a[3] = sub<T>(d02, d13);
-  } else if constexpr (R == 5) {
-    cx<T> b1 = add<T>(a[1], a[4]), b2 = add<T>(a[2], a[3]);
-    cx<T> d1 = sub<T>(a[1], a[4]), d2 = sub<T>(a[2], a[3]);
-    cx<T> a0 = a[0];
-    cx<T> r1 = add<T>(a0, add<T>(scl<T>(b1, (T)PWH_C5A), scl<T>(b2, (T)PWH_C5B)));
-    cx<T> r2 = add<T>(a0, add<T>(scl<T>(b1, (T)PWH_C5B), scl<T>(b2, (T)PWH_C5A)));
-    cx<T> i1 = rot<T>(add<T>(scl<T>(d1, (T)PWH_S5A), scl<T>(d2, (T)PWH_S5B)), sg);
-    cx<T> i2 = rot<T>(sub<T>(scl<T>(d1, (T)PWH_S5B), scl<T>(d2, (T)PWH_S5A)), sg);
-    a[0] = add<T>(a0, add<T>(b1, b2));
-    a[1] = add<T>(r1, i1);
-    a[4] = sub<T>(r1, i1);
-    a[2] = add<T>(r2, i2);
-    a[3] = sub<T>(r2, i2);
-  }
-}
-
-// One butterfly of radix R at stage (M, L) of an n-point transform.
-// DIT: twiddle the inputs, then DFT.  DIF (the transpose): DFT, then twiddle.
-template <typename T, int R, bool DIT>
-__device__ __forceinline__ void butterfly(cx<T>* base, int estride, int M, int k1, int twstep,
-                                          const cx<T>* tw, T sg) {
-  cx<T> a[R];
-#pragma unroll
-  for (int q = 0; q < R; ++q) a[q] = base[q * M * estride];
-  if (DIT) {
-#pragma unroll
-    for (int q = 1; q < R; ++q) {
-      cx<T> w = tw[q * k1 * twstep];
-      w.y *= sg;
-      a[q] = mul<T>(a[q], w);
-    }
-  }
-  dft<T, R>(a, sg);
-  if (!DIT) {
-#pragma unroll
-    for (int q = 1; q < R; ++q) {
-      cx<T> w = tw[q * k1 * twstep];
-      w.y *= sg;
-      a[q] = mul<T>(a[q], w);
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < R; ++q) base[q * M * estride] = a[q];
 }
 
 // nfft independent transforms of length pl.n in shared memory: transform f
@@ -398,29 +318,43 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   const double fp = 2.0 * s.n3 * (ncol * 5.0 * s.n2 * l2(s.n2) + s.n2 * 5.0 * s.n1 * l2(s.n1));
   const double bw = cz * (double)s.nsticks * s.n3;                          // one W slice
   const double bv = sizeof(T) * (double)s.n1 * s.n2 * s.n3;                 // V, once per launch
+  // compile-time specialised kernels for cubic boxes of the common sizes
+  // (PWH_FFT_GENERIC=1 in the environment selects the runtime-plan kernels)
+  static const bool use_spec = [] {
+    const char* e = std::getenv("PWH_FFT_GENERIC");
+    return !(e && e[0] == '1');
+  }();
   for (int b0 = 0; b0 < nb; b0 += batch) {
     int bb = std::min(batch, nb - b0);
     dim3 gz((s.nsticks + spb - 1) / spb, bb);
+    const PassArgs pa{psi + (size_t)b0 * ldp, ldp, hpsi + (size_t)b0 * ldh, ldh, W, wband, spb,
+                      zsmem, rows, psmem, bb, V, tw, st};
     {
       TimedScope ts(s, dp ? KF_FFT_ZINV64 : KF_FFT_ZINV32, st, bb * fz, bb * (16.0 * s.npw + bw));
-      k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
-                                         s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
-      PWH_LAUNCH_CHECK();
+      if (!(use_spec && spec_pass<T>(SPEC_ZINV, s, pa))) {
+        k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
+                                           s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
+        PWH_LAUNCH_CHECK();
+      }
     }
     dim3 gp(s.n3, bb);
     {
       TimedScope ts(s, dp ? KF_FFT_PLANE64 : KF_FFT_PLANE32, st, bb * fp, bb * 2.0 * bw + bv);
-      k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
-                                          s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
-      PWH_LAUNCH_CHECK();
+      if (!(use_spec && spec_pass<T>(SPEC_PLANE, s, pa))) {
+        k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
+                                            s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
+        PWH_LAUNCH_CHECK();
+      }
     }
     {
       TimedScope ts(s, dp ? KF_FFT_ZFWD64 : KF_FFT_ZFWD32, st, bb * fz,
                     bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw));
-      k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
-                                         s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
-                                         hpsi + (size_t)b0 * ldh, ldh, spb);
-      PWH_LAUNCH_CHECK();
+      if (!(use_spec && spec_pass<T>(SPEC_ZFWD, s, pa))) {
+        k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
+                                           s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp,
+                                           ldp, hpsi + (size_t)b0 * ldh, ldh, spb);
+        PWH_LAUNCH_CHECK();
+      }
     }
   }
 }

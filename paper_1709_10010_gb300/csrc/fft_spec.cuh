@@ -1,0 +1,35 @@
+// FFT passes specialised at compile time for cubic boxes of common sizes
+// (interface).  The kernels are in fft_spec_impl.cuh, instantiated once per
+// precision in fft_spec32.cu and fft_spec64.cu.
+#pragma once
+#include "common.cuh"
+
+namespace pwh {
+
+// Everything one pass over a band batch needs (the same launch geometry as the
+// generic passes).  psi/hpsi already point at the batch's first band.
+struct PassArgs {
+  const double2* psi;
+  int64_t ldp;
+  double2* hpsi;
+  int64_t ldh;
+  void* W;
+  int64_t wband;
+  int spb;
+  size_t zsmem;
+  int rows;
+  size_t psmem;
+  int bb;
+  const void* V;
+  const void* tw;
+  cudaStream_t st;
+};
+
+enum SpecPass { SPEC_ZINV = 0, SPEC_PLANE = 1, SPEC_ZFWD = 2 };
+
+// Launch the specialised kernel of this pass for the system's box and return
+// true, or return false (nothing launched) when the box has no specialisation:
+// the box is not cubic or its edge is not one of the compiled sizes.
+template <typename T> bool spec_pass(SpecPass pass, System& s, const PassArgs& a);
+
+}  // namespace pwh

@@ -1,0 +1,6 @@
+// FP32 instances of the compile-time specialised FFT passes.
+#include "fft_spec_impl.cuh"
+
+namespace pwh {
+template bool spec_pass<float>(SpecPass, System&, const PassArgs&);
+}  // namespace pwh

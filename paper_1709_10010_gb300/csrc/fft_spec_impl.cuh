@@ -1,0 +1,241 @@
+// FFT passes specialised at compile time for cubic boxes of common sizes.
+// Same algorithm, data layout and tables as the generic passes in fft.cu
+// (k_zinv, k_plane, k_zfwd): the radix plan of every length is a constant, so
+// the stage loops unroll and every index division is by a constant.  The
+// radix order (4s, 2s, 3s, 5s) matches the host plan, hence the host's
+// twiddle and digit-reversal tables serve both.
+#pragma once
+#include <mutex>
+
+#include "common.cuh"
+#include "fft_device.cuh"
+#include "fft_spec.cuh"
+
+namespace pwh {
+
+struct CPlan {
+  int ns;
+  int R[kMaxStages];
+  int M[kMaxStages];
+  int L[kMaxStages];
+};
+
+constexpr CPlan make_cplan(int n) {
+  CPlan p{};
+  int r = n, ns = 0;
+  int rad[kMaxStages] = {};
+  while (r % 4 == 0) { rad[ns++] = 4; r /= 4; }
+  while (r % 2 == 0) { rad[ns++] = 2; r /= 2; }
+  while (r % 3 == 0) { rad[ns++] = 3; r /= 3; }
+  while (r % 5 == 0) { rad[ns++] = 5; r /= 5; }
+  p.ns = ns;
+  int m = 1;
+  for (int s = 0; s < ns; ++s) {
+    p.R[s] = rad[s];
+    p.M[s] = m;
+    m *= rad[s];
+    p.L[s] = m;
+  }
+  return p;
+}
+
+// Stages S.. of nfft transforms of length N (unit element stride, transform f
+// at data + f * fstride), all threads of the block; ends with __syncthreads().
+template <typename T, bool INV, int N, int S>
+__device__ __forceinline__ void fft_stages(cx<T>* data, int nfft, int fstride, const cx<T>* tw) {
+  constexpr CPlan P = make_cplan(N);
+  if constexpr (S < P.ns) {
+    constexpr int s = INV ? S : P.ns - 1 - S;
+    constexpr int R = P.R[s], M = P.M[s], L = P.L[s];
+    constexpr int nbf = N / R, twstep = N / L;
+    const T sg = INV ? (T)1 : (T)-1;
+    const int total = nfft * nbf;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int f = t / nbf, j = t - f * nbf;
+      const int g = j / M, k1 = j - g * M;
+      butterfly<T, R, INV>(data + f * fstride + g * L + k1, 1, M, k1, twstep, tw, sg);
+    }
+    __syncthreads();
+    fft_stages<T, INV, N, S + 1>(data, nfft, fstride, tw);
+  }
+}
+
+template <typename T> __device__ __forceinline__ cx<T> widen_from64(double2 z) {
+  return mk<T>((T)z.x, (T)z.y);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, int64_t ldp,
+                                               const int32_t* __restrict__ stick_off,
+                                               const int32_t* __restrict__ stick_of,
+                                               const int16_t* __restrict__ zpos, int nsticks,
+                                               int tw_off, int perm_off,
+                                               const cx<T>* __restrict__ tw_g,
+                                               const int16_t* __restrict__ perm_g,
+                                               cx<T>* __restrict__ W, int64_t wband, int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = N + 1;
+  cx<T>* buf = (cx<T>*)smem_raw;
+  cx<T>* tw = buf + spb * ld;
+  int16_t* irev = (int16_t*)(tw + N);
+  const int b = blockIdx.y;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    tw[t] = tw_g[tw_off + t];
+    irev[t] = perm_g[perm_off + t];
+  }
+  for (int t = threadIdx.x; t < spb * ld; t += blockDim.x) buf[t] = mk<T>(0, 0);
+  __syncthreads();
+  const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
+  const double2* src = psi + (size_t)b * ldp;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    buf[(stick_of[i] - s0) * ld + irev[zpos[i]]] = widen_from64<T>(src[i]);
+  __syncthreads();
+  fft_stages<T, true, N, 0>(buf, ns, ld, tw);
+  cx<T>* dst = W + (size_t)b * wband;
+  for (int t = threadIdx.x; t < N * spb; t += blockDim.x) {
+    const int z = t / spb, s = t - z * spb;
+    if (s < ns) dst[(size_t)z * nsticks + s0 + s] = buf[s * ld + z];
+  }
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(512) ks_plane(cx<T>* __restrict__ W, int64_t wband, int nsticks,
+                                                int ncols, const int32_t* __restrict__ stick_col,
+                                                const int32_t* __restrict__ stick_y,
+                                                const int32_t* __restrict__ col_x,
+                                                const T* __restrict__ V, int tw_off,
+                                                int perm_off, const cx<T>* __restrict__ tw_g,
+                                                const int16_t* __restrict__ perm_g, int rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = N + 1;
+  cx<T>* C = (cx<T>*)smem_raw;           // ncols x ld
+  cx<T>* Rw = C + (size_t)ncols * ld;    // rows x ld
+  cx<T>* tw = Rw + (size_t)rows * ld;
+  int16_t* irev = (int16_t*)(tw + N);
+  const int z = blockIdx.x, b = blockIdx.y;
+  cx<T>* plane = W + (size_t)b * wband + (size_t)z * nsticks;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    tw[t] = tw_g[tw_off + t];
+    irev[t] = perm_g[perm_off + t];
+  }
+  for (int t = threadIdx.x; t < ncols * ld; t += blockDim.x) C[t] = mk<T>(0, 0);
+  __syncthreads();
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    C[stick_col[s] * ld + irev[stick_y[s]]] = plane[s];
+  __syncthreads();
+  fft_stages<T, true, N, 0>(C, ncols, ld, tw);
+  const T* Vz = V + (size_t)z * N * N;
+  for (int y0 = 0; y0 < N; y0 += rows) {
+    const int nr = min(rows, N - y0);
+    for (int t = threadIdx.x; t < nr * ld; t += blockDim.x) Rw[t] = mk<T>(0, 0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
+      const int r = t / ncols, c = t - r * ncols;
+      Rw[r * ld + irev[col_x[c]]] = C[c * ld + y0 + r];
+    }
+    __syncthreads();
+    fft_stages<T, true, N, 0>(Rw, nr, ld, tw);
+    for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
+      const int r = t / N, x = t - r * N;
+      Rw[r * ld + x] = scl<T>(Rw[r * ld + x], Vz[(size_t)(y0 + r) * N + x]);
+    }
+    __syncthreads();
+    fft_stages<T, false, N, 0>(Rw, nr, ld, tw);
+    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
+      const int r = t / ncols, c = t - r * ncols;
+      C[c * ld + y0 + r] = Rw[r * ld + irev[col_x[c]]];
+    }
+    __syncthreads();
+  }
+  fft_stages<T, false, N, 0>(C, ncols, ld, tw);
+  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
+    plane[s] = C[stick_col[s] * ld + irev[stick_y[s]]];
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int64_t wband,
+                                               const int32_t* __restrict__ stick_off,
+                                               const int32_t* __restrict__ stick_of,
+                                               const int16_t* __restrict__ zpos, int nsticks,
+                                               int tw_off, int perm_off,
+                                               const cx<T>* __restrict__ tw_g,
+                                               const int16_t* __restrict__ perm_g,
+                                               const double* __restrict__ kin,
+                                               const double2* __restrict__ psi, int64_t ldp,
+                                               double2* __restrict__ hpsi, int64_t ldh, int spb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int ld = N + 1;
+  cx<T>* buf = (cx<T>*)smem_raw;
+  cx<T>* tw = buf + spb * ld;
+  int16_t* irev = (int16_t*)(tw + N);
+  const int b = blockIdx.y;
+  const int s0 = blockIdx.x * spb;
+  const int ns = min(spb, nsticks - s0);
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    tw[t] = tw_g[tw_off + t];
+    irev[t] = perm_g[perm_off + t];
+  }
+  const cx<T>* src = W + (size_t)b * wband;
+  for (int t = threadIdx.x; t < N * spb; t += blockDim.x) {
+    const int z = t / spb, s = t - z * spb;
+    if (s < ns) buf[s * ld + z] = src[(size_t)z * nsticks + s0 + s];
+  }
+  __syncthreads();
+  fft_stages<T, false, N, 0>(buf, ns, ld, tw);
+  const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
+  const double2* pb = psi + (size_t)b * ldp;
+  double2* hb = hpsi + (size_t)b * ldh;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const cx<T> v = buf[(stick_of[i] - s0) * ld + irev[zpos[i]]];
+    const double2 p = pb[i];
+    const double k = kin[i];
+    hb[i] = make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
+  }
+}
+
+template <typename T, int N> void spec_launch(SpecPass pass, System& s, const PassArgs& a) {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(ks_zinv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(ks_plane<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(ks_zfwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  const cx<T>* tw = (const cx<T>*)a.tw;
+  cx<T>* W = (cx<T>*)a.W;
+  const dim3 gz((s.nsticks + a.spb - 1) / a.spb, a.bb);
+  switch (pass) {
+    case SPEC_ZINV:
+      ks_zinv<T, N><<<gz, 256, a.zsmem, a.st>>>(a.psi, a.ldp, s.d_stick_off, s.d_stick_of, s.d_zpos,
+                                                 s.nsticks, s.plan[2].tw_off, s.plan[2].perm_off, tw,
+                                                 s.d_perm, W, a.wband, a.spb);
+      break;
+    case SPEC_PLANE:
+      ks_plane<T, N><<<dim3(N, a.bb), 512, a.psmem, a.st>>>(
+          W, a.wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y, s.d_col_x, (const T*)a.V,
+          s.plan[0].tw_off, s.plan[0].perm_off, tw, s.d_perm, a.rows);
+      break;
+    case SPEC_ZFWD:
+      ks_zfwd<T, N><<<gz, 256, a.zsmem, a.st>>>(W, a.wband, s.d_stick_off, s.d_stick_of, s.d_zpos,
+                                                 s.nsticks, s.plan[2].tw_off, s.plan[2].perm_off, tw,
+                                                 s.d_perm, s.d_kin, a.psi, a.ldp, a.hpsi, a.ldh, a.spb);
+      break;
+  }
+  PWH_LAUNCH_CHECK();
+}
+
+template <typename T> bool spec_pass(SpecPass pass, System& s, const PassArgs& a) {
+  if (s.n1 != s.n2 || s.n2 != s.n3) return false;
+  switch (s.n1) {
+#define PWH_SPEC_CASE(n) \
+  case n: spec_launch<T, n>(pass, s, a); return true;
+    PWH_SPEC_CASE(30) PWH_SPEC_CASE(36) PWH_SPEC_CASE(40) PWH_SPEC_CASE(48) PWH_SPEC_CASE(50)
+    PWH_SPEC_CASE(60) PWH_SPEC_CASE(72) PWH_SPEC_CASE(80) PWH_SPEC_CASE(90) PWH_SPEC_CASE(96)
+    PWH_SPEC_CASE(120) PWH_SPEC_CASE(144)
+#undef PWH_SPEC_CASE
+    default: return false;
+  }
+}
+
+}  // namespace pwh
