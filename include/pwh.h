@@ -312,11 +312,17 @@ pwh_status pwh_batch_davidson_solve(int32_t n, pwh_system* const* systems,
  * receives all n eigenvectors sorted by eigenvalue; with warm > 0, Q must hold
  * on entry the eigenvectors of the leading warm x warm block of H (a previous
  * call's output) and the iteration starts in that basis.  Parallel cyclic
- * Jacobi: sweeps in FP32 to FP32 convergence, the accumulated basis made
- * unitary in FP64 (Newton-Schulz), then FP64 sweeps until
- * max|A_ij| <= 1e-13 max|A_ii|.  Asynchronous on the system's stream; n <= 4096. */
+ * Jacobi: sweeps in FP32 to FP32 convergence (in one 16-CTA cluster with the
+ * matrix in distributed shared memory when it fits there, n up to about 440),
+ * then, for precision = PWH_FP64, the accumulated basis made unitary in FP64
+ * (Newton-Schulz), Q^H H Q in FP64 and FP64 sweeps until
+ * max|A_ij| <= 1e-13 max|A_ii|; for PWH_MIXED the FP32 result (one FP32
+ * Newton-Schulz step; eigenvalues to about 1e-7 ||H||), as the reduced-precision
+ * phase of pwh_davidson_solve uses.  Asynchronous on the system's stream;
+ * n <= 4096; another precision gives PWH_ERR_ARG. */
 pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t ldh, int32_t nk,
-                             double* theta, void* C, void* Q, int64_t ldq, int32_t warm);
+                             double* theta, void* C, void* Q, int64_t ldq, int32_t warm,
+                             int32_t precision);
 
 /* Synchronize the system's stream and report device-side failures: returns
  * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave

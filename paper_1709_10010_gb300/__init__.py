@@ -80,7 +80,7 @@ SIGNATURES = {
     "pwh_sync": (_c_i32, [_c_p]),
     "pwh_batch_davidson_solve": (_c_i32, [_c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i32]),
     "pwh_subspace_eigh": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_i32, _c_p, _c_p, _c_p, _c_i64,
-                                   _c_i32]),
+                                   _c_i32, _c_i32]),
     "pwh_mlp_num_params": (_c_i32, [ctypes.POINTER(_c_i32)]),
     "pwh_mlp_forward": (_c_i32, [_c_p, _c_p, _c_p, _c_i64, _c_p]),
     "pwh_mlp_loss_grad": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p, _c_i64, _c_d, _c_p, _c_p]),
@@ -254,13 +254,14 @@ class System:
                                        "flops": float(arr[i].flops), "bytes": float(arr[i].bytes)}
                 for i in range(min(n.value, 32))}
 
-    def subspace_eigh(self, H, nk, Q=None, warm=0):
+    def subspace_eigh(self, H, nk, Q=None, warm=0, precision="fp64"):
         """Lowest nk eigenpairs of a Hermitian matrix given as an (n, n) CUDA
         complex128 tensor Ht with Ht[j, i] = H[i, j] (column-major H).  Returns
         (theta, C) CUDA tensors, C of shape (nk, n) holding eigenvectors as
         rows.  Q: optional (n_max, n_max) tensor (row j = eigenvector j) that
         receives all n eigenvectors; with warm > 0 it must hold on entry the
-        eigenvectors of the leading warm x warm block."""
+        eigenvectors of the leading warm x warm block.  precision: "fp64"
+        (FP64-accurate) or "mixed" (the FP32 result)."""
         torch = _torch()
         n = int(H.shape[0])
         Hc = H.contiguous()
@@ -270,7 +271,8 @@ class System:
         ldq = int(Q.shape[1]) if Q is not None else 0
         _check(lib().pwh_subspace_eigh(self._h, n, ctypes.c_void_p(Hc.data_ptr()), n, int(nk),
                                        ctypes.c_void_p(theta.data_ptr()),
-                                       ctypes.c_void_p(C.data_ptr()), qp, ldq, int(warm)))
+                                       ctypes.c_void_p(C.data_ptr()), qp, ldq, int(warm),
+                                       PRECISIONS[precision]))
         return theta, C
 
     def sync(self):

@@ -98,7 +98,7 @@ void free_davidson_ws(DavWs* w);
 // Optional per-family kernel timing with CUDA events on the system's stream.
 enum KernelFamily {
   KF_FFT_ZINV64 = 0, KF_FFT_PLANE64, KF_FFT_ZFWD64, KF_FFT_ZINV32, KF_FFT_PLANE32, KF_FFT_ZFWD32,
-  KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_COUNT
+  KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_JACOBI32, KF_COUNT
 };
 extern const char* const kKernelFamilyName[KF_COUNT];
 

@@ -477,23 +477,37 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // the leading hs_valid x hs_valid block was diagonalised last time: start there
     const int warm = hs_valid;
     hs_valid = m;
-    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm);
+    // FP64 eigenpairs in the FP64 phase; FP32 ones (from a subspace matrix
+    // that is itself FP32-accurate) in the reduced-precision phase
+    const bool polish = phase_prec == PWH_FP64;
+    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
     PWH_LAUNCH_CHECK();
     PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (s.timer.on)
+    if (s.timer.on) {
       PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4100, jacobi_sweeps_word(w.dense), sizeof(int),
                                cudaMemcpyDeviceToHost, st));
+      PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4101, jacobi32_sweeps_word(w.dense), sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+    }
     PWH_CUDA(cudaStreamSynchronize(st));
     check_err(s);
     if (s.timer.on) {
       // FP64 work of the eigensolve: polish sweeps x (m-1) rounds x 20 m^2
       // operations, plus the Newton-Schulz step and Q^H H Q (4 complex GEMMs)
       const double sw = w.h_idx[4100];
-      s.timer.flops[KF_JACOBI] += sw * (m - 1) * 20.0 * (double)m * m + 32.0 * (double)m * m * m;
-      s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 3.0 * 16.0 * (double)m * m;
+      if (polish) {
+        s.timer.flops[KF_JACOBI] += sw * (m - 1) * 20.0 * (double)m * m + 32.0 * (double)m * m * m;
+        s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 3.0 * 16.0 * (double)m * m;
+      }
+      // FP32 stage: per round 20 m^2 operations on A (2 x 2 blocks, both
+      // triangles) and 10 m^2 on Q; plus the warm-start transform and the
+      // Newton-Schulz step (complex GEMMs of 8 m^3 each)
+      const double sw32 = w.h_idx[4101];
+      const int ngemm32 = (warm ? 3 : 0) + (polish ? 0 : 3);
+      s.timer.flops[KF_JACOBI32] += sw32 * (m - 1) * 30.0 * (double)m * m + ngemm32 * 8.0 * (double)m * m * m;
     }
     s.timer.resolve();
     S.iters = it;

@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "gemm.cuh"
+#include "jacobi_rot.cuh"
 
 namespace pwh {
 
@@ -135,39 +136,14 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
       for (int k = threadIdx.x; k < P; k += blockDim.x) {
         int p = rr_player(k, r, np), q = rr_player(np - 1 - k, r, np);
         if (p > q) { int t = p; p = q; q = t; }
-        T c = 1, sr = 0, si = 0;
-        if (q < n) {
-          const cx<T> apq = A[(size_t)q * n + p];
-          // |A_pq| scaled against underflow: an inaccurate modulus would make
-          // the rotation non-unitary when zeta is O(1) (degenerate diagonal)
-          const T mx = fmax(fabs(apq.x), fabs(apq.y));
-          T g = 0;
-          if (mx > (T)0) {
-            const T ux = apq.x / mx, uy = apq.y / mx;
-            g = mx * sqrt(ux * ux + uy * uy);
-          }
-          const T app = A[(size_t)p * n + p].x, aqq = A[(size_t)q * n + q].x;
-          // an A_pq too small to change either diagonal entry is dropped
-          // without rotating (the 2 x 2 update below writes it as zero)
-          const bool negligible = (fabs(app) + (T)100 * g == fabs(app)) &&
-                                  (fabs(aqq) + (T)100 * g == fabs(aqq));
-          if (g > (T)0 && !negligible) {
-            const T zeta = (aqq - app) / (2 * g);
-            // tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
-            // (1/(2 zeta) once zeta^2 would overflow)
-            const T t = fabs(zeta) > (T)1e9 ? (T)0.5 / zeta
-                                            : (zeta >= 0 ? (T)1 : (T)-1) /
-                                                  (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-            c = (T)1 / sqrt((T)1 + t * t);
-            const T sn = t * c;
-            sr = sn * apq.x / g;
-            si = sn * apq.y / g;
-          }
-        }
+        T c = 1;
+        cx<T> sv = mk<T>(0, 0);
+        if (q < n)
+          jacobi_rotation<T>(A[(size_t)q * n + p], A[(size_t)p * n + p].x, A[(size_t)q * n + q].x, c, sv);
         pp[k] = p;
         pq[k] = q;
         crot[k] = c;
-        srot[k] = mk<T>(sr, si);
+        srot[k] = sv;
       }
       __syncthreads();
       const cx<T>* Qc = a.Q[cur];
@@ -188,18 +164,8 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
           const cx<T> a01 = vl ? A[(size_t)ql * n + pk] : z;
           const cx<T> a10 = vk ? A[(size_t)pl * n + qk] : z;
           const cx<T> a11 = (vk && vl) ? A[(size_t)ql * n + qk] : z;
-          const cx<T> msl = mk<T>(-sl.x, sl.y);  // -conj(s_l) = J[q][p]
-          // (A J) on the block: columns (pl, ql)
-          const cx<T> x00 = add<T>(scl<T>(a00, cl), mul<T>(a01, msl));
-          const cx<T> x01 = add<T>(mul<T>(a00, sl), scl<T>(a01, cl));
-          const cx<T> x10 = add<T>(scl<T>(a10, cl), mul<T>(a11, msl));
-          const cx<T> x11 = add<T>(mul<T>(a10, sl), scl<T>(a11, cl));
-          // J^H (A J): row pk = c_k x0 - s_k x1, row qk = conj(s_k) x0 + c_k x1
-          const cx<T> csk = mk<T>(sk.x, -sk.y);
-          cx<T> y00 = sub<T>(scl<T>(x00, ck), mul<T>(sk, x10));
-          cx<T> y01 = sub<T>(scl<T>(x01, ck), mul<T>(sk, x11));
-          cx<T> y10 = add<T>(mul<T>(csk, x00), scl<T>(x10, ck));
-          cx<T> y11 = add<T>(mul<T>(csk, x01), scl<T>(x11, ck));
+          cx<T> y00, y01, y10, y11;
+          jacobi_block<T>(a00, a01, a10, a11, ck, sk, cl, sl, y00, y01, y10, y11);
           if (k == l) {
             // rotated 2 x 2 diagonal block: real diagonal, zeroed pair element
             An[(size_t)pk * n + pk] = mk<T>(y00.x, 0);
@@ -291,32 +257,6 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
   }
 }
 
-// Sort the diagonal ascending and gather the lowest nk eigenpairs:
-// theta[k], C[:, k] (n x nk, ld = n).  Also keeps the full eigenvector matrix
-// in Qkeep (ld = ldk) for a warm start of the next call.  One block.
-__global__ void k_jacobi_select(const double2* __restrict__ A0, const double2* __restrict__ A1,
-                                const double2* __restrict__ Q0, const double2* __restrict__ Q1,
-                                const int* __restrict__ buf, int n, int nk,
-                                double* __restrict__ theta, double2* __restrict__ C,
-                                double2* __restrict__ Qkeep, int64_t ldk) {
-  const double2* A = buf[0] ? A1 : A0;
-  const double2* Q = buf[0] ? Q1 : Q0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double di = A[(size_t)i * n + i].x;
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      double dj = A[(size_t)j * n + j].x;
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    if (rank < nk) {
-      theta[rank] = di;
-      for (int r = 0; r < n; ++r) C[(size_t)rank * n + r] = Q[(size_t)i * n + r];
-    }
-    if (Qkeep)
-      for (int r = 0; r < n; ++r) Qkeep[(size_t)rank * ldk + r] = Q[(size_t)i * n + r];
-  }
-}
-
 // dst (FP64) = the FP32 buffer (b0 or b1) holding the result.
 __global__ void k_select_buf(const float2* __restrict__ b0, const float2* __restrict__ b1,
                              const int* __restrict__ buf, int64_t n2, double2* __restrict__ dst) {
@@ -324,6 +264,74 @@ __global__ void k_select_buf(const float2* __restrict__ b0, const float2* __rest
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2;
        t += (int64_t)gridDim.x * blockDim.x)
     dst[t] = make_double2((double)b[t].x, (double)b[t].y);
+}
+
+// Lowest nk eigenpairs from a diagonal d (n) and eigenvector matrix Q (n x n,
+// ld n): theta[rank], C[:, rank] for rank < nk, and every column into Qkeep
+// (ld ldk) in ascending order.  Ties go to the lower index.  Each block ranks
+// all n values itself (n^2 comparisons) and copies a slice of the columns.
+__global__ void k_select_eig(const double* __restrict__ d, const double2* __restrict__ Q, int n,
+                             int nk, double* __restrict__ theta, double2* __restrict__ C,
+                             double2* __restrict__ Qkeep, int64_t ldk) {
+  extern __shared__ int rank_of[];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double di = d[i];
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double dj = d[j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    rank_of[i] = rank;
+    if (blockIdx.x == 0 && rank < nk) theta[rank] = di;
+  }
+  __syncthreads();
+  const int64_t tot = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / n), r = (int)(t - (int64_t)i * n);
+    const int rank = rank_of[i];
+    const double2 v = Q[t];
+    if (rank < nk) C[(size_t)rank * n + r] = v;
+    if (Qkeep) Qkeep[(size_t)rank * ldk + r] = v;
+  }
+}
+
+// d[i] = Re(Q[:, i]^H G[:, i]) (G = H Q): Rayleigh quotients, one block per column.
+__global__ void k_rayleigh(const double2* __restrict__ Q, const double2* __restrict__ G, int n,
+                           double* __restrict__ d) {
+  __shared__ double part[32];
+  const int i = blockIdx.x;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const double2 q = Q[(size_t)i * n + r], g = G[(size_t)i * n + r];
+    acc += q.x * g.x + q.y * g.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+    d[i] = t;
+  }
+}
+
+// d = diagonal of the n x n matrix held in a0 or a1 (buf[0]), either precision.
+template <typename T>
+__global__ void k_diag_of(const cx<T>* __restrict__ a0, const cx<T>* __restrict__ a1,
+                          const int* __restrict__ buf, int n, double* __restrict__ d) {
+  const cx<T>* a = (buf && buf[0]) ? a1 : a0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    d[i] = (double)a[(size_t)i * n + i].x;
+}
+
+// dst = the FP64 buffer (b0 or b1) holding the result.
+__global__ void k_select_buf64(const double2* __restrict__ b0, const double2* __restrict__ b1,
+                               const int* __restrict__ buf, int64_t n2, double2* __restrict__ dst) {
+  const double2* b = buf[0] ? b1 : b0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2;
+       t += (int64_t)gridDim.x * blockDim.x)
+    dst[t] = b[t];
 }
 
 // Q0 = blockdiag(Qprev[0:m0, 0:m0], I) (n x n, ld n).
@@ -555,13 +563,17 @@ static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0
   note_launch();
 }
 
+static size_t jacobi_ws_bytes(size_t nn, int n) {
+  // FP64: A0, A1, Q0, Q1, G;  FP32: a0, a1, q0, q1;  diagonal d
+  return 5 * nn * sizeof(double2) + 4 * nn * sizeof(float2) + (size_t)n * sizeof(double) + 512;
+}
+
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
-                 int warm_m0) {
+                 int warm_m0, bool polish) {
   if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
   const size_t nn = (size_t)n * n;
-  // FP64: A0, A1, Q0, Q1, G;  FP32: a0, a1, q0, q1
-  ensure(w.jac, 5 * nn * sizeof(double2) + 4 * nn * sizeof(float2) + 256);
+  ensure(w.jac, jacobi_ws_bytes(nn, n));
   double2* A0 = (double2*)w.jac.p;
   double2* A1 = A0 + nn;
   double2* Q0 = A1 + nn;
@@ -571,43 +583,72 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   float2* a1 = a0 + nn;
   float2* q0 = a1 + nn;
   float2* q1 = q0 + nn;
+  double* dg = (double*)(q1 + nn);
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
   unsigned* ctl = (unsigned*)w.ctl;
   PWH_CUDA(cudaMemsetAsync(ctl, 0, 64, st));
   int* out_buf = (int*)(ctl + 8);  // FP64 stage: result buffer index, sweeps
+  int* ob32 = (int*)(ctl + 10);    // FP32 stage: result buffer index, sweeps
   const int gq = (int)std::min<int64_t>(1024, ((int64_t)nn + 255) / 256);
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
-  TimedScope ts(s, KF_JACOBI, st);
-  // ---- stage 1 (FP32): rotate the start to near-diagonal
   const bool warm = warm_m0 > 0 && Qkeep;
-  if (warm) {
-    // start in the previous eigenbasis: A = Qw^H H Qw (FP32 arithmetic suffices)
-    k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q1);
-    PWH_LAUNCH_CHECK();
-    cgemm_f32(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
-    cgemm_f32(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
-    k_c64_to_c32<<<gq, 256, 0, st>>>(A1, n, n, a0);
-  } else {
-    k_c64_to_c32<<<gq, 256, 0, st>>>(H, ldh, n, a0);
-  }
-  PWH_LAUNCH_CHECK();
-  k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity, reused below
-  PWH_LAUNCH_CHECK();
-  k_c64_to_c32<<<gq, 256, 0, st>>>(Q0, n, n, q0);
-  PWH_LAUNCH_CHECK();
-  int* ob32 = (int*)(ctl + 10);  // FP32 stage: result buffer index, sweeps
-  // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
-  // convergence) usually finishes
-  launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 4e-7, 30, ob32, st);
-  // the FP32 eigenvectors sit in q0 or q1 (ob32[0]): widen them to FP64
-  k_select_buf<<<gq, 256, 0, st>>>(q0, q1, ob32, (int64_t)nn, Q0);
-  PWH_LAUNCH_CHECK();
-  // ---- stage 2 (FP64): exact unitary basis, A = Q^H H Q
   double2* Q = Q0;
-  if (warm) {
-    cgemm_f32(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
-    Q = A0;
+  {
+    TimedScope ts(s, KF_JACOBI32, st);
+    // ---- stage 1 (FP32): rotate the start to near-diagonal
+    const double2* start = H;
+    int64_t ld_start = ldh;
+    if (warm) {
+      // start in the previous eigenbasis: A = Qw^H H Qw (FP32 arithmetic suffices)
+      k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q1);
+      PWH_LAUNCH_CHECK();
+      cgemm_f32(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
+      cgemm_f32(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
+      start = A1;
+      ld_start = n;
+    }
+    // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
+    // convergence) usually finishes.  The whole matrix in one cluster's shared
+    // memory when it fits, else through global memory.
+    if (!jacobi32_cluster(s, start, ld_start, n, 4e-7, 30, Q0, n, dg, ob32, st)) {
+      k_c64_to_c32<<<gq, 256, 0, st>>>(start, ld_start, n, a0);
+      PWH_LAUNCH_CHECK();
+      k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity
+      PWH_LAUNCH_CHECK();
+      k_c64_to_c32<<<gq, 256, 0, st>>>(Q0, n, n, q0);
+      PWH_LAUNCH_CHECK();
+      launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 4e-7, 30, ob32, st);
+      // the FP32 eigenvectors sit in q0 or q1 (ob32[0]): widen them to FP64
+      k_select_buf<<<gq, 256, 0, st>>>(q0, q1, ob32, (int64_t)nn, Q0);
+      PWH_LAUNCH_CHECK();
+      k_diag_of<float><<<(n + 255) / 256, 256, 0, st>>>(a0, a1, ob32, n, dg);
+      PWH_LAUNCH_CHECK();
+    }
+    if (warm) {
+      cgemm_f32(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
+      Q = A0;
+    }
+    if (!polish) {
+      // reduced-precision result: one Newton-Schulz step towards the nearest
+      // unitary, Q (3I - Q^H Q)/2 in FP32 arithmetic; eigenvalues as Rayleigh
+      // quotients q^H H q of those vectors (the FP32 diagonal drifts by the
+      // accumulated non-unitarity of FP32 rotations, about n sweeps x 1e-7)
+      double2* Qo = (Q == Q0) ? A0 : Q0;
+      cgemm_f32(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
+      k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
+      PWH_LAUNCH_CHECK();
+      cgemm_f32(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
+      cgemm_f32(s, false, n, n, n, one, H, ldh, Qo, n, zero, G, n, st);
+      k_rayleigh<<<n, 128, 0, st>>>(Qo, G, n, dg);
+      PWH_LAUNCH_CHECK();
+      const int sb = (int)std::min<int64_t>(64, ((int64_t)nn + 1023) / 1024);
+      k_select_eig<<<sb, 1024, n * sizeof(int), st>>>(dg, Qo, n, nk, theta, C, Qkeep, ldk);
+      PWH_LAUNCH_CHECK();
+      return;
+    }
   }
+  TimedScope ts(s, KF_JACOBI, st);
+  // ---- stage 2 (FP64): exact unitary basis, A = Q^H H Q
   // Newton-Schulz to the nearest unitary: Q <- Q (3I - Q^H Q)/2, once in FP32
   // arithmetic, once in FP64
   double2* Qo = (Q == Q0) ? A0 : Q0;
@@ -625,13 +666,18 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   PWH_CUDA(cudaMemcpyAsync(Q0, Q1, nn * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   // ---- stage 3 (FP64): polish sweeps on the nearly diagonal matrix
   launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 12, out_buf, st);
-  k_jacobi_select<<<1, 256, 0, st>>>(A0, A1, Q0, Q1, out_buf, n, nk, theta, C, Qkeep, ldk);
+  k_diag_of<double><<<(n + 255) / 256, 256, 0, st>>>(A0, A1, out_buf, n, dg);
+  PWH_LAUNCH_CHECK();
+  k_select_buf64<<<gq, 256, 0, st>>>(Q0, Q1, out_buf, (int64_t)nn, G);
+  PWH_LAUNCH_CHECK();
+  const int sb = (int)std::min<int64_t>(64, ((int64_t)nn + 1023) / 1024);
+  k_select_eig<<<sb, 1024, n * sizeof(int), st>>>(dg, G, n, nk, theta, C, Qkeep, ldk);
   PWH_LAUNCH_CHECK();
 }
 
 void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   const size_t nn = (size_t)nmax * nmax;
-  ensure(w.jac, 5 * nn * sizeof(double2) + 4 * nn * sizeof(float2) + 256);
+  ensure(w.jac, jacobi_ws_bytes(nn, nmax));
   ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
 }
@@ -667,7 +713,7 @@ void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double*
 
 extern "C" pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t ldh,
                                         int32_t nk, double* theta, void* C, void* Q, int64_t ldq,
-                                        int32_t warm) {
+                                        int32_t warm, int32_t precision) {
   using namespace pwh;
   return guarded([&] {
     PWH_CHECK_ARG(sys && H && theta && C, "null argument");
@@ -676,10 +722,11 @@ extern "C" pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* 
     PWH_CHECK_ARG(ldh >= n, "ldh < n");
     PWH_CHECK_ARG(!Q || ldq >= n, "ldq < n");
     PWH_CHECK_ARG(warm >= 0 && warm <= n && (warm == 0 || Q), "warm needs Q and 0 <= warm <= n");
+    PWH_CHECK_ARG(precision == PWH_FP64 || precision == PWH_MIXED, "precision must be FP64 or MIXED");
     System& s = sys->s;
     static thread_local DenseWs* ws = nullptr;
     if (!ws) ws = new DenseWs();
     jacobi_eigh(s, *ws, (const double2*)H, ldh, n, nk, theta, (double2*)C, s.stream, (double2*)Q,
-                ldq, warm);
+                ldq, warm, precision == PWH_FP64);
   });
 }

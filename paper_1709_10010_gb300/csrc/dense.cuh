@@ -21,12 +21,25 @@ constexpr int kJacobiMaxN = 4096;
 // (optional, ld = ldk) receives all n eigenvectors sorted by eigenvalue; with
 // warm_m0 > 0 it must hold the previous call's eigenvectors of the leading
 // warm_m0 x warm_m0 block of H, and the iteration starts in that basis.
+// polish: FP64 result (FP32 Jacobi, then the FP64 unitary basis, Q^H H Q and
+// FP64 sweeps); otherwise the FP32 result (eigenvalues to about FP32 rounding
+// of ||H||, eigenvectors orthonormal to about FP32 rounding).
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep = nullptr,
-                 int64_t ldk = 0, int warm_m0 = 0);
+                 int64_t ldk = 0, int warm_m0 = 0, bool polish = true);
 
-// Device word holding the number of sweeps of the last jacobi_eigh.
+// FP32 stage of jacobi_eigh in one 16-CTA thread-block cluster with the matrix
+// in distributed shared memory (jacobi_dsm.cu): sweeps of the n x n Hermitian
+// A (FP64, ld lda) until max|A_ij| <= tol max|A_ii|; Q (ld ldq) receives the
+// eigenvectors (FP64), diag the final diagonal, info[1] the sweeps.  Returns
+// false, launching nothing, when n is outside its range or the cluster cannot
+// be resident.
+bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double tol, int max_sweeps,
+                      double2* Q, int64_t ldq, double* diag, int* info, cudaStream_t st);
+
+// Device words holding the number of FP64 / FP32 sweeps of the last jacobi_eigh.
 inline int* jacobi_sweeps_word(DenseWs& w) { return (int*)w.ctl + 9; }
+inline int* jacobi32_sweeps_word(DenseWs& w) { return (int*)w.ctl + 11; }
 
 // Grow the workspaces for subspaces up to nmax and Cholesky blocks up to kmax
 // (so that no allocation, hence no device-wide synchronisation, happens later).
