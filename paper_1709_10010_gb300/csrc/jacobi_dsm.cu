@@ -15,14 +15,19 @@
 //    players crossing to a neighbouring CTA move data (at most two columns of
 //    A and two of Q per CTA and round, written into the neighbour's inbox
 //    through distributed shared memory), the rest move by table update.
-//  * a round: each CTA computes the rotations of its own pairs and publishes
-//    them, cluster barrier, each CTA reads all np/2 rotations, then applies
-//    J^H A J to its own columns (2 x 2 blocks: row pair x own column pair, in
-//    place) and Q J to its own Q columns; the crossing columns go to the
-//    inboxes, cluster barrier, inbox columns land in the freed buffers.
-//  * after each sweep every CTA publishes max |A_ij| (i != j) and max |A_ii|
-//    of its columns; all CTAs take the same decision from the same numbers,
-//    so the control flow stays uniform and every barrier is met.
+//  * the diagonal is replicated in every CTA: all CTAs apply every round's
+//    2 x 2 diagonal updates from the published (c, s, A_pq) identically.
+//  * a round, between two cluster barriers: land the arrivals of the last
+//    step, read all np/2 rotations of the round (published by their owners
+//    before the barrier), apply J^H A J to the own columns (2 x 2 blocks: row
+//    pair x own column pair, in place) and Q J to the own Q columns, update
+//    the diagonal, send the departing columns, then compute and publish the
+//    next round's rotations of the own pairs (A_pq from whichever of the two
+//    columns stays here).  Rotation tables and inboxes alternate between two
+//    copies by round parity, so one barrier a round suffices.
+//  * at the end of each sweep every CTA publishes max |A_ij| (i != j) of its
+//    columns and max |A_ii|; all CTAs take the same decision from the same
+//    numbers, so the control flow stays uniform and every barrier is met.
 //
 // No software spin anywhere: only the hardware cluster barrier.
 #include <cooperative_groups.h>
@@ -53,22 +58,33 @@ struct JdsmArgs {
   float tol;
 };
 
-// shared-memory layout of one CTA (element counts), in this order:
-//   float2 colA[nbuf n], colQ[nbuf n], alls[P], rs[PP]
-//   float  allc[P], rc[PP], red[2 + 64]
-//   int    allp[P], allq[P], rp[PP], rq[PP], rbp[PP], rbq[PP],
-//          tab[4][2 PP] (player/buffer, current and next), misc[16]
-// with nbuf = 2 PP + 2 (two inbox buffers at the end).
+// shared-memory layout of one CTA, in this order:
+//   float2 colA[nbuf n], colQ[nbuf n]      column buffers, nbuf = 2 PP + 4 (the
+//                                          last four: inboxes [parity][side])
+//   float4 rot[2][PP][2]                   published rotations of the own pairs,
+//                                          by round parity: (s, c, p | q << 16),
+//                                          (A_pq, -, -)
+//   float4 allr[P][2]                      the round's rotations of every pair
+//   float  dg[np]                          the diagonal, replicated in every CTA
+//   float  red[66]                         [0] off, [1] dmax (published), partials
+//   int    bufof[2 PP], nbufof[2 PP]       buffer of each own slot (current, next)
+//   int    own[4][PP]                      the round's p, q, buffer(p), buffer(q)
 __host__ __device__ inline size_t jdsm_smem_bytes(int n, int P, int PP) {
-  const size_t nbuf = 2 * (size_t)PP + 2;
-  return (2 * nbuf * n + P + PP) * sizeof(float2) + (size_t)(P + PP + 66) * sizeof(float) +
-         (size_t)(2 * P + 4 * PP + 8 * PP + 16) * sizeof(int);
+  const size_t nbuf = 2 * (size_t)PP + 4;
+  const int np = 2 * P;
+  return 2 * nbuf * n * sizeof(float2) + (4 * (size_t)PP + 2 * (size_t)P) * sizeof(float4) +
+         (size_t)(np + 66) * sizeof(float) + (size_t)(8 * PP) * sizeof(int);
 }
 
-// position -> pair, and the pair's owning CTA
+// position -> pair; previous and next position of the round-robin (every
+// position but 0 steps forward, np-1 wraps to 1)
 __device__ __forceinline__ int jd_pair(int x, int np, int P) { return x < P ? x : np - 1 - x; }
 __device__ __forceinline__ int jd_prev(int x, int np) { return x == 0 ? 0 : (x == 1 ? np - 1 : x - 1); }
 __device__ __forceinline__ int jd_next(int x, int np) { return x == 0 ? 0 : (x == np - 1 ? 1 : x + 1); }
+// index standing at position x in round r of a sweep (position x holds x at r = 0)
+__device__ __forceinline__ int jd_player(int x, int r, int np) {
+  return x == 0 ? 0 : 1 + (x - 1 - r + (np - 1)) % (np - 1);
+}
 
 __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -78,31 +94,23 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
   const int k0 = me * PP;
   const int ns = max(0, min(PP, P - k0));  // own pairs
   const int nslot = 2 * ns;
-  const int nbuf = 2 * PP + 2;
-  const int ibuf0 = nbuf - 2;  // inbox buffers ibuf0 (positions < P), ibuf0 + 1 (>= P)
+  const int nbuf = 2 * PP + 4;
+  const int ibuf0 = 2 * PP;  // inbox buffer ibuf0 + 2 parity + side
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   float2* colA = (float2*)dsm;
   float2* colQ = colA + (size_t)nbuf * n;
-  float2* alls = colQ + (size_t)nbuf * n;
-  float2* rs = alls + P;
-  float* allc = (float*)(rs + PP);
-  float* rc = allc + P;
-  float* red = rc + PP;  // [0] off, [1] dmax (published), [2..66) warp partials
-  int* allp = (int*)(red + 66);
-  int* allq = allp + P;
-  int* rp = allq + P;
-  int* rq = rp + PP;
-  int* rbp = rq + PP;
-  int* rbq = rbp + PP;
-  int* tab = rbq + PP;        // 4 arrays of 2 PP: player/buffer x current/next
-  int* misc = tab + 8 * PP;   // [0..1] inbox players, [2..15] schedule
-  int* player = tab;
-  int* bufof = tab + 2 * PP;
-  int* nplayer = tab + 4 * PP;
-  int* nbufof = tab + 6 * PP;
+  float4* rot = (float4*)(colQ + (size_t)nbuf * n);
+  float4* allr = rot + 4 * PP;
+  float* dg = (float*)(allr + 2 * P);
+  float* red = dg + np;
+  int* bufof = (int*)(red + 66);
+  int* nbufof = bufof + 2 * PP;
+  int* own = nbufof + 2 * PP;  // own[0..PP) p, [PP..2PP) q, then buffers of p and q
 
-  // Fixed per CTA: own slot s stands at position pos(s); the slots whose
-  // player leaves this CTA each round, and the slots that receive from an
-  // inbox.  At most two of each (one per side).
+  // Fixed per CTA: own slot s stands at position pos(s) (pair k0 + s/2, first
+  // or second place); the slots whose index leaves for a neighbouring CTA at
+  // each step and the slots filled from an inbox.  At most one of each per
+  // side, and (for at least two pairs per CTA) never both places of a pair.
   auto pos_of = [&](int s) { const int k = k0 + (s >> 1); return (s & 1) ? np - 1 - k : k; };
   auto slot_of = [&](int x) { const int k = jd_pair(x, np, P); return 2 * (k - k0) + (x >= P ? 1 : 0); };
   int n_out = 0, out_slot[2] = {-1, -1}, out_cta[2] = {0, 0}, out_box[2] = {0, 0};
@@ -125,11 +133,57 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
     }
   }
 
-  // ---- load: position x starts with player x; Q starts as the identity
-  for (int s = threadIdx.x; s < nslot; s += blockDim.x) {
-    player[s] = pos_of(s);
-    bufof[s] = s;
-  }
+  // Rotations of round r for the own pairs into rot[par]: A_pq from whichever
+  // of the two columns is here (an arriving column is still in an inbox when
+  // pending), the diagonal from the replicated copy.
+  auto publish = [&](int r, int par, bool pending) {
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+      int p = jd_player(pos_of(2 * j), r, np), q = jd_player(pos_of(2 * j + 1), r, np);
+      int bp = bufof[2 * j], bq = bufof[2 * j + 1];
+      bool hp = true, hq = true;
+      if (pending) {
+        for (int i = 0; i < n_in; ++i) {
+          if (in_slot[i] == 2 * j) hp = false;
+          if (in_slot[i] == 2 * j + 1) hq = false;
+        }
+      }
+      if (p > q) {
+        int t = p; p = q; q = t;
+        t = bp; bp = bq; bq = t;
+        const bool h = hp; hp = hq; hq = h;
+      }
+      float c = 1.f;
+      float2 sv = make_float2(0.f, 0.f), apq = make_float2(0.f, 0.f);
+      if (q < n) {
+        if (hq) {
+          apq = colA[(size_t)bq * n + p];
+        } else {
+          const float2 v = colA[(size_t)bp * n + q];
+          apq = make_float2(v.x, -v.y);
+        }
+        jacobi_rotation<float>(apq, dg[p], dg[q], c, sv);
+      }
+      rot[(par * PP + j) * 2] = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 16)));
+      rot[(par * PP + j) * 2 + 1] = make_float4(apq.x, apq.y, 0.f, 0.f);
+    }
+  };
+  // Arrivals of the last step: inbox[par] into the buffers the tables gave them.
+  auto land = [&](int r, int par) {
+    for (int i = 0; i < n_in; ++i) {
+      const int b = bufof[in_slot[i]];
+      const size_t src = (size_t)(ibuf0 + 2 * par + in_box[i]) * n;
+      if (jd_player(pos_of(in_slot[i]), r, np) < n) {
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+          colA[(size_t)b * n + e] = colA[src + e];
+          colQ[(size_t)b * n + e] = colQ[src + e];
+        }
+      }
+    }
+  };
+
+  // ---- load: position x starts with index x; Q starts as the identity
+  for (int s = threadIdx.x; s < nslot; s += blockDim.x) bufof[s] = s;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) dg[i] = i < n ? (float)a.A[(size_t)i * a.lda + i].x : 0.f;
   for (int t = threadIdx.x; t < nslot * n; t += blockDim.x) {
     const int s = t / n, i = t - s * n;
     const int pl = pos_of(s);
@@ -140,190 +194,233 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
     }
   }
   __syncthreads();
+  publish(0, 0, false);
+  cluster.sync();
 
-  int sweep = 0;
-  bool done = false;
-  while (!done && sweep < a.max_sweeps) {
-    for (int r = 0; r < np - 1; ++r) {
-      // (a) rotations of the own pairs, published in rp/rq/rc/rs
+  // warp tasks of the update: A in chunks of 64 row pairs, Q in chunks of 128
+  // rows, per own column pair; a warp's next task is nwarps further on
+  const int nchA = (P + 63) >> 6, nchQ = (n + 127) >> 7;
+  const int stepA_j = nwarps / nchA, stepA_c = nwarps - stepA_j * nchA;
+  const int stepQ_j = nwarps / nchQ, stepQ_c = nwarps - stepQ_j * nchQ;
+  const float2 z = make_float2(0.f, 0.f);
+  int sweep = 0, t = 0;  // t: rounds done (its parity picks the rotation table and inboxes)
+  while (true) {
+    for (int r = 0; r < np - 1; ++r, ++t) {
+      const int par = t & 1;
+      // (1) every rotation of the round from the CTAs that own them (remote
+      //     loads issued first), the arrivals of the last step into their
+      //     buffers meanwhile, then the indices and buffers of the own pairs
+      float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+      if (threadIdx.x < P) {
+        const int o = threadIdx.x / PP, jj = threadIdx.x - o * PP;
+        const float4* src = cluster.map_shared_rank(rot, o) + (par * PP + jj) * 2;
+        g0 = src[0];
+        g1 = src[1];
+      }
+      if (t > 0) land(r, par);
+      if (threadIdx.x < P) {
+        allr[2 * threadIdx.x] = g0;
+        allr[2 * threadIdx.x + 1] = g1;
+      }
+      for (int i = threadIdx.x + blockDim.x; i < P; i += blockDim.x) {
+        const int o = i / PP, jj = i - o * PP;
+        const float4* src = cluster.map_shared_rank(rot, o) + (par * PP + jj) * 2;
+        allr[2 * i] = src[0];
+        allr[2 * i + 1] = src[1];
+      }
       for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-        int p = player[2 * j], q = player[2 * j + 1];
+        int p = jd_player(pos_of(2 * j), r, np), q = jd_player(pos_of(2 * j + 1), r, np);
         int bp = bufof[2 * j], bq = bufof[2 * j + 1];
         if (p > q) {
-          int t = p; p = q; q = t;
-          t = bp; bp = bq; bq = t;
+          int u = p; p = q; q = u;
+          u = bp; bp = bq; bq = u;
         }
-        float c = 1.f;
-        float2 sv = make_float2(0.f, 0.f);
-        if (q < n)
-          jacobi_rotation<float>(colA[(size_t)bq * n + p], colA[(size_t)bp * n + p].x,
-                                 colA[(size_t)bq * n + q].x, c, sv);
-        rp[j] = p;
-        rq[j] = q;
-        rc[j] = c;
-        rs[j] = sv;
-        rbp[j] = bp;
-        rbq[j] = bq;
-      }
-      cluster.sync();
-      // (b) every rotation of the round, from the CTAs that own them
-      for (int t = threadIdx.x; t < P; t += blockDim.x) {
-        const int o = t / PP, jj = t - o * PP;
-        allp[t] = cluster.map_shared_rank(rp, o)[jj];
-        allq[t] = cluster.map_shared_rank(rq, o)[jj];
-        allc[t] = cluster.map_shared_rank(rc, o)[jj];
-        alls[t] = cluster.map_shared_rank(rs, o)[jj];
+        own[j] = p;
+        own[PP + j] = q;
+        own[2 * PP + j] = bp;
+        own[3 * PP + j] = bq;
       }
       __syncthreads();
-      // (c) A <- J^H A J on the own columns, Q <- Q J on the own Q columns
-      const int nA = ns * P, nQ = ns * n;
-      for (int t = threadIdx.x; t < nA + nQ; t += blockDim.x) {
-        if (t < nA) {
-          const int j = t / P, kk = t - j * P;
-          const int pk = allp[kk], qk = allq[kk];
-          if (pk >= n) continue;
-          const int pl = rp[j], ql = rq[j];
-          if (pl >= n) continue;
-          const bool vk = qk < n, vl = ql < n;
-          float2* cp = colA + (size_t)rbp[j] * n;
-          float2* cq = colA + (size_t)rbq[j] * n;
-          const float2 z = make_float2(0.f, 0.f);
-          const float2 a00 = cp[pk];
-          const float2 a01 = vl ? cq[pk] : z;
-          const float2 a10 = vk ? cp[qk] : z;
-          const float2 a11 = (vk && vl) ? cq[qk] : z;
-          float2 y00, y01, y10, y11;
-          jacobi_block<float>(a00, a01, a10, a11, allc[kk], alls[kk], rc[j], rs[j], y00, y01, y10,
-                              y11);
-          if (kk == k0 + j) {
-            // rotated 2 x 2 diagonal block: real diagonal, zeroed pair element
-            cp[pk] = make_float2(y00.x, 0.f);
-            if (vk) {
-              cq[qk] = make_float2(y11.x, 0.f);
-              cq[pk] = z;
-              cp[qk] = z;
-            }
-          } else {
-            cp[pk] = y00;
-            if (vl) cq[pk] = y01;
-            if (vk) cp[qk] = y10;
-            if (vk && vl) cq[qk] = y11;
-          }
-        } else {
-          const int e = t - nA;
-          const int j = e / n, i = e - j * n;
-          if (rq[j] >= n) continue;  // pair with the dummy index: identity
-          const float cl = rc[j];
-          const float2 sl = rs[j];
-          float2* qp = colQ + (size_t)rbp[j] * n;
-          float2* qq = colQ + (size_t)rbq[j] * n;
-          const float2 q0 = qp[i], q1 = qq[i];
-          qp[i] = add<float>(scl<float>(q0, cl), mul<float>(q1, make_float2(-sl.x, sl.y)));
-          qq[i] = add<float>(mul<float>(q0, sl), scl<float>(q1, cl));
-        }
-      }
-      __syncthreads();
-      // (d) players leaving this CTA: their columns into the neighbours' inboxes
-      for (int o = 0; o < n_out; ++o) {
-        const int b = bufof[out_slot[o]];
-        const size_t dst = (size_t)(ibuf0 + out_box[o]) * n;
-        float2* rA = cluster.map_shared_rank(colA, out_cta[o]);
-        float2* rQ = cluster.map_shared_rank(colQ, out_cta[o]);
-        if (player[out_slot[o]] < n) {
-          for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            rA[dst + i] = colA[(size_t)b * n + i];
-            rQ[dst + i] = colQ[(size_t)b * n + i];
-          }
-        }
-        if (threadIdx.x == 0) cluster.map_shared_rank(misc, out_cta[o])[out_box[o]] = player[out_slot[o]];
-      }
-      cluster.sync();
-      // (e) step every player to its next position
-      for (int s = threadIdx.x; s < nslot; s += blockDim.x) {
-        const int x = pos_of(s);
-        const int src = jd_prev(x, np);
-        if (jd_pair(src, np, P) / PP == me) {
-          const int ss = slot_of(src);
-          nplayer[s] = player[ss];
-          nbufof[s] = bufof[ss];
-        }
-      }
-      if (threadIdx.x == 0) {
-        // arrivals take the buffers of the departures (equal counts)
-        for (int i = 0; i < n_in; ++i) {
-          nplayer[in_slot[i]] = misc[in_box[i]];
-          nbufof[in_slot[i]] = i < n_out ? bufof[out_slot[i]] : ibuf0 + in_box[i];
-        }
-      }
-      __syncthreads();
-      for (int i = 0; i < n_in; ++i) {
-        const int b = nbufof[in_slot[i]];
-        const size_t src = (size_t)(ibuf0 + in_box[i]) * n;
-        if (b != ibuf0 + in_box[i] && nplayer[in_slot[i]] < n) {
-          for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            colA[(size_t)b * n + e] = colA[src + e];
-            colQ[(size_t)b * n + e] = colQ[src + e];
-          }
-        }
-      }
+      // (2) A <- J^H A J on the own columns: a warp task is one own column
+      //     pair against 64 row pairs (two 2 x 2 blocks a lane); the pair
+      //     element of an own pair becomes zero, its diagonal lives in dg.
+      //     Q <- Q J: a warp task is one own column pair, 128 rows (four a
+      //     lane).  Tasks are dealt to warps round-robin: (j, chunk) advance
+      //     by nwarps without division.
       {
-        int* t = player; player = nplayer; nplayer = t;
-        t = bufof; bufof = nbufof; nbufof = t;
+        const int ntA = ns * nchA, ntQ = ns * nchQ;
+        int j = warp / nchA, c = warp - (warp / nchA) * nchA;
+        for (int task = warp; task < ntA; task += nwarps) {
+          const float4 Rl = allr[2 * (k0 + j)];
+          const float cl = Rl.z;
+          const float2 sl = make_float2(Rl.x, Rl.y);
+          const int ql = own[PP + j];
+          const bool vl = ql < n;
+          float2* cp = colA + (size_t)own[2 * PP + j] * n;
+          float2* cq = colA + (size_t)own[3 * PP + j] * n;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int kk = c * 64 + h * 32 + lane;
+            if (kk < P) {
+              const float4 Rk = allr[2 * kk];
+              const int pqk = __float_as_int(Rk.w);
+              const int pk = pqk & 0xffff, qk = pqk >> 16;
+              const bool vk = qk < n;
+              if (kk == k0 + j) {
+                if (vk) {
+                  cq[pk] = z;
+                  cp[qk] = z;
+                }
+              } else {
+                const float2 a00 = cp[pk];
+                const float2 a01 = vl ? cq[pk] : z;
+                const float2 a10 = vk ? cp[qk] : z;
+                const float2 a11 = (vk && vl) ? cq[qk] : z;
+                float2 y00, y01, y10, y11;
+                jacobi_block<float>(a00, a01, a10, a11, Rk.z, make_float2(Rk.x, Rk.y), cl, sl, y00,
+                                    y01, y10, y11);
+                cp[pk] = y00;
+                if (vl) cq[pk] = y01;
+                if (vk) cp[qk] = y10;
+                if (vk && vl) cq[qk] = y11;
+              }
+            }
+          }
+          c += stepA_c;
+          j += stepA_j;
+          if (c >= nchA) {
+            c -= nchA;
+            ++j;
+          }
+        }
+        int task = warp - ntA % nwarps;
+        if (task < 0) task += nwarps;
+        j = task / nchQ;
+        c = task - j * nchQ;
+        for (; task < ntQ; task += nwarps) {
+          if (own[PP + j] < n) {  // a pair with the dummy index: identity
+            const float4 Rl = allr[2 * (k0 + j)];
+            const float cl = Rl.z;
+            const float2 sl = make_float2(Rl.x, Rl.y), msl = make_float2(-sl.x, sl.y);
+            float2* qp = colQ + (size_t)own[2 * PP + j] * n;
+            float2* qq = colQ + (size_t)own[3 * PP + j] * n;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const int i = c * 128 + h * 32 + lane;
+              if (i < n) {
+                const float2 q0 = qp[i], q1 = qq[i];
+                qp[i] = add<float>(scl<float>(q0, cl), mul<float>(q1, msl));
+                qq[i] = add<float>(mul<float>(q0, sl), scl<float>(q1, cl));
+              }
+            }
+          }
+          c += stepQ_c;
+          j += stepQ_j;
+          if (c >= nchQ) {
+            c -= nchQ;
+            ++j;
+          }
+        }
+      }
+      // the diagonal of every rotated pair (each CTA, identically)
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const float4 R0 = allr[2 * i], R1 = allr[2 * i + 1];
+        const int pq = __float_as_int(R0.w);
+        const int p = pq & 0xffff, q = pq >> 16;
+        if (q >= n) continue;
+        const float2 sv = make_float2(R0.x, R0.y), apq = make_float2(R1.x, R1.y);
+        float2 y00, y01, y10, y11;
+        jacobi_block<float>(make_float2(dg[p], 0.f), apq, make_float2(apq.x, -apq.y),
+                            make_float2(dg[q], 0.f), R0.z, sv, R0.z, sv, y00, y01, y10, y11);
+        dg[p] = y00.x;
+        dg[q] = y11.x;
       }
       __syncthreads();
+      // (3b) last round of a sweep: max |A_ij| (i != j) of the own columns and
+      //      max |A_ii|, published for the decision after the barrier
+      if (r == np - 2) {
+        float off = 0.f, dm = 0.f;
+        for (int e = threadIdx.x; e < nslot * n; e += blockDim.x) {
+          const int sl = e / n, i = e - sl * n;
+          const int pl = jd_player(pos_of(sl), r, np);
+          if (pl >= n || i == pl) continue;
+          const float2 v = colA[(size_t)bufof[sl] * n + i];
+          off = fmaxf(off, sqrtf(v.x * v.x + v.y * v.y));
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dm = fmaxf(dm, fabsf(dg[i]));
+        for (int o = 16; o > 0; o >>= 1) {
+          off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+          dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+        }
+        if (lane == 0) {
+          red[2 + warp] = off;
+          red[34 + warp] = dm;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          float o2 = 0.f, d2 = 0.f;
+          for (int w = 0; w < nwarps; ++w) {
+            o2 = fmaxf(o2, red[2 + w]);
+            d2 = fmaxf(d2, red[34 + w]);
+          }
+          red[0] = o2;
+          red[1] = d2;
+        }
+      }
+      // (4) buffers after the step: indices that stay here keep theirs, the
+      //     arrivals take those of the departures
+      for (int sl = threadIdx.x; sl < nslot; sl += blockDim.x) {
+        const int src = jd_prev(pos_of(sl), np);
+        if (jd_pair(src, np, P) / PP == me) nbufof[sl] = bufof[slot_of(src)];
+      }
+      if (threadIdx.x == 0)
+        for (int i = 0; i < n_in; ++i) nbufof[in_slot[i]] = bufof[out_slot[i]];
+      // (5) departing columns into the neighbours' inboxes of the other parity
+      for (int o = 0; o < n_out; ++o) {
+        if (jd_player(pos_of(out_slot[o]), r, np) >= n) continue;
+        const int b = bufof[out_slot[o]];
+        const size_t dst = (size_t)(ibuf0 + 2 * (par ^ 1) + out_box[o]) * n;
+        float2* rA = cluster.map_shared_rank(colA, out_cta[o]) + dst;
+        float2* rQ = cluster.map_shared_rank(colQ, out_cta[o]) + dst;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          rA[i] = colA[(size_t)b * n + i];
+          rQ[i] = colQ[(size_t)b * n + i];
+        }
+      }
+      __syncthreads();
+      {
+        int* u = bufof; bufof = nbufof; nbufof = u;
+      }
+      // (6) rotations of the next round (arrivals still in their inboxes)
+      publish(r + 1 == np - 1 ? 0 : r + 1, par ^ 1, true);
+      cluster.sync();
     }
     ++sweep;
-    // convergence: max |A_ij| (i != j) against max |A_ii| over every column
-    float off = 0.f, dm = 0.f;
-    for (int t = threadIdx.x; t < nslot * n; t += blockDim.x) {
-      const int s = t / n, i = t - s * n;
-      const int pl = player[s];
-      if (pl >= n) continue;
-      const float2 v = colA[(size_t)bufof[s] * n + i];
-      if (i == pl) dm = fmaxf(dm, fabsf(v.x));
-      else off = fmaxf(off, sqrtf(v.x * v.x + v.y * v.y));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
-      dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[2 + (threadIdx.x >> 5)] = off;
-      red[34 + (threadIdx.x >> 5)] = dm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float o2 = 0.f, d2 = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        o2 = fmaxf(o2, red[2 + w]);
-        d2 = fmaxf(d2, red[34 + w]);
-      }
-      red[0] = o2;
-      red[1] = d2;
-    }
-    cluster.sync();
     float goff = 0.f, gdm = 0.f;
     for (int c = 0; c < (int)cluster.num_blocks(); ++c) {
       const float* rr = cluster.map_shared_rank(red, c);
       goff = fmaxf(goff, rr[0]);
       gdm = fmaxf(gdm, rr[1]);
     }
-    done = goff <= a.tol * fmaxf(gdm, 1e-30f);
-    cluster.sync();  // every CTA has read the published values
+    if (goff <= a.tol * fmaxf(gdm, 1e-30f) || sweep >= a.max_sweeps) break;
   }
 
-  // ---- results: column j of Q and A_jj for every own index j
-  for (int t = threadIdx.x; t < nslot * n; t += blockDim.x) {
-    const int s = t / n, i = t - s * n;
-    const int pl = player[s];
+  // ---- results (after whole sweeps every index is back at its own position)
+  land(0, t & 1);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nslot * n; e += blockDim.x) {
+    const int sl = e / n, i = e - sl * n;
+    const int pl = pos_of(sl);
     if (pl >= n) continue;
-    const float2 v = colQ[(size_t)bufof[s] * n + i];
+    const float2 v = colQ[(size_t)bufof[sl] * n + i];
     a.Q[(size_t)pl * a.ldq + i] = make_double2((double)v.x, (double)v.y);
-    if (i == pl) a.diag[pl] = (double)colA[(size_t)bufof[s] * n + i].x;
   }
-  if (me == 0 && threadIdx.x == 0) {
-    a.info[0] = 0;
-    a.info[1] = sweep;
+  if (me == 0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a.diag[i] = (double)dg[i];
+    if (threadIdx.x == 0) {
+      a.info[0] = 0;
+      a.info[1] = sweep;
+    }
   }
   cluster.sync();
 }
@@ -336,7 +433,7 @@ bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double to
     const char* e = std::getenv("PWH_JACOBI_GLOBAL");
     return e && e[0] == '1';
   }();
-  if (off || n < 4) return false;
+  if (off || n < 64) return false;  // at least two pairs per CTA
   const int np = n + (n & 1), P = np / 2;
   const int PP = (P + kDsmCluster - 1) / kDsmCluster;
   const size_t smem = jdsm_smem_bytes(n, P, PP);

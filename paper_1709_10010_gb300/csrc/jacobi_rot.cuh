@@ -15,26 +15,25 @@ __device__ __forceinline__ void jacobi_rotation(cx<T> apq, T app, T aqq, T& c, c
   // |A_pq| scaled against underflow: an inaccurate modulus would make the
   // rotation non-unitary when zeta is O(1) (degenerate diagonal)
   const T mx = fmax(fabs(apq.x), fabs(apq.y));
-  T g = 0;
-  if (mx > (T)0) {
-    const T ux = apq.x / mx, uy = apq.y / mx;
-    g = mx * sqrt(ux * ux + uy * uy);
-  }
+  if (!(mx > (T)0)) return;
+  // unit direction of A_pq from quotients of at most 1 (no reciprocal of a
+  // possibly subnormal |A_pq|), h in [1, sqrt 2]
+  const T ux = apq.x / mx, uy = apq.y / mx;
+  const T h = sqrt(ux * ux + uy * uy);
+  const T g = mx * h;
   // an A_pq too small to change either diagonal entry is dropped without
   // rotating (the 2 x 2 update writes it as zero)
   const bool negligible = (fabs(app) + (T)100 * g == fabs(app)) &&
                           (fabs(aqq) + (T)100 * g == fabs(aqq));
-  if (g > (T)0 && !negligible) {
-    const T zeta = (aqq - app) / (2 * g);
-    // tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
-    // (1/(2 zeta) once zeta^2 would overflow)
-    const T t = fabs(zeta) > (T)1e9 ? (T)0.5 / zeta
-                                    : (zeta >= 0 ? (T)1 : (T)-1) /
-                                          (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-    c = (T)1 / sqrt((T)1 + t * t);
-    const T sn = t * c;
-    s = mk<T>(sn * apq.x / g, sn * apq.y / g);
-  }
+  if (negligible) return;
+  const T zeta = (aqq - app) / (2 * g);
+  // tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
+  // (1/(2 zeta) once zeta^2 would overflow)
+  const T t = fabs(zeta) > (T)1e9 ? (T)0.5 / zeta
+                                  : (zeta >= 0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+  c = (T)1 / sqrt((T)1 + t * t);
+  const T e = t * c / h;
+  s = mk<T>(e * ux, e * uy);
 }
 
 // The 2 x 2 block of J^H A J on rows (pk, qk) and columns (pl, ql), from the
