@@ -324,6 +324,19 @@ pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t 
                              double* theta, void* C, void* Q, int64_t ldq, int32_t warm,
                              int32_t precision);
 
+/* Complex GEMM of the subspace algebra (the O_ij = <psi_i|O|psi_j> products and
+ * basis rotations of Sec. "New parallelization levels"), as the eigensolver
+ * uses it: C = alpha op(A) B + beta C, op(A) = A^H when conj_a else A; op(A)
+ * is M x K, B is K x N, C is M x N; all DEVICE complex128, column-major with
+ * the given leading dimensions (lda >= rows of A as stored).  alpha, beta:
+ * HOST double[2] (re, im).  precision PWH_FP64: FP64 arithmetic; PWH_MIXED:
+ * operands rounded to FP32, FP32 accumulation (relative error about
+ * sqrt(K) 1e-7), result widened.  Asynchronous on the system's stream; uses
+ * the system's split-K workspace (one GEMM at a time per system). */
+pwh_status pwh_subspace_gemm(pwh_system* sys, int32_t precision, int32_t conj_a, int32_t M,
+                             int32_t N, int32_t K, const double* alpha, const void* A, int64_t lda,
+                             const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc);
+
 /* Synchronize the system's stream and report device-side failures: returns
  * PWH_ERR_TIMEOUT (and clears the flag) if a bounded wait inside a kernel gave
  * up since the last call, so that its results must be discarded. */

@@ -94,6 +94,8 @@ SIGNATURES = {
     "pwh_davidson_solve": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
                                     ctypes.POINTER(DavidsonStats)]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_subspace_gemm": (_c_i32, [_c_p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_p, _c_p, _c_i64,
+                                   _c_p, _c_i64, _c_p, _c_p, _c_i64]),
     "pwh_last_error": (ctypes.c_char_p, []),
 }
 
@@ -274,6 +276,27 @@ class System:
                                        ctypes.c_void_p(C.data_ptr()), qp, ldq, int(warm),
                                        PRECISIONS[precision]))
         return theta, C
+
+    def gemm(self, A, B, C=None, conj_a=False, alpha=1.0, beta=0.0, precision="fp64"):
+        """C = alpha op(A) B + beta C on the device (the eigensolver's subspace
+        GEMM).  Matrices are CUDA complex128 tensors holding column-major
+        matrices as their transposes (row j of the tensor = column j), like
+        subspace_eigh: A has shape (cols, rows) of the stored A, op(A) = A^H
+        when conj_a.  Returns C (shape (N, M))."""
+        torch = _torch()
+        ka, ra = int(A.shape[0]), int(A.shape[1])     # stored A: ra rows x ka columns
+        M, K = (ka, ra) if conj_a else (ra, ka)
+        N = int(B.shape[0])
+        assert int(B.shape[1]) == K, "inner dimensions differ"
+        if C is None:
+            C = torch.zeros((N, M), dtype=torch.complex128, device=A.device)
+        al = (ctypes.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+        be = (ctypes.c_double * 2)(complex(beta).real, complex(beta).imag)
+        _check(lib().pwh_subspace_gemm(self._h, PRECISIONS[precision], int(bool(conj_a)), M, N, K, al,
+                                       ctypes.c_void_p(A.data_ptr()), max(1, ra),
+                                       ctypes.c_void_p(B.data_ptr()), max(1, K), be,
+                                       ctypes.c_void_p(C.data_ptr()), max(1, M)))
+        return C
 
     def sync(self):
         """Wait for the stream; raises PwhError(PWH_ERR_TIMEOUT) if a bounded
