@@ -381,10 +381,10 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   const int64_t npw = s.npw;
   const int p1 = prec_first < 0 ? prec : prec_first;  // first pass may be cheaper
   sgemm(s, p1, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
-  cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st);
+  cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st, p1 != PWH_FP64);
   sgemm(s, p1, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
   sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
-  cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st);
+  cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st, prec != PWH_FP64);
   sgemm(s, prec, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
   PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4096, L.kk, sizeof(int), cudaMemcpyDeviceToHost, st));
   PWH_CUDA(cudaStreamSynchronize(st));

@@ -378,19 +378,22 @@ __global__ void k_hermitize(double2* __restrict__ H, int64_t ld, int m0, int m) 
 // orthonormal columns (other columns zero); *kk = number kept.  The lower
 // triangle lives in shared memory (packed by columns) when SMEM, else in the
 // k x k global scratch W.
-template <bool SMEM>
-__global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __restrict__ t0,
-                         double drop_rel, double piv_tol, double2* __restrict__ Wg,
-                         double2* __restrict__ Tr, int* __restrict__ kk) {
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(1024) k_cholqr(const double2* __restrict__ S, int k,
+                                                 const double* __restrict__ t0, double drop_rel,
+                                                 double piv_tol, cx<T>* __restrict__ Wg,
+                                                 double2* __restrict__ Tr, int* __restrict__ kk) {
   extern __shared__ __align__(16) unsigned char chsm[];
   __shared__ int keep_s[1024];
   __shared__ int rank_s[1024];
   __shared__ double dinv_s[1024];
   __shared__ int nkeep_s;
-  __shared__ double piv_s;
-  double2* L = SMEM ? (double2*)chsm : Wg;
-  // element (i, j), i >= j, of the lower triangle
-  auto at = [&](int i, int j) -> double2& {
+  __shared__ T piv_s;
+  cx<T>* L = SMEM ? (cx<T>*)chsm : Wg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // element (i, j), i >= j, of the lower triangle (packed by columns in
+  // shared memory, else a k x k column-major scratch)
+  auto at = [&](int i, int j) -> cx<T>& {
     return SMEM ? L[(size_t)j * k - (size_t)j * (j - 1) / 2 + (i - j)] : L[(size_t)j * k + i];
   };
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
@@ -400,32 +403,35 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
     dinv_s[j] = keep ? 1.0 / sqrt(d) : 0.0;
   }
   __syncthreads();
-  // unit-diagonal scaling of the lower triangle
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
-    const int i = t % k, j = t / k;
-    if (i >= j) at(i, j) = scl<double>(S[t], dinv_s[i] * dinv_s[j]);
-  }
+  // unit-diagonal scaling of the lower triangle (a warp per column)
+  for (int j = warp; j < k; j += nwarps)
+    for (int i = j + lane; i < k; i += 32) {
+      const double2 v = S[(size_t)j * k + i];
+      const double sc = dinv_s[i] * dinv_s[j];
+      at(i, j) = mk<T>((T)(v.x * sc), (T)(v.y * sc));
+    }
   __syncthreads();
   // right-looking Cholesky on the kept set
   for (int j = 0; j < k; ++j) {
     if (threadIdx.x == 0) {
-      const double piv = at(j, j).x;
-      if (keep_s[j] && !(piv > piv_tol)) keep_s[j] = 0;
-      piv_s = keep_s[j] ? sqrt(piv) : 0.0;
+      const T piv = at(j, j).x;
+      if (keep_s[j] && !(piv > (T)piv_tol)) keep_s[j] = 0;
+      piv_s = keep_s[j] ? sqrt(piv) : (T)0;
     }
     __syncthreads();
     if (keep_s[j]) {
-      const double lj = piv_s;
+      const T rl = (T)1 / piv_s;
       for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
-        if (keep_s[i]) at(i, j) = scl<double>(at(i, j), 1.0 / lj);
+        if (keep_s[i]) at(i, j) = scl<T>(at(i, j), rl);
       __syncthreads();
-      const int r = k - j - 1;
-      for (int t = threadIdx.x; t < r * r; t += blockDim.x) {
-        const int i = j + 1 + t % r, l = j + 1 + t / r;
-        if (i >= l && keep_s[i] && keep_s[l])
-          at(i, l) = sub<double>(at(i, l), mulc<double>(at(i, j), at(l, j)));
+      // trailing update of the lower triangle: a warp per column l, lanes over rows i >= l
+      for (int l = j + 1 + warp; l < k; l += nwarps) {
+        if (!keep_s[l]) continue;
+        const cx<T> ljc = at(l, j);
+        for (int i = l + lane; i < k; i += 32)
+          if (keep_s[i]) at(i, l) = sub<T>(at(i, l), mulc<T>(at(i, j), ljc));
       }
-      if (threadIdx.x == 0) at(j, j) = make_double2(lj, 0.0);
+      if (threadIdx.x == 0) at(j, j) = mk<T>(piv_s, (T)0);
     }
     __syncthreads();
   }
@@ -440,18 +446,21 @@ __global__ void k_cholqr(const double2* __restrict__ S, int k, const double* __r
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) Tr[t] = make_double2(0.0, 0.0);
   __syncthreads();
   // Tr = D^-1/2 L^-H: column rank(j) solves L^H x = e_j by back substitution
+  // (a thread per column, in the compute precision)
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     if (!keep_s[j]) continue;
     double2* x = Tr + (size_t)rank_s[j] * k;
     for (int i = j; i >= 0; --i) {
       if (!keep_s[i]) continue;
-      double2 v = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      cx<T> v = mk<T>(i == j ? (T)1 : (T)0, (T)0);
       for (int l = i + 1; l <= j; ++l)
         if (keep_s[l]) {
-          const double2 lli = at(l, i);  // (L^H)_{il} = conj(L_li)
-          v = sub<double>(v, mul<double>(make_double2(lli.x, -lli.y), x[l]));
+          const cx<T> lli = at(l, i);  // (L^H)_{il} = conj(L_li)
+          const double2 xl = x[l];
+          v = sub<T>(v, mul<T>(mk<T>(lli.x, -lli.y), mk<T>((T)xl.x, (T)xl.y)));
         }
-      x[i] = scl<double>(v, 1.0 / at(i, i).x);
+      const T rd = (T)1 / at(i, i).x;
+      x[i] = make_double2((double)(v.x * rd), (double)(v.y * rd));
     }
   }
   __syncthreads();
@@ -690,23 +699,35 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {
   PWH_LAUNCH_CHECK();
 }
 
-void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
-                   double drop_rel, double2* Tr, int* kk, cudaStream_t st) {
-  if (k > 1024) throw Error{PWH_ERR_ARG, "block of more than 1024 new directions"};
-  // the packed lower triangle fits the shared memory up to k = 160
-  const size_t tri = (size_t)k * (k + 1) / 2 * sizeof(double2);
+template <typename T>
+static void cholqr_launch(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
+                          double piv_tol, double2* Tr, int* kk, cudaStream_t st) {
+  // the packed lower triangle in shared memory up to 200 KB (k = 160 in FP64,
+  // 226 in FP32), else in the global scratch
+  const size_t tri = (size_t)k * (k + 1) / 2 * sizeof(cx<T>);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_cholqr<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(k_cholqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   });
-  TimedScope ts(s, KF_CHOLQR, st);
   if (tri <= 200 * 1024) {
-    k_cholqr<true><<<1, 1024, tri, st>>>(S, k, t0, drop_rel, 1e-12, nullptr, Tr, kk);
+    k_cholqr<T, true><<<1, 1024, tri, st>>>(S, k, t0, drop_rel, piv_tol, nullptr, Tr, kk);
   } else {
     ensure(w.chol, (size_t)k * k * sizeof(double2));
-    k_cholqr<false><<<1, 1024, 0, st>>>(S, k, t0, drop_rel, 1e-12, (double2*)w.chol.p, Tr, kk);
+    k_cholqr<T, false><<<1, 1024, 0, st>>>(S, k, t0, drop_rel, piv_tol, (cx<T>*)w.chol.p, Tr, kk);
   }
   PWH_LAUNCH_CHECK();
+}
+
+void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
+                   double drop_rel, double2* Tr, int* kk, cudaStream_t st, bool fp32) {
+  if (k > 1024) throw Error{PWH_ERR_ARG, "block of more than 1024 new directions"};
+  TimedScope ts(s, KF_CHOLQR, st);
+  // a pivot of the unit-diagonal Gram matrix below ~10x the rounding of its
+  // arithmetic marks a numerically dependent column
+  if (fp32)
+    cholqr_launch<float>(w, S, k, t0, drop_rel, 1e-6, Tr, kk, st);
+  else
+    cholqr_launch<double>(w, S, k, t0, drop_rel, 1e-12, Tr, kk, st);
 }
 
 }  // namespace pwh

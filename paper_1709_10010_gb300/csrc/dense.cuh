@@ -50,8 +50,9 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);
 
 // Tr (k x k) such that T Tr has orthonormal first *kk columns (device int),
 // from the Gram matrix S = T^H T; t0 (optional) = column norms before the
-// projection that produced T, for the relative drop test.
+// projection that produced T, for the relative drop test.  fp32: Cholesky in
+// FP32 arithmetic (for a Gram matrix that is itself FP32-accurate), else FP64.
 void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
-                   double drop_rel, double2* Tr, int* kk, cudaStream_t st);
+                   double drop_rel, double2* Tr, int* kk, cudaStream_t st, bool fp32 = false);
 
 }  // namespace pwh
