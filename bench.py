@@ -364,7 +364,7 @@ FAMILY_BOUND = {
     "tc_gemm_becp": ("tensor", "flops", "bf16"), "tc_gemm_backproj": ("tensor", "flops", "bf16"),
     "cgemm_fp64": ("alu", "flops", "fp64"), "cgemm_fp32": ("alu", "flops", "fp32"),
     "jacobi_fp64": ("alu", "flops", "fp64"), "cholqr_fp64": ("alu", "flops", "fp64"),
-    "jacobi_fp32": ("alu", "flops", "fp32"),
+    "jacobi_fp32": ("alu", "flops", "fp32"), "zgemm_fp64_tc": ("tensor", "flops", "bf16"),
 }
 
 

@@ -98,7 +98,8 @@ void free_davidson_ws(DavWs* w);
 // Optional per-family kernel timing with CUDA events on the system's stream.
 enum KernelFamily {
   KF_FFT_ZINV64 = 0, KF_FFT_PLANE64, KF_FFT_ZFWD64, KF_FFT_ZINV32, KF_FFT_PLANE32, KF_FFT_ZFWD32,
-  KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_JACOBI32, KF_COUNT
+  KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_JACOBI32,
+  KF_GEMM_OZ, KF_COUNT
 };
 extern const char* const kKernelFamilyName[KF_COUNT];
 
@@ -175,6 +176,7 @@ struct System {
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
+  DevBuf<char> ws_oz;               // sliced operands and partials of the FP64-equivalent GEMM
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
   int* d_err = nullptr;             // device error word (bounded waits that gave up)
   float* d_mlp = nullptr;           // learned-preconditioner parameters

@@ -12,6 +12,7 @@
 // reduction (K = npw) with few output tiles is split over blockIdx.z into a
 // workspace and summed by k_splitk_reduce in a fixed order (deterministic).
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "gemm.cuh"
@@ -277,10 +278,25 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
   }
 }
 
+// FP64 products of at least this many flops go to the tensor cores as sliced
+// integer products (oz_gemm); PWH_GEMM_FP64_SIMT=1 in the environment keeps
+// every FP64 product on the FP64 pipe.
+constexpr double kOzMinFlops = 2e8;
+
 template <typename T>
 void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
            const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
            const double* rowscale) {
+  if constexpr (sizeof(T) == 8) {
+    static const bool simt_only = [] {
+      const char* e = std::getenv("PWH_GEMM_FP64_SIMT");
+      return e && e[0] == '1';
+    }();
+    if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kOzMinFlops) {
+      oz_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
+      return;
+    }
+  }
   cgemm_impl<T, T>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
 }
 

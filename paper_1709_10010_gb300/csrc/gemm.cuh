@@ -18,4 +18,11 @@ void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const 
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st);
 
+// FP64-equivalent complex GEMM on the BF16 tensor cores (gemm_tc.cu): same
+// contract as cgemm<double>, results within FP64-level rounding (integer
+// slices of the operands, exact partial sums).
+void oz_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+             int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+             cudaStream_t st, const double* rowscale = nullptr);
+
 }  // namespace pwh

@@ -58,6 +58,10 @@ struct TcArgs {
   int64_t ldh;
   int nb;
   int* err;          // device error word
+  // sliced operands (FP64-equivalent GEMM): product t multiplies A segment
+  // oz_a[t] by B segment oz_b[t]
+  int oz;
+  unsigned char oz_a[32], oz_b[32];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -216,7 +220,13 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       int xa, xb;
-      kb_coords(kb0 + kb, args.kb_seg, xa, xb);
+      if (args.oz) {
+        const int t = (kb0 + kb) / args.kb_seg, r = (kb0 + kb) - t * args.kb_seg;
+        xa = (args.oz_a[t] * args.kb_seg + r) * TC_BK;
+        xb = (args.oz_b[t] * args.kb_seg + r) * TC_BK;
+      } else {
+        kb_coords(kb0 + kb, args.kb_seg, xa, xb);
+      }
       uint8_t* sa = smem + s * TC_STAGE_BYTES;
       mbar_expect_tx(&full[s], TC_STAGE_BYTES);
       tma_load_2d(sa, &tma_a, xa, m0, &full[s]);
@@ -546,6 +556,382 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
   a2.kb_per_split = terms * kbs2; a2.hpsi = hpsi; a2.ldh = ldh; a2.nb = nb;
   a2.err = device_error_word(s);
   launch_tc(s, 1, ma2, mb2, a2, gm2, gn2, 1, st);
+}
+
+
+// ------------------------------------ FP64-equivalent complex GEMM (slices) ----
+// C = alpha op(A) B + beta C for FP64 (complex128) operands on the BF16 tensor
+// cores, accurate to about FP64 rounding: the error-free splitting of Ozaki et
+// al. (products of integer slices summed exactly).  Each real row r of an
+// operand (after the complex interleaving of the projector GEMM above) gets
+// the exponent e_r with max|x_r| < 2^e_r and is written as
+//     x = 2^e_r sum_{s < OZ_S} a_s 2^(-7 - 8 s),   a_s integers, |a_s| <= 128,
+// which BF16 holds exactly.  A product a_s b_t is at most 2^14 and a sum of
+// 1024 of them at most 2^24, so every FP32 partial of a 1024-wide K chunk is an
+// exact integer.  The partials of the pairs with s + t <= OZ_G are summed in
+// int64 by weight 2^(-8(s+t)) and scaled once in FP64.  Dropped terms and
+// slice truncation are below 2^-54 of max|a| max|b| per elementary product.
+constexpr int OZ_S = 7;
+constexpr int OZ_G = OZ_S - 1;
+constexpr int OZ_PAIRS = (OZ_S * (OZ_S + 1)) / 2;  // pairs with s + t <= OZ_G
+static_assert(OZ_PAIRS <= 32, "pair table");
+__constant__ unsigned char c_oz_g[32];            // s + t of pair p
+
+__device__ __forceinline__ int oz_exp(double mx) {
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  return e;  // mx < 2^e
+}
+// the OZ_S integer slices of x for exponent e, as BF16
+__device__ __forceinline__ void oz_split(double x, int e, __nv_bfloat16* a) {
+  double r = ldexp(x, 7 - e);  // |r| < 128
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    const double q = rint(r);
+    a[s] = __float2bfloat16_rn((float)q);
+    r = (r - q) * 256.0;
+  }
+}
+
+// Exponents of the rows 2j (real parts) and 2j+1 (imaginary parts) of the
+// interleaved operand whose row pair j is column j of X (K x J, ld): one block
+// per column.
+__global__ void k_oz_colexp(const double2* __restrict__ X, int64_t ld, int K, int* __restrict__ ex) {
+  __shared__ double red[2][32];
+  const int j = blockIdx.x;
+  double mr = 0.0, mi = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double2 v = X[(size_t)j * ld + k];
+    mr = fmax(mr, fabs(v.x));
+    mi = fmax(mi, fabs(v.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mi = fmax(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = mr;
+    red[1][threadIdx.x >> 5] = mi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mr = fmax(mr, red[0][w]);
+      mi = fmax(mi, red[1][w]);
+    }
+    ex[2 * j] = oz_exp(mr);
+    ex[2 * j + 1] = oz_exp(mi);
+  }
+}
+// Slices of that operand: row 2j+c, segment s holds a_s of (Re, Im) X[k][j]
+// at column s seg + k (zero for K <= k < seg).
+__global__ void k_oz_slice_cols(const double2* __restrict__ X, int64_t ld, int K, int seg,
+                                const int* __restrict__ ex, __nv_bfloat16* __restrict__ out,
+                                int64_t pitch) {
+  const int j = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= seg) return;
+  const double2 v = k < K ? X[(size_t)j * ld + k] : make_double2(0.0, 0.0);
+  __nv_bfloat16 ar[OZ_S], ai[OZ_S];
+  oz_split(v.x, ex[2 * j], ar);
+  oz_split(v.y, ex[2 * j + 1], ai);
+  __nv_bfloat16* r0 = out + (size_t)(2 * j) * pitch + k;
+  __nv_bfloat16* r1 = r0 + pitch;
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    r0[(size_t)s * seg] = ar[s];
+    r1[(size_t)s * seg] = ai[s];
+  }
+}
+
+// Exponent of row m of the operand A2[m][2k+c] = (Re, Im) A[m][k] (A: M x K,
+// column-major, ld): one thread per row.
+__global__ void k_oz_rowexp(const double2* __restrict__ A, int64_t ld, int M, int K,
+                            int* __restrict__ ex) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double mx = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double2 v = A[(size_t)k * ld + m];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  ex[m] = oz_exp(mx);
+}
+// Slices of A2: row m, segment s, column 2k+c (zero for 2K <= 2k+c < seg);
+// 32 x 32 tiles transposed through shared memory.
+__global__ void k_oz_slice_rows(const double2* __restrict__ A, int64_t ld, int M, int K, int seg,
+                                const int* __restrict__ ex, __nv_bfloat16* __restrict__ out,
+                                int64_t pitch) {
+  __shared__ double2 tile[32][33];
+  const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
+    const int mm = t & 31, kk = t >> 5;
+    const int m = m0 + mm, k = k0 + kk;
+    tile[kk][mm] = (m < M && k < K) ? A[(size_t)k * ld + m] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
+    const int kk = t & 31, mm = t >> 5;
+    const int m = m0 + mm, k = k0 + kk;
+    if (m >= M || 2 * k >= seg) continue;
+    const double2 v = tile[kk][mm];
+    const int e = ex[m];
+    __nv_bfloat16 ar[OZ_S], ai[OZ_S];
+    oz_split(v.x, e, ar);
+    oz_split(v.y, e, ai);
+    __nv_bfloat16* r = out + (size_t)m * pitch + 2 * k;
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      __nv_bfloat162 p;
+      p.x = ar[s];
+      p.y = ai[s];
+      *(__nv_bfloat162*)(r + (size_t)s * seg) = p;
+    }
+  }
+}
+
+// B operand of the non-conjugated product: rows 2n, 2n+1 of
+//     B2[2n][2k] = Re, B2[2n][2k+1] = -Im, B2[2n+1][2k] = Im, B2[2n+1][2k+1] = Re
+// of B[k][n] (B: K x N, column-major, ld), both rows with the exponent of
+// max(|Re|, |Im|) over column n: one block per column.
+__global__ void k_oz_colexp_b2(const double2* __restrict__ B, int64_t ld, int K,
+                               int* __restrict__ ex) {
+  __shared__ double red[32];
+  const int n = blockIdx.x;
+  double mx = 0.0;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const double2 v = B[(size_t)n * ld + k];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    ex[2 * n] = ex[2 * n + 1] = oz_exp(mx);
+  }
+}
+__global__ void k_oz_slice_b2(const double2* __restrict__ B, int64_t ld, int K, int seg,
+                              const int* __restrict__ ex, __nv_bfloat16* __restrict__ out,
+                              int64_t pitch) {
+  const int n = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * k >= seg) return;
+  const double2 v = k < K ? B[(size_t)n * ld + k] : make_double2(0.0, 0.0);
+  const int e = ex[2 * n];
+  __nv_bfloat16 ar[OZ_S], ai[OZ_S];
+  oz_split(v.x, e, ar);
+  oz_split(v.y, e, ai);
+  __nv_bfloat16* r0 = out + (size_t)(2 * n) * pitch + 2 * k;
+  __nv_bfloat16* r1 = r0 + pitch;
+#pragma unroll
+  for (int s = 0; s < OZ_S; ++s) {
+    __nv_bfloat162 p0, p1;
+    p0.x = ar[s];
+    p0.y = __hneg(ai[s]);
+    p1.x = ai[s];
+    p1.y = ar[s];
+    *(__nv_bfloat162*)(r0 + (size_t)s * seg) = p0;
+    *(__nv_bfloat162*)(r1 + (size_t)s * seg) = p1;
+  }
+}
+
+// Exact accumulation of the integer partials of one real output: weights
+// 2^(-8g) folded into hi (g <= 2) and lo (g >= 3); value
+// 2^(e - 14) (hi 2^-16 + lo 2^-(8 OZ_G)).
+struct OzAcc {
+  long long hi = 0, lo = 0;
+  __device__ __forceinline__ void add(float v, int g) {
+    const long long i = __float2ll_rn(v);
+    if (g <= 2) hi += i * (1ll << (8 * (2 - g)));
+    else lo += i * (1ll << (8 * (OZ_G - g)));
+  }
+  __device__ __forceinline__ double value(int e) const {
+    return ldexp((double)hi, e - 14 - 16) + ldexp((double)lo, e - 14 - 8 * OZ_G);
+  }
+};
+
+// op(A) = A^H: complex (m, n) from the four real products of rows 2m, 2m+1 and
+// columns 2n, 2n+1 (Re = C[2m][2n] + C[2m+1][2n+1], Im = C[2m][2n+1] -
+// C[2m+1][2n]); part[z][n'][m'] with M' = 2M, N' = 2N, z = pair * nchunk + chunk.
+__global__ void k_oz_reduce_cj(const float* __restrict__ part, int nz, int nchunk, int M, int N,
+                               const int* __restrict__ exa, const int* __restrict__ exb,
+                               const double* __restrict__ rowscale, double2 alpha, double2 beta,
+                               double2* __restrict__ C, int64_t ldc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)M * N) return;
+  const int m = (int)(t % M), n = (int)(t / M);
+  const int64_t Mr = 2 * (int64_t)M, plane = Mr * 2 * (int64_t)N;
+  OzAcc q00, q10, q01, q11;
+  for (int z = 0; z < nz; ++z) {
+    const int g = c_oz_g[z / nchunk];
+    const float* pz = part + (size_t)z * plane;
+    const float2 c0 = *(const float2*)(pz + (size_t)(2 * n) * Mr + 2 * m);      // (2m,2n), (2m+1,2n)
+    const float2 c1 = *(const float2*)(pz + (size_t)(2 * n + 1) * Mr + 2 * m);  // (2m,2n+1), (2m+1,2n+1)
+    q00.add(c0.x, g);
+    q10.add(c0.y, g);
+    q01.add(c1.x, g);
+    q11.add(c1.y, g);
+  }
+  const int ea0 = exa[2 * m], ea1 = exa[2 * m + 1], eb0 = exb[2 * n], eb1 = exb[2 * n + 1];
+  double re = q00.value(ea0 + eb0) + q11.value(ea1 + eb1);
+  double im = q01.value(ea0 + eb1) - q10.value(ea1 + eb0);
+  if (rowscale) {
+    re *= rowscale[m];
+    im *= rowscale[m];
+  }
+  double2 r = make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+  if (beta.x != 0.0 || beta.y != 0.0) {
+    const double2 c = C[(size_t)n * ldc + m];
+    r.x += beta.x * c.x - beta.y * c.y;
+    r.y += beta.x * c.y + beta.y * c.x;
+  }
+  C[(size_t)n * ldc + m] = r;
+}
+
+// op(A) = A: complex (m, n) = (C2[m][2n], C2[m][2n+1]); part[z][n'][m'] with
+// M' = M, N' = 2N.
+__global__ void k_oz_reduce_nn(const float* __restrict__ part, int nz, int nchunk, int M, int N,
+                               const int* __restrict__ exa, const int* __restrict__ exb,
+                               const double* __restrict__ rowscale, double2 alpha, double2 beta,
+                               double2* __restrict__ C, int64_t ldc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)M * N) return;
+  const int m = (int)(t % M), n = (int)(t / M);
+  const int64_t plane = (int64_t)M * 2 * N;
+  OzAcc qr, qi;
+  for (int z = 0; z < nz; ++z) {
+    const int g = c_oz_g[z / nchunk];
+    const float* pz = part + (size_t)z * plane;
+    qr.add(pz[(size_t)(2 * n) * M + m], g);
+    qi.add(pz[(size_t)(2 * n + 1) * M + m], g);
+  }
+  const int e = exa[m] + exb[2 * n];
+  double re = qr.value(e), im = qi.value(e);
+  if (rowscale) {
+    re *= rowscale[m];
+    im *= rowscale[m];
+  }
+  double2 r = make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+  if (beta.x != 0.0 || beta.y != 0.0) {
+    const double2 c = C[(size_t)n * ldc + m];
+    r.x += beta.x * c.x - beta.y * c.y;
+    r.y += beta.x * c.y + beta.y * c.x;
+  }
+  C[(size_t)n * ldc + m] = r;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void oz_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+             int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+             cudaStream_t st, const double* rowscale) {
+  if (M <= 0 || N <= 0) return;
+  static std::once_flag once;
+  static unsigned char pa[32], pb[32];
+  std::call_once(once, [] {
+    unsigned char g[32] = {};
+    int p = 0;
+    for (int gg = 0; gg <= OZ_G; ++gg)
+      for (int sa = 0; sa <= gg; ++sa) {
+        pa[p] = (unsigned char)sa;
+        pb[p] = (unsigned char)(gg - sa);
+        g[p] = (unsigned char)gg;
+        ++p;
+      }
+    cudaMemcpyToSymbol(c_oz_g, g, sizeof(g));
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  // real GEMM geometry: C' (Mr x Nr) = A' (Mr x Kr) B'^T, both K-major
+  const int64_t Mr = conjA ? 2 * (int64_t)M : M, Nr = 2 * (int64_t)N;
+  const int64_t Kr = conjA ? K : 2 * (int64_t)K;
+  int64_t seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
+  int kb_seg = (int)(seg / TC_BK);
+  // K blocks per exact partial: at most 16 (1024 wide) and dividing kb_seg;
+  // pad the segment to whole 16-block chunks when that costs little, else
+  // take a divisor of at least 8
+  int kbps = kb_seg;
+  if (kb_seg > 16) {
+    const int pad16 = (kb_seg + 15) / 16 * 16;
+    kbps = 0;
+    if ((pad16 - kb_seg) * 16 > kb_seg)
+      for (int d = 16; d >= 8 && !kbps; --d)
+        if (kb_seg % d == 0) kbps = d;
+    if (!kbps) {
+      kb_seg = pad16;
+      seg = (int64_t)kb_seg * TC_BK;
+      kbps = 16;
+    }
+  }
+  const int nchunk = kb_seg / kbps;
+  const int nz = OZ_PAIRS * nchunk;
+  const int64_t pitch = OZ_S * seg;
+  const size_t bytes_a = align256((size_t)Mr * pitch * 2), bytes_b = align256((size_t)Nr * pitch * 2);
+  const size_t bytes_e = align256((size_t)(Mr + Nr) * sizeof(int));
+  const size_t bytes_p = (size_t)nz * Mr * Nr * sizeof(float);
+  ensure(s.ws_oz, bytes_a + bytes_b + bytes_e + bytes_p);
+  char* base = s.ws_oz.p;
+  __nv_bfloat16* pA = (__nv_bfloat16*)base;
+  __nv_bfloat16* pB = (__nv_bfloat16*)(base + bytes_a);
+  int* exa = (int*)(base + bytes_a + bytes_b);
+  int* exb = exa + Mr;
+  float* part = (float*)(base + bytes_a + bytes_b + bytes_e);
+
+  // timed as its own family: the work is the real BF16 tensor-core GEMM of
+  // all slice pairs (2 Mr Nr Kr per pair)
+  TimedScope ts(s, KF_GEMM_OZ, st, 2.0 * OZ_PAIRS * (double)Mr * Nr * (double)seg,
+                2.0 * OZ_PAIRS * ((double)Mr + Nr) * seg + 8.0 * nz * (double)Mr * Nr);
+  // slices of op(A) and B
+  if (conjA) {
+    k_oz_colexp<<<M, 256, 0, st>>>(A, lda, K, exa);
+    PWH_LAUNCH_CHECK();
+    k_oz_slice_cols<<<dim3((unsigned)((seg + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg, exa,
+                                                                            pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_oz_colexp<<<N, 256, 0, st>>>(B, ldb, K, exb);
+    PWH_LAUNCH_CHECK();
+    k_oz_slice_cols<<<dim3((unsigned)((seg + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg, exb,
+                                                                            pB, pitch);
+    PWH_LAUNCH_CHECK();
+  } else {
+    k_oz_rowexp<<<(M + 255) / 256, 256, 0, st>>>(A, lda, M, K, exa);
+    PWH_LAUNCH_CHECK();
+    k_oz_slice_rows<<<dim3((M + 31) / 32, (unsigned)((seg / 2 + 31) / 32)), 256, 0, st>>>(
+        A, lda, M, K, (int)seg, exa, pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_oz_colexp_b2<<<N, 256, 0, st>>>(B, ldb, K, exb);
+    PWH_LAUNCH_CHECK();
+    k_oz_slice_b2<<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+                                                                              exb, pB, pitch);
+    PWH_LAUNCH_CHECK();
+  }
+  // every slice pair, every K chunk: exact FP32 partials on the tensor cores
+  CUtensorMap ma = make_map(pA, Mr, pitch, pitch, TC_BM);
+  CUtensorMap mb = make_map(pB, Nr, pitch, pitch, TC_BN);
+  TcArgs a{};
+  a.M = (int)Mr;
+  a.N = (int)Nr;
+  a.kb_seg = kb_seg;
+  a.terms = OZ_PAIRS;
+  a.kb_per_split = kbps;
+  a.part = part;
+  a.err = device_error_word(s);
+  a.oz = 1;
+  for (int p = 0; p < OZ_PAIRS; ++p) {
+    a.oz_a[p] = pa[p];
+    a.oz_b[p] = pb[p];
+  }
+  dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), nz);
+  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  PWH_LAUNCH_CHECK();
+  const int64_t tot = (int64_t)M * N;
+  if (conjA)
+    k_oz_reduce_cj<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nz, nchunk, M, N, exa, exb,
+                                                                  rowscale, alpha, beta, C, ldc);
+  else
+    k_oz_reduce_nn<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nz, nchunk, M, N, exa, exb,
+                                                                  rowscale, alpha, beta, C, ldc);
+  PWH_LAUNCH_CHECK();
 }
 
 }  // namespace pwh

@@ -28,7 +28,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 const char* const kKernelFamilyName[KF_COUNT] = {
     "fft_z_inverse_fp64", "fft_plane_fp64", "fft_z_forward_fp64", "fft_z_inverse_fp32",
     "fft_plane_fp32", "fft_z_forward_fp32", "tc_gemm_becp", "tc_gemm_backproj", "cgemm_fp64",
-    "cgemm_fp32", "jacobi_fp64", "cholqr_fp64", "jacobi_fp32"};
+    "cgemm_fp32", "jacobi_fp64", "cholqr_fp64", "jacobi_fp32", "zgemm_fp64_tc"};
 
 cudaEvent_t KernelTimer::get() {
   if (!pool.empty()) {
@@ -79,7 +79,7 @@ System::~System() {
                   d_stick_y, d_col_x, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
-                  ws_tc.p, d_err, d_shell, d_Tshell, d_mlp};
+                  ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }

@@ -1,7 +1,8 @@
 """The eigensolver's complex GEMM (pwh_subspace_gemm) against numpy complex128
 products: every tile shape (widths N from 1 to 200 select different tiles),
 op(A) = A and A^H, ragged M and K, a long split-K reduction (K = 34,265, the
-plane-wave count of the medium cell), K = 0, alpha/beta combinations.  Bars:
+plane-wave count of the medium cell), K = 0, alpha/beta combinations, and the
+large FP64 products that run on the tensor cores as integer slices.  Bars:
 FP64 arithmetic max|C - C_ref| <= 4e-15 sqrt(K) max|A| max|B| (plus
 |beta| |C0| rounding); FP32 arithmetic 4e-7 sqrt(K) max|A| max|B|."""
 import numpy as np
@@ -26,7 +27,10 @@ def cplx(rng, *shape):
 
 SHAPES = [(63, 1, 17), (129, 5, 40), (300, 8, 33), (257, 9, 100), (64, 16, 64), (100, 17, 7),
           (513, 32, 129), (77, 33, 250), (128, 64, 16), (130, 65, 64), (384, 128, 384),
-          (1000, 200, 31), (384, 96, 34265), (1, 1, 1), (5, 3, 0)]
+          (1000, 200, 31), (384, 96, 34265), (1, 1, 1), (5, 3, 0),
+          # FP64 products of >= 2e8 flops run as exact integer slice products on
+          # the tensor cores: long and short K, padded chunks, narrow outputs
+          (34265, 128, 384), (5000, 40, 1200), (3000, 7, 2000), (576, 33, 34265)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
