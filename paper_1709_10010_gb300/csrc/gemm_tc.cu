@@ -566,7 +566,8 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
 // operand (after the complex interleaving of the projector GEMM above) gets
 // the exponent e_r with max|x_r| < 2^e_r and is written as
 //     x = 2^e_r sum_{s < OZ_S} a_s 2^(-7 - 8 s),   a_s integers, |a_s| <= 128,
-// which BF16 holds exactly.  A product a_s b_t is at most 2^14 and a sum of
+// which BF16 holds exactly (balanced base-256 digits of the row-scaled value
+// as an integer).  A product a_s b_t is at most 2^14 and a sum of
 // 1024 of them at most 2^24, so every FP32 partial of a 1024-wide K chunk is an
 // exact integer.  The partials of the pairs with s + t <= OZ_G are summed in
 // int64 by weight 2^(-8(s+t)) and scaled once in FP64.  Dropped terms and
@@ -577,37 +578,54 @@ constexpr int OZ_PAIRS = (OZ_S * (OZ_S + 1)) / 2;  // pairs with s + t <= OZ_G
 static_assert(OZ_PAIRS <= 32, "pair table");
 __constant__ unsigned char c_oz_g[32];            // s + t of pair p
 
-__device__ __forceinline__ int oz_exp(double mx) {
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);
-  return e;  // mx < 2^e
+// Slicing works on the IEEE bit patterns with integer arithmetic only (the
+// FP64 pipe of this GPU would make it the slowest step).  |x| as an unsigned
+// integer orders like |x|, so row maxima are integer maxima of these keys.
+__device__ __forceinline__ unsigned long long oz_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
-// the OZ_S integer slices of x for exponent e, as BF16
+// exponent e with |x| < 2^e for the largest key of a row (0 for a zero row)
+__device__ __forceinline__ int oz_exp_of_key(unsigned long long k) {
+  if (k == 0) return 0;
+  const int eb = (int)(k >> 52);
+  return eb ? eb - 1022 : -1021;  // frexp exponent; subnormals lie below 2^-1022
+}
+// The OZ_S balanced base-256 digits of X = round(x 2^(55 - e)), |X| < 2^55:
+// x = 2^e sum_s a_s 2^(-7 - 8 s) up to 2^(e - 56), |a_s| <= 128, as BF16.
 __device__ __forceinline__ void oz_split(double x, int e, __nv_bfloat16* a) {
-  double r = ldexp(x, 7 - e);  // |r| < 128
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long m = (bits & 0xfffffffffffffull) | (eb ? (1ull << 52) : 0ull);
+  const int sh = (eb ? eb : 1) - 1075 + 55 - e;  // X = m 2^sh
+  long long X;
+  if (sh >= 0) X = (long long)(m << sh);
+  else if (sh > -64) X = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else X = 0;
+  if (bits >> 63) X = -X;
 #pragma unroll
-  for (int s = 0; s < OZ_S; ++s) {
-    const double q = rint(r);
-    a[s] = __float2bfloat16_rn((float)q);
-    r = (r - q) * 256.0;
+  for (int s = OZ_S - 1; s > 0; --s) {
+    const int d = (int)((X + 128) & 255) - 128;
+    a[s] = __int2bfloat16_rn(d);
+    X = (X - d) >> 8;
   }
+  a[0] = __int2bfloat16_rn((int)X);
 }
 
 // Exponents of the rows 2j (real parts) and 2j+1 (imaginary parts) of the
 // interleaved operand whose row pair j is column j of X (K x J, ld): one block
 // per column.
 __global__ void k_oz_colexp(const double2* __restrict__ X, int64_t ld, int K, int* __restrict__ ex) {
-  __shared__ double red[2][32];
+  __shared__ unsigned long long red[2][32];
   const int j = blockIdx.x;
-  double mr = 0.0, mi = 0.0;
+  unsigned long long mr = 0, mi = 0;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const double2 v = X[(size_t)j * ld + k];
-    mr = fmax(mr, fabs(v.x));
-    mi = fmax(mi, fabs(v.y));
+    mr = max(mr, oz_key(v.x));
+    mi = max(mi, oz_key(v.y));
   }
   for (int o = 16; o > 0; o >>= 1) {
-    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
-    mi = fmax(mi, __shfl_xor_sync(0xffffffffu, mi, o));
+    mr = max(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mi = max(mi, __shfl_xor_sync(0xffffffffu, mi, o));
   }
   if ((threadIdx.x & 31) == 0) {
     red[0][threadIdx.x >> 5] = mr;
@@ -616,11 +634,11 @@ __global__ void k_oz_colexp(const double2* __restrict__ X, int64_t ld, int K, in
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      mr = fmax(mr, red[0][w]);
-      mi = fmax(mi, red[1][w]);
+      mr = max(mr, red[0][w]);
+      mi = max(mi, red[1][w]);
     }
-    ex[2 * j] = oz_exp(mr);
-    ex[2 * j + 1] = oz_exp(mi);
+    ex[2 * j] = oz_exp_of_key(mr);
+    ex[2 * j + 1] = oz_exp_of_key(mi);
   }
 }
 // Slices of that operand: row 2j+c, segment s holds a_s of (Re, Im) X[k][j]
@@ -650,12 +668,12 @@ __global__ void k_oz_rowexp(const double2* __restrict__ A, int64_t ld, int M, in
                             int* __restrict__ ex) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   for (int k = 0; k < K; ++k) {
     const double2 v = A[(size_t)k * ld + m];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    mx = max(mx, max(oz_key(v.x), oz_key(v.y)));
   }
-  ex[m] = oz_exp(mx);
+  ex[m] = oz_exp_of_key(mx);
 }
 // Slices of A2: row m, segment s, column 2k+c (zero for 2K <= 2k+c < seg);
 // 32 x 32 tiles transposed through shared memory.
@@ -696,19 +714,19 @@ __global__ void k_oz_slice_rows(const double2* __restrict__ A, int64_t ld, int M
 // max(|Re|, |Im|) over column n: one block per column.
 __global__ void k_oz_colexp_b2(const double2* __restrict__ B, int64_t ld, int K,
                                int* __restrict__ ex) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const int n = blockIdx.x;
-  double mx = 0.0;
+  unsigned long long mx = 0;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     const double2 v = B[(size_t)n * ld + k];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    mx = max(mx, max(oz_key(v.x), oz_key(v.y)));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
-    ex[2 * n] = ex[2 * n + 1] = oz_exp(mx);
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, red[w]);
+    ex[2 * n] = ex[2 * n + 1] = oz_exp_of_key(mx);
   }
 }
 __global__ void k_oz_slice_b2(const double2* __restrict__ B, int64_t ld, int K, int seg,
@@ -742,7 +760,7 @@ __global__ void k_oz_slice_b2(const double2* __restrict__ B, int64_t ld, int K, 
 struct OzAcc {
   long long hi = 0, lo = 0;
   __device__ __forceinline__ void add(float v, int g) {
-    const long long i = __float2ll_rn(v);
+    const long long i = __float2int_rn(v);  // an exact integer, |v| <= 2^24
     if (g <= 2) hi += i * (1ll << (8 * (2 - g)));
     else lo += i * (1ll << (8 * (OZ_G - g)));
   }
