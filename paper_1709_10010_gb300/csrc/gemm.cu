@@ -211,10 +211,12 @@ static void cgemm_launch(System& s, bool conjA, int M, int N, int K, cx<TS> alph
   // split the reduction when the output tiles alone fill less than one wave
   // (into about two blocks per SM, chunks of at least 32: small square
   // products such as the eigensolver's n x n x n ones still spread out)
+  // (the partials of a split stay below 64 MB)
   int nsplit = 1;
   if (tiles < 152 && K > 2 * BK) {
     nsplit = std::min((2 * 152 + tiles - 1) / tiles, std::max(1, K / 32));
-    nsplit = std::max(1, std::min(nsplit, 64));
+    const int64_t cap = std::max<int64_t>(1, ((int64_t)64 << 20) / ((int64_t)M * N * (int64_t)sizeof(cx<TS>)));
+    nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(nsplit, cap));
   }
   int kchunk = (K + nsplit - 1) / nsplit;
   kchunk = ((kchunk + BK - 1) / BK) * BK;
@@ -262,8 +264,12 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
       cgemm_launch<TS, T, 128, 128, 8, 8, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
     else if (N > 32)
       cgemm_launch<TS, T, 128, 64, 8, 4, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
+    else if (N > 16 && M <= 128)
+      cgemm_launch<TS, T, 128, 32, 4, 4, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
     else if (N > 16)
       cgemm_launch<TS, T, 256, 32, 8, 4, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
+    else if (M <= 128)
+      cgemm_launch<TS, T, 128, 16, 4, 2, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
     else
       cgemm_launch<TS, T, 256, 16, 8, 2, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
   } else {

@@ -185,7 +185,11 @@ __global__ void __launch_bounds__(128, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
   const int kb_total = args.terms * args.kb_seg;
-  const int kb0 = blockIdx.z * args.kb_per_split;
+  // sliced operands: z = chunk * pairs + pair, so that the pairs of one K chunk
+  // (which share operand slices) run close together and hit in L2
+  const int kb0 = args.oz ? (int)(blockIdx.z % args.terms) * args.kb_seg +
+                                (int)(blockIdx.z / args.terms) * args.kb_per_split
+                          : (int)blockIdx.z * args.kb_per_split;
   const int nkb = max(0, min(kb_total, kb0 + args.kb_per_split) - kb0);
 
   if (threadIdx.x == 0) {
@@ -759,8 +763,8 @@ __global__ void k_oz_slice_b2(const double2* __restrict__ B, int64_t ld, int K, 
 // 2^(e - 14) (hi 2^-16 + lo 2^-(8 OZ_G)).
 struct OzAcc {
   long long hi = 0, lo = 0;
-  __device__ __forceinline__ void add(float v, int g) {
-    const long long i = __float2int_rn(v);  // an exact integer, |v| <= 2^24
+  // i: a sum of exact integer partials (each |v| <= 2^24) of weight 2^(-8g)
+  __device__ __forceinline__ void add_int(long long i, int g) {
     if (g <= 2) hi += i * (1ll << (8 * (2 - g)));
     else lo += i * (1ll << (8 * (OZ_G - g)));
   }
@@ -771,7 +775,7 @@ struct OzAcc {
 
 // op(A) = A^H: complex (m, n) from the four real products of rows 2m, 2m+1 and
 // columns 2n, 2n+1 (Re = C[2m][2n] + C[2m+1][2n+1], Im = C[2m][2n+1] -
-// C[2m+1][2n]); part[z][n'][m'] with M' = 2M, N' = 2N, z = pair * nchunk + chunk.
+// C[2m+1][2n]); part[z][n'][m'] with M' = 2M, N' = 2N, z = chunk * pairs + pair.
 __global__ void k_oz_reduce_cj(const float* __restrict__ part, int nz, int nchunk, int M, int N,
                                const int* __restrict__ exa, const int* __restrict__ exb,
                                const double* __restrict__ rowscale, double2 alpha, double2 beta,
@@ -781,15 +785,43 @@ __global__ void k_oz_reduce_cj(const float* __restrict__ part, int nz, int nchun
   const int m = (int)(t % M), n = (int)(t / M);
   const int64_t Mr = 2 * (int64_t)M, plane = Mr * 2 * (int64_t)N;
   OzAcc q00, q10, q01, q11;
-  for (int z = 0; z < nz; ++z) {
-    const int g = c_oz_g[z / nchunk];
-    const float* pz = part + (size_t)z * plane;
-    const float2 c0 = *(const float2*)(pz + (size_t)(2 * n) * Mr + 2 * m);      // (2m,2n), (2m+1,2n)
-    const float2 c1 = *(const float2*)(pz + (size_t)(2 * n + 1) * Mr + 2 * m);  // (2m,2n+1), (2m+1,2n+1)
-    q00.add(c0.x, g);
-    q10.add(c0.y, g);
-    q01.add(c1.x, g);
-    q11.add(c1.y, g);
+  const float* p0 = part + (size_t)(2 * n) * Mr + 2 * m;      // (2m,2n), (2m+1,2n)
+  const float* p1 = part + (size_t)(2 * n + 1) * Mr + 2 * m;  // (2m,2n+1), (2m+1,2n+1)
+  const int npair = nz / nchunk;
+  for (int pr = 0; pr < npair; ++pr) {
+    const int g = c_oz_g[pr];
+    // the chunks of one pair share the weight: integer sums first, four
+    // partials in flight
+    long long s00 = 0, s10 = 0, s01 = 0, s11 = 0;
+    int c = 0;
+    for (; c + 3 < nchunk; c += 4) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t z = (size_t)(c + u) * npair + pr;
+        a[u] = *(const float2*)(p0 + z * plane);
+        b[u] = *(const float2*)(p1 + z * plane);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s00 += __float2int_rn(a[u].x);
+        s10 += __float2int_rn(a[u].y);
+        s01 += __float2int_rn(b[u].x);
+        s11 += __float2int_rn(b[u].y);
+      }
+    }
+    for (; c < nchunk; ++c) {
+      const size_t z = (size_t)c * npair + pr;
+      const float2 a = *(const float2*)(p0 + z * plane), b = *(const float2*)(p1 + z * plane);
+      s00 += __float2int_rn(a.x);
+      s10 += __float2int_rn(a.y);
+      s01 += __float2int_rn(b.x);
+      s11 += __float2int_rn(b.y);
+    }
+    q00.add_int(s00, g);
+    q10.add_int(s10, g);
+    q01.add_int(s01, g);
+    q11.add_int(s11, g);
   }
   const int ea0 = exa[2 * m], ea1 = exa[2 * m + 1], eb0 = exb[2 * n], eb1 = exb[2 * n + 1];
   double re = q00.value(ea0 + eb0) + q11.value(ea1 + eb1);
@@ -818,11 +850,18 @@ __global__ void k_oz_reduce_nn(const float* __restrict__ part, int nz, int nchun
   const int m = (int)(t % M), n = (int)(t / M);
   const int64_t plane = (int64_t)M * 2 * N;
   OzAcc qr, qi;
-  for (int z = 0; z < nz; ++z) {
-    const int g = c_oz_g[z / nchunk];
-    const float* pz = part + (size_t)z * plane;
-    qr.add(pz[(size_t)(2 * n) * M + m], g);
-    qi.add(pz[(size_t)(2 * n + 1) * M + m], g);
+  const float* p0 = part + (size_t)(2 * n) * M + m;
+  const float* p1 = p0 + M;
+  const int npair = nz / nchunk;
+  for (int pr = 0; pr < npair; ++pr) {
+    long long sr = 0, si = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      const size_t z = (size_t)c * npair + pr;
+      sr += __float2int_rn(p0[z * plane]);
+      si += __float2int_rn(p1[z * plane]);
+    }
+    qr.add_int(sr, c_oz_g[pr]);
+    qi.add_int(si, c_oz_g[pr]);
   }
   const int e = exa[m] + exb[2 * n];
   double re = qr.value(e), im = qi.value(e);

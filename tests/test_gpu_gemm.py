@@ -30,7 +30,9 @@ SHAPES = [(63, 1, 17), (129, 5, 40), (300, 8, 33), (257, 9, 100), (64, 16, 64), 
           (1000, 200, 31), (384, 96, 34265), (1, 1, 1), (5, 3, 0),
           # FP64 products of >= 2e8 flops run as exact integer slice products on
           # the tensor cores: long and short K, padded chunks, narrow outputs
-          (34265, 128, 384), (5000, 40, 1200), (3000, 7, 2000), (576, 33, 34265)]
+          (34265, 128, 384), (5000, 40, 1200), (3000, 7, 2000), (576, 33, 34265),
+          # narrow inner products of few rows (the Jacobi-Davidson projections)
+          (128, 9, 34265), (100, 20, 5000)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
