@@ -442,31 +442,39 @@ __global__ void __launch_bounds__(1024) k_cholqr(const double2* __restrict__ S, 
     *kk = c;
   }
   __syncthreads();
-  const int kp = nkeep_s;
+  // L <- L^-1 in place on the kept set, columns from the last: for i > j,
+  // (L^-1)_ij = -(1/L_jj) sum_{j < l <= i} (L^-1)_il L_lj, with the trailing
+  // block already inverted; the original column j is kept in col_s.  A warp
+  // per row i, lanes over l.
+  __shared__ cx<T> col_s[1024];
+  for (int j = k - 1; j >= 0; --j) {
+    if (!keep_s[j]) continue;
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
+      col_s[i] = keep_s[i] ? at(i, j) : mk<T>((T)0, (T)0);
+    __syncthreads();
+    const T djj = (T)1 / at(j, j).x;
+    for (int i = j + 1 + warp; i < k; i += nwarps) {
+      if (!keep_s[i]) continue;
+      cx<T> acc = mk<T>((T)0, (T)0);
+      for (int l = j + 1 + lane; l <= i; l += 32)
+        if (keep_s[l]) acc = add<T>(acc, mul<T>(at(i, l), col_s[l]));
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) at(i, j) = scl<T>(acc, -djj);
+    }
+    if (threadIdx.x == 0) at(j, j) = mk<T>(djj, (T)0);
+    __syncthreads();
+  }
+  // Tr = D^-1/2 L^-H: column rank(j), row i <= j holds conj((L^-1)_ji) / sqrt(S_ii)
   for (int t = threadIdx.x; t < k * k; t += blockDim.x) Tr[t] = make_double2(0.0, 0.0);
   __syncthreads();
-  // Tr = D^-1/2 L^-H: column rank(j) solves L^H x = e_j by back substitution
-  // (a thread per column, in the compute precision)
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    if (!keep_s[j]) continue;
-    double2* x = Tr + (size_t)rank_s[j] * k;
-    for (int i = j; i >= 0; --i) {
-      if (!keep_s[i]) continue;
-      cx<T> v = mk<T>(i == j ? (T)1 : (T)0, (T)0);
-      for (int l = i + 1; l <= j; ++l)
-        if (keep_s[l]) {
-          const cx<T> lli = at(l, i);  // (L^H)_{il} = conj(L_li)
-          const double2 xl = x[l];
-          v = sub<T>(v, mul<T>(mk<T>(lli.x, -lli.y), mk<T>((T)xl.x, (T)xl.y)));
-        }
-      const T rd = (T)1 / at(i, i).x;
-      x[i] = make_double2((double)(v.x * rd), (double)(v.y * rd));
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < k * kp; t += blockDim.x) {
-    const int i = t % k;
-    Tr[t] = scl<double>(Tr[t], dinv_s[i]);
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t % k, j = t / k;
+    if (i > j || !keep_s[i] || !keep_s[j]) continue;
+    const cx<T> v = at(j, i);
+    Tr[(size_t)rank_s[j] * k + i] = make_double2((double)v.x * dinv_s[i], -(double)v.y * dinv_s[i]);
   }
 }
 
@@ -702,14 +710,15 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {
 template <typename T>
 static void cholqr_launch(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
                           double piv_tol, double2* Tr, int* kk, cudaStream_t st) {
-  // the packed lower triangle in shared memory up to 200 KB (k = 160 in FP64,
-  // 226 in FP32), else in the global scratch
+  // the packed lower triangle in shared memory up to 192 KB (k = 156 in FP64,
+  // 221 in FP32; the kernel's static arrays take the rest), else in the
+  // global scratch
   const size_t tri = (size_t)k * (k + 1) / 2 * sizeof(cx<T>);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_cholqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(k_cholqr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024);
   });
-  if (tri <= 200 * 1024) {
+  if (tri <= 192 * 1024) {
     k_cholqr<T, true><<<1, 1024, tri, st>>>(S, k, t0, drop_rel, piv_tol, nullptr, Tr, kk);
   } else {
     ensure(w.chol, (size_t)k * k * sizeof(double2));

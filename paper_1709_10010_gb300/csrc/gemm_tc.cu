@@ -853,15 +853,24 @@ __global__ void k_oz_reduce_nn(const float* __restrict__ part, int nz, int nchun
   const float* p0 = part + (size_t)(2 * n) * M + m;
   const float* p1 = p0 + M;
   const int npair = nz / nchunk;
-  for (int pr = 0; pr < npair; ++pr) {
-    long long sr = 0, si = 0;
-    for (int c = 0; c < nchunk; ++c) {
-      const size_t z = (size_t)c * npair + pr;
-      sr += __float2int_rn(p0[z * plane]);
-      si += __float2int_rn(p1[z * plane]);
+  if (nchunk == 1) {
+    // one chunk: every pair's partial in flight together
+#pragma unroll 7
+    for (int pr = 0; pr < OZ_PAIRS; ++pr) {
+      qr.add_int(__float2int_rn(p0[(size_t)pr * plane]), c_oz_g[pr]);
+      qi.add_int(__float2int_rn(p1[(size_t)pr * plane]), c_oz_g[pr]);
     }
-    qr.add_int(sr, c_oz_g[pr]);
-    qi.add_int(si, c_oz_g[pr]);
+  } else {
+    for (int pr = 0; pr < npair; ++pr) {
+      long long sr = 0, si = 0;
+      for (int c = 0; c < nchunk; ++c) {
+        const size_t z = (size_t)c * npair + pr;
+        sr += __float2int_rn(p0[z * plane]);
+        si += __float2int_rn(p1[z * plane]);
+      }
+      qr.add_int(sr, c_oz_g[pr]);
+      qi.add_int(si, c_oz_g[pr]);
+    }
   }
   const int e = exa[m] + exb[2 * n];
   double re = qr.value(e), im = qi.value(e);
