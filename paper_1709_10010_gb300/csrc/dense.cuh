@@ -6,10 +6,12 @@ namespace pwh {
 
 struct DenseWs {
   DevBuf<char> jac, chol;
+  DevBuf<char> jlog;    // rotation log of the cluster Jacobi
   void* ctl = nullptr;  // barrier words and flags of the Jacobi launch
   ~DenseWs() {
     if (jac.p) cudaFree(jac.p);
     if (chol.p) cudaFree(chol.p);
+    if (jlog.p) cudaFree(jlog.p);
     if (ctl) cudaFree(ctl);
   }
 };
@@ -31,11 +33,16 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
 // FP32 stage of jacobi_eigh in one 16-CTA thread-block cluster with the matrix
 // in distributed shared memory (jacobi_dsm.cu): sweeps of the n x n Hermitian
 // A (FP64, ld lda) until max|A_ij| <= tol max|A_ii|; Q (ld ldq) receives the
-// eigenvectors (FP64), diag the final diagonal, info[1] the sweeps.  Returns
+// eigenvectors (FP64), diag the final diagonal, info[1] the sweeps, info[2]
+// the rounds; the rotations of every round go to a log in w (grown here once,
+// reserved by jacobi_reserve) from which a second kernel forms Q.  Returns
 // false, launching nothing, when n is outside its range or the cluster cannot
 // be resident.
-bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double tol, int max_sweeps,
-                      double2* Q, int64_t ldq, double* diag, int* info, cudaStream_t st);
+bool jacobi32_cluster(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
+                      int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
+                      cudaStream_t st);
+// Bytes of the rotation log of jacobi32_cluster for an n x n matrix.
+size_t jacobi32_log_bytes(int n, int max_sweeps);
 
 // Device words holding the number of FP64 / FP32 sweeps of the last jacobi_eigh.
 inline int* jacobi_sweeps_word(DenseWs& w) { return (int*)w.ctl + 9; }

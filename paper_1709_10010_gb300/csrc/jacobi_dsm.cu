@@ -50,16 +50,16 @@ constexpr int kDsmThreads = 1024;
 struct JdsmArgs {
   const double2* A;  // n x n Hermitian start (full), ld lda
   int64_t lda;
-  double2* Q;        // out: eigenvectors, column j for index j, ld ldq
-  int64_t ldq;
   double* diag;      // out: final diagonal (eigenvalue estimates), n
-  int* info;         // out: [0] = 0, [1] = sweeps used
+  int* info;         // out: [0] = 0, [1] = sweeps used, [2] = rounds logged
+  float4* log;       // out: rotations, round t pair k at [t P + k]: (s, c, p | q << 16)
+  int64_t log_rounds;  // capacity of log in rounds
   int n, np, P, PP, max_sweeps;
   float tol;
 };
 
 // shared-memory layout of one CTA, in this order:
-//   float2 colA[nbuf n], colQ[nbuf n]      column buffers, nbuf = 2 PP + 4 (the
+//   float2 colA[nbuf n]                    column buffers, nbuf = 2 PP + 4 (the
 //                                          last four: inboxes [parity][side])
 //   float4 rot[2][PP][2]                   published rotations of the own pairs,
 //                                          by round parity: (s, c, p | q << 16),
@@ -72,7 +72,7 @@ struct JdsmArgs {
 __host__ __device__ inline size_t jdsm_smem_bytes(int n, int P, int PP) {
   const size_t nbuf = 2 * (size_t)PP + 4;
   const int np = 2 * P;
-  return 2 * nbuf * n * sizeof(float2) + (4 * (size_t)PP + 2 * (size_t)P) * sizeof(float4) +
+  return nbuf * n * sizeof(float2) + (4 * (size_t)PP + 2 * (size_t)P) * sizeof(float4) +
          (size_t)(np + 66) * sizeof(float) + (size_t)(8 * PP) * sizeof(int);
 }
 
@@ -98,8 +98,7 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
   const int ibuf0 = 2 * PP;  // inbox buffer ibuf0 + 2 parity + side
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   float2* colA = (float2*)dsm;
-  float2* colQ = colA + (size_t)nbuf * n;
-  float4* rot = (float4*)(colQ + (size_t)nbuf * n);
+  float4* rot = (float4*)(colA + (size_t)nbuf * n);
   float4* allr = rot + 4 * PP;
   float* dg = (float*)(allr + 2 * P);
   float* red = dg + np;
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
   // Rotations of round r for the own pairs into rot[par]: A_pq from whichever
   // of the two columns is here (an arriving column is still in an inbox when
   // pending), the diagonal from the replicated copy.
-  auto publish = [&](int r, int par, bool pending) {
+  auto publish = [&](int r, int par, bool pending, int64_t tr) {
     for (int j = threadIdx.x; j < ns; j += blockDim.x) {
       int p = jd_player(pos_of(2 * j), r, np), q = jd_player(pos_of(2 * j + 1), r, np);
       int bp = bufof[2 * j], bq = bufof[2 * j + 1];
@@ -161,9 +160,11 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
           const float2 v = colA[(size_t)bp * n + q];
           apq = make_float2(v.x, -v.y);
         }
-        jacobi_rotation<float>(apq, dg[p], dg[q], c, sv);
+        jacobi_rotation_fast(apq, dg[p], dg[q], c, sv);
       }
-      rot[(par * PP + j) * 2] = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 16)));
+      const float4 r0 = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 16)));
+      rot[(par * PP + j) * 2] = r0;
+      if (tr < a.log_rounds) a.log[tr * P + k0 + j] = r0;
       rot[(par * PP + j) * 2 + 1] = make_float4(apq.x, apq.y, 0.f, 0.f);
     }
   };
@@ -173,15 +174,12 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
       const int b = bufof[in_slot[i]];
       const size_t src = (size_t)(ibuf0 + 2 * par + in_box[i]) * n;
       if (jd_player(pos_of(in_slot[i]), r, np) < n) {
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-          colA[(size_t)b * n + e] = colA[src + e];
-          colQ[(size_t)b * n + e] = colQ[src + e];
-        }
+        for (int e = threadIdx.x; e < n; e += blockDim.x) colA[(size_t)b * n + e] = colA[src + e];
       }
     }
   };
 
-  // ---- load: position x starts with index x; Q starts as the identity
+  // ---- load: position x starts with index x
   for (int s = threadIdx.x; s < nslot; s += blockDim.x) bufof[s] = s;
   for (int i = threadIdx.x; i < np; i += blockDim.x) dg[i] = i < n ? (float)a.A[(size_t)i * a.lda + i].x : 0.f;
   for (int t = threadIdx.x; t < nslot * n; t += blockDim.x) {
@@ -190,18 +188,16 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
     if (pl < n) {
       const double2 v = a.A[(size_t)pl * a.lda + i];
       colA[(size_t)s * n + i] = make_float2((float)v.x, (float)v.y);
-      colQ[(size_t)s * n + i] = make_float2(i == pl ? 1.f : 0.f, 0.f);
     }
   }
   __syncthreads();
-  publish(0, 0, false);
+  publish(0, 0, false, 0);
   cluster.sync();
 
-  // warp tasks of the update: A in chunks of 64 row pairs, Q in chunks of 128
-  // rows, per own column pair; a warp's next task is nwarps further on
-  const int nchA = (P + 63) >> 6, nchQ = (n + 127) >> 7;
+  // warp tasks of the update: chunks of 64 row pairs per own column pair; a
+  // warp's next task is nwarps further on
+  const int nchA = (P + 63) >> 6;
   const int stepA_j = nwarps / nchA, stepA_c = nwarps - stepA_j * nchA;
-  const int stepQ_j = nwarps / nchQ, stepQ_c = nwarps - stepQ_j * nchQ;
   const float2 z = make_float2(0.f, 0.f);
   int sweep = 0, t = 0;  // t: rounds done (its parity picks the rotation table and inboxes)
   while (true) {
@@ -244,11 +240,11 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
       // (2) A <- J^H A J on the own columns: a warp task is one own column
       //     pair against 64 row pairs (two 2 x 2 blocks a lane); the pair
       //     element of an own pair becomes zero, its diagonal lives in dg.
-      //     Q <- Q J: a warp task is one own column pair, 128 rows (four a
-      //     lane).  Tasks are dealt to warps round-robin: (j, chunk) advance
-      //     by nwarps without division.
+      //     Tasks are dealt to warps round-robin: (j, chunk) advance by
+      //     nwarps without division.  (Q is accumulated afterwards from the
+      //     rotation log, k_jacobi_qlog.)
       {
-        const int ntA = ns * nchA, ntQ = ns * nchQ;
+        const int ntA = ns * nchA;
         int j = warp / nchA, c = warp - (warp / nchA) * nchA;
         for (int task = warp; task < ntA; task += nwarps) {
           const float4 Rl = allr[2 * (k0 + j)];
@@ -290,34 +286,6 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
           j += stepA_j;
           if (c >= nchA) {
             c -= nchA;
-            ++j;
-          }
-        }
-        int task = warp - ntA % nwarps;
-        if (task < 0) task += nwarps;
-        j = task / nchQ;
-        c = task - j * nchQ;
-        for (; task < ntQ; task += nwarps) {
-          if (own[PP + j] < n) {  // a pair with the dummy index: identity
-            const float4 Rl = allr[2 * (k0 + j)];
-            const float cl = Rl.z;
-            const float2 sl = make_float2(Rl.x, Rl.y), msl = make_float2(-sl.x, sl.y);
-            float2* qp = colQ + (size_t)own[2 * PP + j] * n;
-            float2* qq = colQ + (size_t)own[3 * PP + j] * n;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const int i = c * 128 + h * 32 + lane;
-              if (i < n) {
-                const float2 q0 = qp[i], q1 = qq[i];
-                qp[i] = add<float>(scl<float>(q0, cl), mul<float>(q1, msl));
-                qq[i] = add<float>(mul<float>(q0, sl), scl<float>(q1, cl));
-              }
-            }
-          }
-          c += stepQ_c;
-          j += stepQ_j;
-          if (c >= nchQ) {
-            c -= nchQ;
             ++j;
           }
         }
@@ -381,18 +349,14 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
         const int b = bufof[out_slot[o]];
         const size_t dst = (size_t)(ibuf0 + 2 * (par ^ 1) + out_box[o]) * n;
         float2* rA = cluster.map_shared_rank(colA, out_cta[o]) + dst;
-        float2* rQ = cluster.map_shared_rank(colQ, out_cta[o]) + dst;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          rA[i] = colA[(size_t)b * n + i];
-          rQ[i] = colQ[(size_t)b * n + i];
-        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) rA[i] = colA[(size_t)b * n + i];
       }
       __syncthreads();
       {
         int* u = bufof; bufof = nbufof; nbufof = u;
       }
       // (6) rotations of the next round (arrivals still in their inboxes)
-      publish(r + 1 == np - 1 ? 0 : r + 1, par ^ 1, true);
+      publish(r + 1 == np - 1 ? 0 : r + 1, par ^ 1, true, (int64_t)t + 1);
       cluster.sync();
     }
     ++sweep;
@@ -405,28 +369,73 @@ __global__ void __launch_bounds__(kDsmThreads, 1) k_jacobi_dsm(JdsmArgs a) {
     if (goff <= a.tol * fmaxf(gdm, 1e-30f) || sweep >= a.max_sweeps) break;
   }
 
-  // ---- results (after whole sweeps every index is back at its own position)
-  land(0, t & 1);
-  __syncthreads();
-  for (int e = threadIdx.x; e < nslot * n; e += blockDim.x) {
-    const int sl = e / n, i = e - sl * n;
-    const int pl = pos_of(sl);
-    if (pl >= n) continue;
-    const float2 v = colQ[(size_t)bufof[sl] * n + i];
-    a.Q[(size_t)pl * a.ldq + i] = make_double2((double)v.x, (double)v.y);
-  }
+  // ---- results: the diagonal, the sweeps and the rounds logged (t)
   if (me == 0) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) a.diag[i] = (double)dg[i];
     if (threadIdx.x == 0) {
       a.info[0] = 0;
       a.info[1] = sweep;
+      a.info[2] = t;
     }
   }
   cluster.sync();
 }
 
-bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double tol, int max_sweeps,
-                      double2* Q, int64_t ldq, double* diag, int* info, cudaStream_t st) {
+// Q = J_0 J_1 ... J_{R-1} from the rotation log (R = info[2] rounds): rows of
+// Q evolve independently, so each block takes kQlogRows rows in shared memory
+// (starting as rows of the identity) and applies every round to them in
+// order, a thread per (row, pair); the next round's rotation is fetched
+// before the barrier that closes the current one.
+constexpr int kQlogRows = 4;
+__global__ void __launch_bounds__(1024) k_jacobi_qlog(const float4* __restrict__ log,
+                                                      const int* __restrict__ info, int n, int P,
+                                                      double2* __restrict__ Q, int64_t ldq) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  float2* qs = (float2*)qsm;  // [kQlogRows][n]
+  const int i0 = blockIdx.x * kQlogRows;
+  const int nr = min(kQlogRows, n - i0);
+  for (int t = threadIdx.x; t < kQlogRows * n; t += blockDim.x) {
+    const int r = t / n, c = t - r * n;
+    qs[t] = make_float2((r < nr && i0 + r == c) ? 1.f : 0.f, 0.f);
+  }
+  const int R = info[2];
+  const int it = threadIdx.x;  // one (row, pair) item a thread
+  const bool active = it < kQlogRows * P;
+  const int k = active ? it % P : 0, r = active ? it / P : 0;
+  float4 rc = (active && R > 0) ? log[k] : make_float4(0.f, 0.f, 1.f, 0.f);
+  __syncthreads();
+  for (int rd = 0; rd < R; ++rd) {
+    const float4 cur = rc;
+    if (active && rd + 1 < R) rc = log[(size_t)(rd + 1) * P + k];
+    if (active && r < nr) {
+      const int pq = __float_as_int(cur.w);
+      const int p = pq & 0xffff, q = pq >> 16;
+      if (q < n) {
+        const float c = cur.z;
+        const float2 sv = make_float2(cur.x, cur.y);
+        float2* row = qs + (size_t)r * n;
+        const float2 q0 = row[p], q1 = row[q];
+        row[p] = add<float>(scl<float>(q0, c), mul<float>(q1, make_float2(-sv.x, sv.y)));
+        row[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
+    const int c = t / nr, rr = t - c * nr;
+    const float2 v = qs[(size_t)rr * n + c];
+    Q[(size_t)c * ldq + i0 + rr] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+size_t jacobi32_log_bytes(int n, int max_sweeps) {
+  const int np = n + (n & 1);
+  return (size_t)max_sweeps * (np - 1) * (np / 2) * sizeof(float4);
+}
+
+bool jacobi32_cluster(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
+                      int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
+                      cudaStream_t st) {
   (void)s;
   // PWH_JACOBI_GLOBAL=1 in the environment selects the global-memory kernel
   static const bool off = [] {
@@ -437,7 +446,7 @@ bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double to
   const int np = n + (n & 1), P = np / 2;
   const int PP = (P + kDsmCluster - 1) / kDsmCluster;
   const size_t smem = jdsm_smem_bytes(n, P, PP);
-  if (smem > 220 * 1024) return false;
+  if (smem > 220 * 1024 || n > 512) return false;  // k_jacobi_qlog: a thread per (row, pair)
   static std::once_flag attr_once;
   static bool attr_ok = false;
   std::call_once(attr_once, [] {
@@ -477,11 +486,22 @@ bool jacobi32_cluster(System& s, const double2* A, int64_t lda, int n, double to
       fits_upto = smem;
     }
   }
+  ensure(w.jlog, jacobi32_log_bytes(n, max_sweeps));
   JdsmArgs a;
-  a.A = A; a.lda = lda; a.Q = Q; a.ldq = ldq; a.diag = diag; a.info = info;
+  a.A = A; a.lda = lda; a.diag = diag; a.info = info;
+  a.log = (float4*)w.jlog.p;
+  a.log_rounds = (int64_t)max_sweeps * (np - 1);
   a.n = n; a.np = np; a.P = P; a.PP = PP; a.max_sweeps = max_sweeps; a.tol = (float)tol;
   PWH_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_dsm, a));
   note_launch();
+  // eigenvectors from the logged rotations, rows spread over the GPU
+  static std::once_flag q_once;
+  std::call_once(q_once, [] {
+    cudaFuncSetAttribute(k_jacobi_qlog, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  k_jacobi_qlog<<<(n + kQlogRows - 1) / kQlogRows, 1024, (size_t)kQlogRows * n * sizeof(float2), st>>>(
+      a.log, info, n, P, Q, ldq);
+  PWH_LAUNCH_CHECK();
   return true;
 }
 

@@ -36,6 +36,41 @@ __device__ __forceinline__ void jacobi_rotation(cx<T> apq, T app, T aqq, T& c, c
   s = mk<T>(e * ux, e * uy);
 }
 
+// The same rotation from approximate reciprocals and square roots (a few
+// MUFU operations instead of IEEE divisions): c^2 + |s|^2 = 1 to a few FP32
+// roundings, for the FP32 stage whose basis is re-orthonormalised afterwards.
+// Off-diagonal elements below 1e-30 take the exact path (no reciprocal of a
+// tiny or subnormal value).
+__device__ __forceinline__ void jacobi_rotation_fast(float2 apq, float app, float aqq, float& c,
+                                                     float2& s) {
+  const float mx = fmaxf(fabsf(apq.x), fabsf(apq.y));
+  if (!(mx >= 1e-30f)) {
+    jacobi_rotation<float>(apq, app, aqq, c, s);
+    return;
+  }
+  c = 1.f;
+  s = make_float2(0.f, 0.f);
+  const float r = __fdividef(1.f, mx);
+  const float ux = apq.x * r, uy = apq.y * r;
+  const float h2 = ux * ux + uy * uy;  // in [1, 2]
+  const float ih = rsqrtf(h2);
+  const float g = mx * (h2 * ih);
+  const bool negligible = (fabsf(app) + 100.f * g == fabsf(app)) &&
+                          (fabsf(aqq) + 100.f * g == fabsf(aqq));
+  if (negligible) return;
+  const float zeta = (aqq - app) * (0.5f * r * ih);
+  float t;
+  if (fabsf(zeta) > 1e9f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float w = 1.f + zeta * zeta;
+    t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + w * rsqrtf(w));
+  }
+  c = rsqrtf(1.f + t * t);
+  const float e = t * c * ih;
+  s = make_float2(e * ux, e * uy);
+}
+
 // The 2 x 2 block of J^H A J on rows (pk, qk) and columns (pl, ql), from the
 // block a00 = A[pk][pl], a01 = A[pk][ql], a10 = A[qk][pl], a11 = A[qk][ql]
 // and the rotations (ck, sk) of the row pair and (cl, sl) of the column pair.
