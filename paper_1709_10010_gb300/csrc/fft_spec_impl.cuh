@@ -1,9 +1,9 @@
 // FFT passes specialised at compile time for cubic boxes of common sizes.
-// Same algorithm, data layout and tables as the generic passes in fft.cu
-// (k_zinv, k_plane, k_zfwd): the radix plan of every length is a constant, so
-// the stage loops unroll and every index division is by a constant.  The
-// radix order (4s, 2s, 3s, 5s) matches the host plan, hence the host's
-// twiddle and digit-reversal tables serve both.
+// Same data layout and twiddle table as the generic passes in fft.cu
+// (k_zinv, k_plane, k_zfwd), but every 1D transform is a two-pass four-step
+// FFT in natural order whose small DFTs run in registers with compile-time
+// indices (no digit-reversed scatter, two shared-memory passes per
+// transform instead of one per radix stage).
 #pragma once
 #include <mutex>
 
@@ -60,6 +60,134 @@ __device__ __forceinline__ void fft_stages(cx<T>* data, int nfft, int fstride, c
   }
 }
 
+// ---- natural-order transforms: N = N1 N2 in two passes (the four-step
+// factorisation), each pass a batch of small DFTs held in registers.
+//   pass 1: for each n2 < N2, the N1-point DFT over x[N2 n1 + n2], times
+//           w_N^(n2 k1), back to x[N2 k1 + n2];
+//   pass 2: for each k1 < N1, the N2-point DFT over x[N2 k1 + n2], to
+//           x[k1 + N1 k2].
+// The small DFTs are the same mixed-radix DIT (input in the digit-reversed
+// order of make_cplan, a free renaming of registers) with every index a
+// compile-time constant; twiddles come from the length-N table tw.
+struct RevTab {
+  int v[32];
+};
+// position q of the DIT input holds element v[q] (digits of q, recombined
+// in reverse radix order)
+constexpr RevTab make_rev(int n) {
+  const CPlan p = make_cplan(n);
+  RevTab t{};
+  for (int q = 0; q < n; ++q) {
+    int rem = q, dig[kMaxStages] = {};
+    for (int s = 0; s < p.ns; ++s) {
+      dig[s] = rem % p.R[s];
+      rem /= p.R[s];
+    }
+    int acc = p.ns ? dig[0] : 0;
+    for (int s = 1; s < p.ns; ++s) acc = dig[s] + p.R[s] * acc;
+    t.v[q] = acc;
+  }
+  return t;
+}
+// a factor N1 of N near sqrt(N) with N1, N / N1 <= 16
+constexpr int fft_factor(int n) {
+  int best = 1;
+  for (int d = 2; d <= 16; ++d)
+    if (n % d == 0 && n / d <= 16 && (best == 1 || (d <= n / d && d > best))) best = d;
+  return best;
+}
+
+template <typename T, int R, bool INV, int NT, int S>
+__device__ __forceinline__ void reg_stages(cx<T>* a, const cx<T>* tw) {
+  constexpr CPlan P = make_cplan(R);
+  if constexpr (S < P.ns) {
+    constexpr int Rs = P.R[S], M = P.M[S], L = P.L[S];
+    constexpr int twstep = NT / L;
+    const T sg = INV ? (T)1 : (T)-1;
+#pragma unroll
+    for (int g = 0; g < R / L; ++g)
+#pragma unroll
+      for (int k1 = 0; k1 < M; ++k1) {
+        cx<T> b[Rs];
+#pragma unroll
+        for (int q = 0; q < Rs; ++q) b[q] = a[g * L + k1 + q * M];
+        if (k1 != 0) {
+#pragma unroll
+          for (int q = 1; q < Rs; ++q) {
+            cx<T> w = tw[q * k1 * twstep];
+            w.y *= sg;
+            b[q] = mul<T>(b[q], w);
+          }
+        }
+        dft<T, Rs>(b, sg);
+#pragma unroll
+        for (int q = 0; q < Rs; ++q) a[g * L + k1 + q * M] = b[q];
+      }
+    reg_stages<T, R, INV, NT, S + 1>(a, tw);
+  }
+}
+// In-register DFT of length R (natural order in and out) with sign +1 (INV)
+// or -1; tw[t] = exp(2 pi i t / NT), R | NT.
+template <typename T, int R, bool INV, int NT>
+__device__ __forceinline__ void dft_reg(cx<T>* x, const cx<T>* tw) {
+  constexpr RevTab rv = make_rev(R);
+  cx<T> a[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) a[q] = x[rv.v[q]];
+  reg_stages<T, R, INV, NT, 0>(a, tw);
+#pragma unroll
+  for (int k = 0; k < R; ++k) x[k] = a[k];
+}
+
+// nfft transforms of length N in shared memory (transform f at data + f
+// fstride, unit stride), natural order in and out; all threads of the block;
+// ends with __syncthreads().
+template <typename T, bool INV, int N>
+__device__ __forceinline__ void fft_nat(cx<T>* data, int nfft, int fstride, const cx<T>* tw) {
+  constexpr int N1 = fft_factor(N), N2 = N / N1;
+  static_assert(N1 > 1 && N1 <= 16 && N2 <= 16, "factor");
+  const T sg = INV ? (T)1 : (T)-1;
+  for (int t = threadIdx.x; t < nfft * N2; t += blockDim.x) {
+    const int f = t / N2, n2 = t - f * N2;
+    cx<T>* xf = data + f * fstride;
+    cx<T> v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = xf[N2 * n1 + n2];
+    dft_reg<T, N1, INV, N>(v, tw);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) {
+      cx<T> w = tw[n2 * k1];
+      w.y *= sg;
+      v[k1] = mul<T>(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) xf[N2 * k1 + n2] = v[k1];
+  }
+  __syncthreads();
+  // pass 2 writes other positions than it reads: whole transforms per round,
+  // loads and stores separated by a barrier
+  const int per = blockDim.x / N1;
+  const int fl = threadIdx.x / N1, k1 = threadIdx.x - fl * N1;
+  for (int f0 = 0; f0 < nfft; f0 += per) {
+    const int f = f0 + fl;
+    const bool act = fl < per && f < nfft;
+    cx<T> w[N2];
+    if (act) {
+      const cx<T>* xf = data + f * fstride + N2 * k1;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) w[n2] = xf[n2];
+      dft_reg<T, N2, INV, N>(w, tw);
+    }
+    __syncthreads();
+    if (act) {
+      cx<T>* xf = data + f * fstride + k1;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) xf[N1 * k2] = w[k2];
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T> __device__ __forceinline__ cx<T> widen_from64(double2 z) {
   return mk<T>((T)z.x, (T)z.y);
 }
@@ -90,9 +218,9 @@ __global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, 
   const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
   const double2* src = psi + (size_t)b * ldp;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-    buf[(stick_of[i] - s0) * ld + irev[zpos[i]]] = widen_from64<T>(src[i]);
+    buf[(stick_of[i] - s0) * ld + zpos[i]] = widen_from64<T>(src[i]);
   __syncthreads();
-  fft_stages<T, true, N, 0>(buf, ns, ld, tw);
+  fft_nat<T, true, N>(buf, ns, ld, tw);
   cx<T>* dst = W + (size_t)b * wband;
   for (int t = threadIdx.x; t < N * spb; t += blockDim.x) {
     const int z = t / spb, s = t - z * spb;
@@ -123,9 +251,9 @@ __global__ void __launch_bounds__(512) ks_plane(cx<T>* __restrict__ W, int64_t w
   for (int t = threadIdx.x; t < ncols * ld; t += blockDim.x) C[t] = mk<T>(0, 0);
   __syncthreads();
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
-    C[stick_col[s] * ld + irev[stick_y[s]]] = plane[s];
+    C[stick_col[s] * ld + stick_y[s]] = plane[s];
   __syncthreads();
-  fft_stages<T, true, N, 0>(C, ncols, ld, tw);
+  fft_nat<T, true, N>(C, ncols, ld, tw);
   const T* Vz = V + (size_t)z * N * N;
   for (int y0 = 0; y0 < N; y0 += rows) {
     const int nr = min(rows, N - y0);
@@ -133,25 +261,25 @@ __global__ void __launch_bounds__(512) ks_plane(cx<T>* __restrict__ W, int64_t w
     __syncthreads();
     for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
       const int r = t / ncols, c = t - r * ncols;
-      Rw[r * ld + irev[col_x[c]]] = C[c * ld + y0 + r];
+      Rw[r * ld + col_x[c]] = C[c * ld + y0 + r];
     }
     __syncthreads();
-    fft_stages<T, true, N, 0>(Rw, nr, ld, tw);
+    fft_nat<T, true, N>(Rw, nr, ld, tw);
     for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
       const int r = t / N, x = t - r * N;
       Rw[r * ld + x] = scl<T>(Rw[r * ld + x], Vz[(size_t)(y0 + r) * N + x]);
     }
     __syncthreads();
-    fft_stages<T, false, N, 0>(Rw, nr, ld, tw);
+    fft_nat<T, false, N>(Rw, nr, ld, tw);
     for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
       const int r = t / ncols, c = t - r * ncols;
-      C[c * ld + y0 + r] = Rw[r * ld + irev[col_x[c]]];
+      C[c * ld + y0 + r] = Rw[r * ld + col_x[c]];
     }
     __syncthreads();
   }
-  fft_stages<T, false, N, 0>(C, ncols, ld, tw);
+  fft_nat<T, false, N>(C, ncols, ld, tw);
   for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
-    plane[s] = C[stick_col[s] * ld + irev[stick_y[s]]];
+    plane[s] = C[stick_col[s] * ld + stick_y[s]];
 }
 
 template <typename T, int N>
@@ -183,12 +311,12 @@ __global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int6
     if (s < ns) buf[s * ld + z] = src[(size_t)z * nsticks + s0 + s];
   }
   __syncthreads();
-  fft_stages<T, false, N, 0>(buf, ns, ld, tw);
+  fft_nat<T, false, N>(buf, ns, ld, tw);
   const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
   const double2* pb = psi + (size_t)b * ldp;
   double2* hb = hpsi + (size_t)b * ldh;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const cx<T> v = buf[(stick_of[i] - s0) * ld + irev[zpos[i]]];
+    const cx<T> v = buf[(stick_of[i] - s0) * ld + zpos[i]];
     const double2 p = pb[i];
     const double k = kin[i];
     hb[i] = make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
