@@ -480,7 +480,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // FP64 eigenpairs in the FP64 phase; FP32 ones (from a subspace matrix
     // that is itself FP32-accurate) in the reduced-precision phase
     const bool polish = phase_prec == PWH_FP64;
-    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish);
+    // the reduced-precision phase needs the Ritz pairs only to well below its
+    // current residuals: FP32 sweeps to 1e-3 of the last largest residual
+    // (relative to the largest diagonal entry), between 4e-7 and 1e-4
+    const double tol32 = polish || it == 1 ? 4e-7 : std::min(1e-4, std::max(4e-7, 1e-3 * maxr));
+    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);

@@ -587,7 +587,7 @@ static size_t jacobi_ws_bytes(size_t nn, int n) {
 
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
-                 int warm_m0, bool polish) {
+                 int warm_m0, bool polish, double tol32) {
   if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
   const size_t nn = (size_t)n * n;
   ensure(w.jac, jacobi_ws_bytes(nn, n));
@@ -627,14 +627,14 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
     // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
     // convergence) usually finishes.  The whole matrix in one cluster's shared
     // memory when it fits, else through global memory.
-    if (!jacobi32_cluster(s, w, start, ld_start, n, 4e-7, 30, Q0, n, dg, ob32, st)) {
+    if (!jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
       k_c64_to_c32<<<gq, 256, 0, st>>>(start, ld_start, n, a0);
       PWH_LAUNCH_CHECK();
       k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity
       PWH_LAUNCH_CHECK();
       k_c64_to_c32<<<gq, 256, 0, st>>>(Q0, n, n, q0);
       PWH_LAUNCH_CHECK();
-      launch_jacobi<float>(s, w, a0, a1, q0, q1, n, 4e-7, 30, ob32, st);
+      launch_jacobi<float>(s, w, a0, a1, q0, q1, n, tol32, 30, ob32, st);
       // the FP32 eigenvectors sit in q0 or q1 (ob32[0]): widen them to FP64
       k_select_buf<<<gq, 256, 0, st>>>(q0, q1, ob32, (int64_t)nn, Q0);
       PWH_LAUNCH_CHECK();

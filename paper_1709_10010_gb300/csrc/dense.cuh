@@ -25,10 +25,12 @@ constexpr int kJacobiMaxN = 4096;
 // warm_m0 x warm_m0 block of H, and the iteration starts in that basis.
 // polish: FP64 result (FP32 Jacobi, then the FP64 unitary basis, Q^H H Q and
 // FP64 sweeps); otherwise the FP32 result (eigenvalues to about FP32 rounding
-// of ||H||, eigenvectors orthonormal to about FP32 rounding).
+// of ||H||, eigenvectors orthonormal to about FP32 rounding).  tol32: the
+// FP32 sweeps stop at max|A_ij| <= tol32 max|A_ii| (4e-7, about five FP32
+// roundings, lets one FP64 sweep finish the polish).
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep = nullptr,
-                 int64_t ldk = 0, int warm_m0 = 0, bool polish = true);
+                 int64_t ldk = 0, int warm_m0 = 0, bool polish = true, double tol32 = 4e-7);
 
 // FP32 stage of jacobi_eigh in one 16-CTA thread-block cluster with the matrix
 // in distributed shared memory (jacobi_dsm.cu): sweeps of the n x n Hermitian
