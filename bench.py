@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison solve")
     p.add_argument("--skip-batched", action="store_true", help="omit the batched cells x k-points solve")
+    p.add_argument("--profile", action="store_true",
+                   help="for a profiler's launch list: only the warm-up and timed solves, a short "
+                        "JSON line (no FP64 solve, H-only, e2e, batched or CPU legs)")
     return p.parse_args()
 
 
@@ -216,6 +219,11 @@ def run_ours(a):
         dist.destroy_process_group() if dist is not None else None
         return
     ms_per_step = 1e3 * elapsed / a.steps
+    if a.profile:
+        print(json.dumps({"metric": METRIC, "value": tot_apply / t_max, "unit": "band-applies/s",
+                          "ms_per_step": ms_per_step, "steps": a.steps, "warmup": a.warmup,
+                          "profile_run": True, "gpu_launches": int(launches)}))
+        return
 
     # ---- mixed vs FP64: one plain FP64 solve of the same system
     fp64 = None

@@ -204,13 +204,29 @@ __global__ void k_cg_precond(const double2* __restrict__ r, int64_t npw, const i
     z[(size_t)j * npw + i] = make_double2(k * v.x, k * v.y);
   }
 }
-// out[j] = Re <a_j, b_j>, one block per column (fixed-order reduction)
-__global__ void k_col_dot(const double2* __restrict__ a, const double2* __restrict__ b, int64_t npw,
-                          double* __restrict__ out) {
+// out[j] = Re <a_j, b_j>, one 1024-thread block per column, four element
+// pairs in flight a thread (fixed-order reduction)
+__global__ void __launch_bounds__(1024) k_col_dot(const double2* __restrict__ a,
+                                                  const double2* __restrict__ b, int64_t npw,
+                                                  double* __restrict__ out) {
   const int j = blockIdx.x;
+  const double2* aj = a + (size_t)j * npw;
+  const double2* bj = b + (size_t)j * npw;
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < npw; i += blockDim.x) {
-    const double2 x = a[(size_t)j * npw + i], y = b[(size_t)j * npw + i];
+  int64_t i = threadIdx.x;
+  const int64_t st = blockDim.x;
+  for (; i + 3 * st < npw; i += 4 * st) {
+    double2 x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = aj[i + u * st];
+      y[u] = bj[i + u * st];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc += x[u].x * y[u].x + x[u].y * y[u].y;
+  }
+  for (; i < npw; i += st) {
+    const double2 x = aj[i], y = bj[i];
     acc += x.x * y.x + x.y * y.y;
   }
   __shared__ double red[32];
@@ -309,7 +325,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
   PWH_LAUNCH_CHECK();
   project_out(s, X, nb, z, k, Wc, st);
   PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  k_col_dot<<<k, 256, 0, st>>>(r, z, npw, rho[0]);
+  k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[0]);
   PWH_LAUNCH_CHECK();
   int cur = 0;
   for (int it = 0; it < iters; ++it) {
@@ -318,7 +334,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     k_cg_shift<<<g2, 256, 0, st>>>(q, p, npw, idx, theta);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, q, k, Wc, st);
-    k_col_dot<<<k, 256, 0, st>>>(p, q, npw, pq);
+    k_col_dot<<<k, 1024, 0, st>>>(p, q, npw, pq);
     PWH_LAUNCH_CHECK();
     k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[cur], pq);
     PWH_LAUNCH_CHECK();
@@ -326,7 +342,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, z, k, Wc, st);
-    k_col_dot<<<k, 256, 0, st>>>(r, z, npw, rho[cur ^ 1]);
+    k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[cur ^ 1]);
     PWH_LAUNCH_CHECK();
     k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[cur ^ 1], rho[cur]);
     PWH_LAUNCH_CHECK();
@@ -565,7 +581,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       const int red = s.precision == PWH_FP64 ? PWH_MIXED : s.precision;
       jd_correction(s, w, L.X, nb, L.R, L.idx, k, L.theta, L.eref, o.jd_inner, red, T, L.Wc,
                     &S.n_apply, st);
-      k_col_dot<<<k, 256, 0, st>>>(T, T, npw, L.t0);
+      k_col_dot<<<k, 1024, 0, st>>>(T, T, npw, L.t0);
       PWH_LAUNCH_CHECK();
       k_sqrt<<<1, 256, 0, st>>>(L.t0, k);
       PWH_LAUNCH_CHECK();
