@@ -261,7 +261,7 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
   if (M <= 0 || N <= 0) return;
   if constexpr (sizeof(T) == 4) {
     if (N > 64)
-      cgemm_launch<TS, T, 128, 128, 8, 8, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
+      cgemm_launch<TS, T, 128, 128, 8, 8, 16>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
     else if (N > 32)
       cgemm_launch<TS, T, 128, 64, 8, 4, 8>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
     else if (N > 16 && M <= 128)
