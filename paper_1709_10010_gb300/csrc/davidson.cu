@@ -397,7 +397,10 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   const int64_t npw = s.npw;
   const int p1 = prec_first < 0 ? prec : prec_first;  // first pass may be cheaper
   sgemm(s, p1, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
-  cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st, p1 != PWH_FP64);
+  // the first factor only has to make T Tr well conditioned (the second pass,
+  // in the phase's precision, makes it orthonormal): FP32 Cholesky always;
+  // T Tr stays a combination of T's columns in the GEMM's precision
+  cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st, true);
   sgemm(s, p1, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
   sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
   cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st, prec != PWH_FP64);
