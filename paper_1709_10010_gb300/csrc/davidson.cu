@@ -447,6 +447,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   // grow every workspace the loop can need now, so that no allocation (and no
   // device-wide synchronisation) happens inside the iterations
   jacobi_reserve(w.dense, mmax, nb);
+  // the largest FP64 products of the FP64 phase: subspace matrix columns
+  // (up to m_max x m_max over npw), Ritz rotations (npw x nb over m_max),
+  // FP64 projector products (P x nb over npw, npw x nb over P)
+  oz_reserve(s, true, mmax, mmax, (int)npw);
+  oz_reserve(s, false, (int)npw, nb, mmax);
+  if (s.nproj > 0) {
+    oz_reserve(s, true, s.nproj, nb, (int)npw);
+    oz_reserve(s, false, (int)npw, nb, s.nproj);
+  }
   if (o.mixed && o.jd_inner > 0)
     ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);

@@ -284,10 +284,9 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
   }
 }
 
-// FP64 products of at least this many flops go to the tensor cores as sliced
+// FP64 products of at least kOzMinFlops go to the tensor cores as sliced
 // integer products (oz_gemm); PWH_GEMM_FP64_SIMT=1 in the environment keeps
 // every FP64 product on the FP64 pipe.
-constexpr double kOzMinFlops = 2e8;
 
 template <typename T>
 void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,

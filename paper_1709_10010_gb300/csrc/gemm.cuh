@@ -18,6 +18,12 @@ void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const 
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st);
 
+// Grow the sliced-product workspace for op(A) B of these sizes now (so that
+// later products of at most this size allocate nothing).
+void oz_reserve(System& s, bool conjA, int M, int N, int K);
+// Products of at least this many flops (8 M N K) take oz_gemm in cgemm<double>.
+constexpr double kOzMinFlops = 2e8;
+
 // FP64-equivalent complex GEMM on the BF16 tensor cores (gemm_tc.cu): same
 // contract as cgemm<double>, results within FP64-level rounding (integer
 // slices of the operands, exact partial sums).

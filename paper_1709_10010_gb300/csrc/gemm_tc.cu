@@ -889,10 +889,122 @@ __global__ void k_oz_reduce_nn(const float* __restrict__ part, int nz, int nchun
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Geometry and workspace of one sliced product.
+struct OzGeom {
+  int64_t Mr, Nr, seg, pitch;
+  int kb_seg, kbps, nchunk, nz;
+  size_t bytes_a, bytes_b, bytes_e, bytes_p;
+  size_t total() const { return bytes_a + bytes_b + bytes_e + bytes_p; }
+};
+static OzGeom oz_geom(bool conjA, int M, int N, int K) {
+  OzGeom g;
+  // real GEMM geometry: C' (Mr x Nr) = A' (Mr x Kr) B'^T, both K-major
+  g.Mr = conjA ? 2 * (int64_t)M : M;
+  g.Nr = 2 * (int64_t)N;
+  const int64_t Kr = conjA ? K : 2 * (int64_t)K;
+  g.seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
+  g.kb_seg = (int)(g.seg / TC_BK);
+  // K blocks per exact partial: at most 16 (1024 wide) and dividing kb_seg;
+  // pad the segment to whole 16-block chunks when that costs little, else
+  // take a divisor of at least 8
+  g.kbps = g.kb_seg;
+  if (g.kb_seg > 16) {
+    const int pad16 = (g.kb_seg + 15) / 16 * 16;
+    g.kbps = 0;
+    if ((pad16 - g.kb_seg) * 16 > g.kb_seg)
+      for (int d = 16; d >= 8 && !g.kbps; --d)
+        if (g.kb_seg % d == 0) g.kbps = d;
+    if (!g.kbps) {
+      g.kb_seg = pad16;
+      g.seg = (int64_t)g.kb_seg * TC_BK;
+      g.kbps = 16;
+    }
+  }
+  g.nchunk = g.kb_seg / g.kbps;
+  g.nz = OZ_PAIRS * g.nchunk;
+  g.pitch = OZ_S * g.seg;
+  g.bytes_a = align256((size_t)g.Mr * g.pitch * 2);
+  g.bytes_b = align256((size_t)g.Nr * g.pitch * 2);
+  g.bytes_e = align256((size_t)(g.Mr + g.Nr) * sizeof(int));
+  g.bytes_p = (size_t)g.nz * g.Mr * g.Nr * sizeof(float);
+  return g;
+}
+
+// The exact partials (28 per K chunk, FP32, of the whole real output) are
+// bounded.  A product over many chunks first runs as K segments of whole
+// chunks, each added into C in FP64 (one more rounding per segment, no
+// operand sliced twice); a segment that still does not fit runs as pieces of
+// its larger output dimension, which give the same bits as the whole segment
+// (the exponents belong to single rows of op(A) and single columns of B).
+constexpr size_t kOzPartCap = (size_t)4 << 30;
+
+struct OzSplit {
+  int kseg;      // complex K per segment
+  bool split_m;  // pieces of M (else of N)
+  int piece;     // rows or columns per piece
+};
+static OzSplit oz_split_of(bool conjA, int M, int N, int K) {
+  OzSplit sp{K, M >= N, M >= N ? M : N};
+  const OzGeom g = oz_geom(conjA, M, N, K);
+  if (g.bytes_p <= kOzPartCap) return sp;
+  const size_t per_chunk = g.bytes_p / (size_t)g.nchunk;
+  if (g.nchunk > 1) {
+    // whole 1024-wide real chunks per segment (1024 complex K for A^H B,
+    // 512 for A B, whose real K is 2K)
+    const int64_t c = std::max<int64_t>(1, (int64_t)(kOzPartCap / per_chunk));
+    const int64_t kc = conjA ? 1024 : 512;
+    if (c < g.nchunk) sp.kseg = (int)std::min<int64_t>(K, c * kc);
+  }
+  const OzGeom gs = oz_geom(conjA, M, N, sp.kseg);
+  if (gs.bytes_p <= kOzPartCap) return sp;
+  const size_t per = gs.bytes_p / (size_t)sp.piece;  // partial bytes per row or column
+  const int64_t fit = (int64_t)(kOzPartCap / per) / 64 * 64;
+  sp.piece = (int)std::max<int64_t>(64, std::min<int64_t>(fit, sp.piece));
+  return sp;
+}
+
+void oz_reserve(System& s, bool conjA, int M, int N, int K) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  const OzSplit sp = oz_split_of(conjA, M, N, K);
+  ensure(s.ws_oz, oz_geom(conjA, sp.split_m ? std::min(sp.piece, M) : M,
+                          sp.split_m ? N : std::min(sp.piece, N), sp.kseg)
+                      .total());
+}
+
+static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 alpha,
+                          const double2* A, int64_t lda, const double2* B, int64_t ldb,
+                          double2 beta, double2* C, int64_t ldc, cudaStream_t st,
+                          const double* rowscale);
+
 void oz_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
              int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
              cudaStream_t st, const double* rowscale) {
   if (M <= 0 || N <= 0) return;
+  const OzSplit sp = oz_split_of(conjA, M, N, K);
+  for (int k0 = 0; k0 == 0 || k0 < K; k0 += sp.kseg) {
+    const int kk = std::min(sp.kseg, K - k0);
+    // K rows k0.. of B and of A (A^H), or K columns k0.. of A
+    const double2* Ak = A + (conjA ? (int64_t)k0 : (int64_t)k0 * lda);
+    const double2* Bk = B + k0;
+    const double2 bk = k0 == 0 ? beta : make_double2(1, 0);
+    if (sp.split_m) {
+      // rows m0.. of C: columns m0.. of A (A^H) or rows m0.. of A
+      for (int m0 = 0; m0 < M; m0 += sp.piece)
+        oz_gemm_piece(s, conjA, std::min(sp.piece, M - m0), N, kk, alpha,
+                      Ak + (conjA ? (int64_t)m0 * lda : (int64_t)m0), lda, Bk, ldb, bk, C + m0,
+                      ldc, st, rowscale ? rowscale + m0 : nullptr);
+    } else {
+      for (int n0 = 0; n0 < N; n0 += sp.piece)
+        oz_gemm_piece(s, conjA, M, std::min(sp.piece, N - n0), kk, alpha, Ak, lda,
+                      Bk + (int64_t)n0 * ldb, ldb, bk, C + (int64_t)n0 * ldc, ldc, st, rowscale);
+    }
+  }
+}
+
+static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 alpha,
+                          const double2* A, int64_t lda, const double2* B, int64_t ldb,
+                          double2 beta, double2* C, int64_t ldc, cudaStream_t st,
+                          const double* rowscale) {
   static std::once_flag once;
   static unsigned char pa[32], pb[32];
   std::call_once(once, [] {
@@ -908,34 +1020,12 @@ void oz_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const do
     cudaMemcpyToSymbol(c_oz_g, g, sizeof(g));
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   });
-  // real GEMM geometry: C' (Mr x Nr) = A' (Mr x Kr) B'^T, both K-major
-  const int64_t Mr = conjA ? 2 * (int64_t)M : M, Nr = 2 * (int64_t)N;
-  const int64_t Kr = conjA ? K : 2 * (int64_t)K;
-  int64_t seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
-  int kb_seg = (int)(seg / TC_BK);
-  // K blocks per exact partial: at most 16 (1024 wide) and dividing kb_seg;
-  // pad the segment to whole 16-block chunks when that costs little, else
-  // take a divisor of at least 8
-  int kbps = kb_seg;
-  if (kb_seg > 16) {
-    const int pad16 = (kb_seg + 15) / 16 * 16;
-    kbps = 0;
-    if ((pad16 - kb_seg) * 16 > kb_seg)
-      for (int d = 16; d >= 8 && !kbps; --d)
-        if (kb_seg % d == 0) kbps = d;
-    if (!kbps) {
-      kb_seg = pad16;
-      seg = (int64_t)kb_seg * TC_BK;
-      kbps = 16;
-    }
-  }
-  const int nchunk = kb_seg / kbps;
-  const int nz = OZ_PAIRS * nchunk;
-  const int64_t pitch = OZ_S * seg;
-  const size_t bytes_a = align256((size_t)Mr * pitch * 2), bytes_b = align256((size_t)Nr * pitch * 2);
-  const size_t bytes_e = align256((size_t)(Mr + Nr) * sizeof(int));
-  const size_t bytes_p = (size_t)nz * Mr * Nr * sizeof(float);
-  ensure(s.ws_oz, bytes_a + bytes_b + bytes_e + bytes_p);
+  const OzGeom gg = oz_geom(conjA, M, N, K);
+  const int64_t Mr = gg.Mr, Nr = gg.Nr, seg = gg.seg;
+  const int kb_seg = gg.kb_seg, kbps = gg.kbps, nchunk = gg.nchunk, nz = gg.nz;
+  const int64_t pitch = gg.pitch;
+  const size_t bytes_a = gg.bytes_a, bytes_b = gg.bytes_b, bytes_e = gg.bytes_e;
+  ensure(s.ws_oz, gg.total());
   char* base = s.ws_oz.p;
   __nv_bfloat16* pA = (__nv_bfloat16*)base;
   __nv_bfloat16* pB = (__nv_bfloat16*)(base + bytes_a);

@@ -56,3 +56,26 @@ def test_gemm_vs_numpy(env, M, N, K, conj_a, precision):
     eps = 4e-15 if precision == "fp64" else 4e-7
     bar = eps * scale * abs(alpha) + 4e-15 * abs(beta) * np.abs(C0).max()
     assert np.abs(C - ref).max() <= bar, (np.abs(C - ref).max(), bar)
+
+
+# FP64 products whose exact partials would pass 4 GiB run in parts: K
+# segments of whole chunks added into C (A^H B over a long K), or pieces of the
+# larger output dimension (a tall A B whose one chunk is already too large).
+@pytest.mark.parametrize("M,N,K,conj_a", [(600, 600, 40000, True), (160000, 128, 512, False)])
+def test_gemm_fp64_pieces(env, M, N, K, conj_a):
+    torch, s = env
+    rng = np.random.default_rng([M, N, K, 7])
+    A = cplx(rng, K, M) if conj_a else cplx(rng, M, K)
+    B = cplx(rng, K, N)
+    C0 = cplx(rng, M, N)
+    alpha, beta = (0.7 - 0.2j), (0.3 + 0.4j)
+    opA = A.conj().T if conj_a else A
+    ref = alpha * (opA @ B) + beta * C0
+    dev = lambda X: torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    Ct = dev(C0)
+    s.gemm(dev(A), dev(B), Ct, conj_a=conj_a, alpha=alpha, beta=beta, precision="fp64")
+    s.sync()
+    C = Ct.cpu().numpy().T
+    scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
+    bar = 4e-15 * scale * abs(alpha) + 4e-15 * abs(beta) * np.abs(C0).max()
+    assert np.abs(C - ref).max() <= bar, (np.abs(C - ref).max(), bar)
