@@ -373,6 +373,7 @@ FAMILY_BOUND = {
     "cgemm_fp64": ("alu", "flops", "fp64"), "cgemm_fp32": ("alu", "flops", "fp32"),
     "jacobi_fp64": ("alu", "flops", "fp64"), "cholqr_fp64": ("alu", "flops", "fp64"),
     "jacobi_fp32": ("alu", "flops", "fp32"), "zgemm_fp64_tc": ("tensor", "flops", "bf16"),
+    "zgemm_fp32_tc": ("tensor", "flops", "bf16"),
 }
 
 

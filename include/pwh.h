@@ -269,7 +269,10 @@ pwh_status pwh_get_shells(const pwh_system* sys, int32_t* nshell, int32_t* shell
 typedef struct {
   char name[32];     /* family: fft_z_inverse_fp64|fp32, fft_plane_fp64|fp32,
                         fft_z_forward_fp64|fp32, tc_gemm_becp, tc_gemm_backproj,
-                        cgemm_fp64, cgemm_fp32, jacobi_fp64, cholqr_fp64 */
+                        cgemm_fp64, cgemm_fp32, jacobi_fp64, cholqr_fp64,
+                        jacobi_fp32, zgemm_fp64_tc (sliced FP64-equivalent
+                        GEMM), zgemm_fp32_tc (three-slice FP32-equivalent
+                        GEMM) */
   int64_t launches;  /* timed launches (bracketed groups) */
   double total_ms;   /* summed device time */
   double flops;      /* algorithmic floating-point operations of those launches
@@ -329,10 +332,13 @@ pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t 
  * uses it: C = alpha op(A) B + beta C, op(A) = A^H when conj_a else A; op(A)
  * is M x K, B is K x N, C is M x N; all DEVICE complex128, column-major with
  * the given leading dimensions (lda >= rows of A as stored).  alpha, beta:
- * HOST double[2] (re, im).  precision PWH_FP64: FP64 arithmetic; PWH_MIXED:
- * operands rounded to FP32, FP32 accumulation (relative error about
- * sqrt(K) 1e-7), result widened.  Asynchronous on the system's stream; uses
- * the system's split-K workspace (one GEMM at a time per system). */
+ * HOST double[2] (re, im).  precision PWH_FP64: FP64 arithmetic (products of
+ * at least 2e8 flops as exact integer-slice products on the tensor cores);
+ * PWH_MIXED: operands rounded to FP32, FP32 accumulation (relative error about
+ * sqrt(K) 1e-7), result widened (products of at least 4e8 flops as three BF16
+ * slices of each FP32 operand, six slice products on the tensor cores).
+ * Asynchronous on the system's stream; uses the system's workspaces (one GEMM
+ * at a time per system). */
 pwh_status pwh_subspace_gemm(pwh_system* sys, int32_t precision, int32_t conj_a, int32_t M,
                              int32_t N, int32_t K, const double* alpha, const void* A, int64_t lda,
                              const void* B, int64_t ldb, const double* beta, void* C, int64_t ldc);

@@ -69,6 +69,57 @@ template <typename T> __host__ __device__ __forceinline__ cx<T> scl(cx<T> a, T s
   return mk<T>(a.x * s, a.y * s);
 }
 
+// --------------------------------------------------- format conversion ----
+// IEEE 754 binary64 <-> binary32 conversions with integer operations only: on
+// this GPU conversions to and from FP64 issue on the narrow FP64 pipe, which
+// made them the bottleneck of kernels that widen or narrow every element.
+// d2f_rn rounds to nearest, ties to even (subnormal results included, overflow
+// to infinity, NaN stays NaN); f2d is exact.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+  const int ef = e - 1023 + 127;
+  if (ef > 0) {
+    if (ef >= 255) return __uint_as_float(sign | 0x7f800000u);
+    // 23 kept fraction bits, 29 dropped; a carry out of the fraction moves
+    // into the exponent (up to infinity), as the encoding intends
+    unsigned q = (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1fffffffu);
+    q += (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ? 1u : 0u;
+    return __uint_as_float(sign | (((unsigned)ef << 23) + q));
+  }
+  // binary32 subnormal or zero: value = M 2^(e - 1075), unit 2^-149
+  if (e == 0) return __uint_as_float(sign);
+  const unsigned long long M = m | (1ull << 52);
+  const int sh = 926 - e;  // >= 30
+  if (sh >= 64) return __uint_as_float(sign);
+  unsigned long long q = M >> sh;
+  const unsigned long long rem = M & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  return __uint_as_float(sign | (unsigned)q);
+}
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  int e = (int)((b >> 23) & 0xff);
+  unsigned m = b & 0x7fffffu;
+  if (e == 255)
+    return __longlong_as_double((long long)(sign | (0x7ffull << 52) | ((unsigned long long)m << 29)));
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)sign);
+    const int sh = __clz(m) - 8;  // normalise the subnormal fraction
+    m = (m << sh) & 0x7fffffu;
+    e = 1 - sh;
+  }
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) | ((unsigned long long)m << 29)));
+}
+__device__ __forceinline__ float2 d2f_rn(double2 z) { return make_float2(d2f_rn(z.x), d2f_rn(z.y)); }
+__device__ __forceinline__ double2 f2d(float2 z) { return make_double2(f2d(z.x), f2d(z.y)); }
+
 // ------------------------------------------------------------- FFT plan -----
 constexpr int kMaxStages = 10;
 constexpr int kMaxFft = 512;
@@ -99,7 +150,7 @@ void free_davidson_ws(DavWs* w);
 enum KernelFamily {
   KF_FFT_ZINV64 = 0, KF_FFT_PLANE64, KF_FFT_ZFWD64, KF_FFT_ZINV32, KF_FFT_PLANE32, KF_FFT_ZFWD32,
   KF_TC_BECP, KF_TC_BACK, KF_GEMM_FP64, KF_GEMM_FP32, KF_JACOBI, KF_CHOLQR, KF_JACOBI32,
-  KF_GEMM_OZ, KF_COUNT
+  KF_GEMM_OZ, KF_GEMM_X3, KF_COUNT
 };
 extern const char* const kKernelFamilyName[KF_COUNT];
 

@@ -619,8 +619,8 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
       // start in the previous eigenbasis: A = Qw^H H Qw (FP32 arithmetic suffices)
       k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q1);
       PWH_LAUNCH_CHECK();
-      cgemm_f32(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
-      cgemm_f32(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
+      cgemm_f32_simt(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
+      cgemm_f32_simt(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
       start = A1;
       ld_start = n;
     }
@@ -642,7 +642,7 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
       PWH_LAUNCH_CHECK();
     }
     if (warm) {
-      cgemm_f32(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
+      cgemm_f32_simt(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
       Q = A0;
     }
     if (!polish) {
@@ -651,11 +651,11 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
       // quotients q^H H q of those vectors (the FP32 diagonal drifts by the
       // accumulated non-unitarity of FP32 rotations, about n sweeps x 1e-7)
       double2* Qo = (Q == Q0) ? A0 : Q0;
-      cgemm_f32(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
+      cgemm_f32_simt(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
       k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
       PWH_LAUNCH_CHECK();
-      cgemm_f32(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
-      cgemm_f32(s, false, n, n, n, one, H, ldh, Qo, n, zero, G, n, st);
+      cgemm_f32_simt(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
+      cgemm_f32_simt(s, false, n, n, n, one, H, ldh, Qo, n, zero, G, n, st);
       k_rayleigh<<<n, 128, 0, st>>>(Qo, G, n, dg);
       PWH_LAUNCH_CHECK();
       const int sb = (int)std::min<int64_t>(64, ((int64_t)nn + 1023) / 1024);
@@ -669,10 +669,10 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   // Newton-Schulz to the nearest unitary: Q <- Q (3I - Q^H Q)/2, once in FP32
   // arithmetic, once in FP64
   double2* Qo = (Q == Q0) ? A0 : Q0;
-  cgemm_f32(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
+  cgemm_f32_simt(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
   k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
   PWH_LAUNCH_CHECK();
-  cgemm_f32(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
+  cgemm_f32_simt(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
   cgemm<double>(s, true, n, n, n, one, Qo, n, Qo, n, zero, G, n, st);
   k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
   PWH_LAUNCH_CHECK();

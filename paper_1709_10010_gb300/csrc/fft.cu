@@ -126,7 +126,7 @@ template <> struct TwT<double> { static const double2* get(const System& s) { re
 template <> struct TwT<float> { static const float2* get(const System& s) { return s.d_tw32; } };
 
 template <typename T> __device__ __forceinline__ cx<T> from64(double2 z) {
-  return mk<T>((T)z.x, (T)z.y);
+  return widen_from64<T>(z);
 }
 
 // ---------------------------------------------------- pass 1: z inverse ----
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256) k_zfwd(const cx<T>* __restrict__ W, int64
     cx<T> v = buf[s * ld + irev[zpos[i]]];
     double2 p = pb[i];
     double k = kin[i];
-    hb[i] = make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
+    hb[i] = kin_plus<T>(k, p, v);
   }
 }
 

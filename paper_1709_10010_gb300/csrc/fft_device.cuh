@@ -90,4 +90,15 @@ __device__ __forceinline__ void butterfly(cx<T>* base, int estride, int M, int k
 }
 
 
+// Format conversions at the edges of the FFT passes (band data is FP64 in
+// HBM; the FP32 passes compute in FP32).
+template <typename T> __device__ __forceinline__ cx<T> widen_from64(double2 z) {
+  return mk<T>((T)z.x, (T)z.y);
+}
+// hpsi = kin psi + v (FP64)
+template <typename T>
+__device__ __forceinline__ double2 kin_plus(double k, double2 p, cx<T> v) {
+  return make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
+}
+
 }  // namespace pwh

@@ -188,10 +188,6 @@ __device__ __forceinline__ void fft_nat(cx<T>* data, int nfft, int fstride, cons
   __syncthreads();
 }
 
-template <typename T> __device__ __forceinline__ cx<T> widen_from64(double2 z) {
-  return mk<T>((T)z.x, (T)z.y);
-}
-
 template <typename T, int N>
 __global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, int64_t ldp,
                                                const int32_t* __restrict__ stick_off,
@@ -319,7 +315,7 @@ __global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int6
     const cx<T> v = buf[(stick_of[i] - s0) * ld + zpos[i]];
     const double2 p = pb[i];
     const double k = kin[i];
-    hb[i] = make_double2(k * p.x + (double)v.x, k * p.y + (double)v.y);
+    hb[i] = kin_plus<T>(k, p, v);
   }
 }
 

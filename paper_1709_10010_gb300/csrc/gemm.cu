@@ -305,9 +305,29 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
   cgemm_impl<T, T>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
 }
 
+void cgemm_f32_simt(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+                    int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C,
+                    int64_t ldc, cudaStream_t st) {
+  cgemm_impl<double, float>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, nullptr);
+}
+
 void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st) {
+  // large products run on the tensor cores as three-slice BF16 products;
+  // PWH_GEMM_FP32_SIMT=1 in the environment keeps them on the FP32 pipe
+  static const bool simt_only = [] {
+    const char* e = std::getenv("PWH_GEMM_FP32_SIMT");
+    return e && e[0] == '1';
+  }();
+  // (narrow products stay on the FP32 pipe: the tensor-core path's slicing and
+  // reduction cost more than it saves below about 48 columns of A^H B and 96
+  // of A B)
+  const int narrow = conjA ? std::min(M, N) : N;
+  if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96)) {
+    x3_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    return;
+  }
   cgemm_impl<double, float>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, nullptr);
 }
 

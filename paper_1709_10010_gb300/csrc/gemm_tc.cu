@@ -58,10 +58,14 @@ struct TcArgs {
   int64_t ldh;
   int nb;
   int* err;          // device error word
-  // sliced operands (FP64-equivalent GEMM): product t multiplies A segment
-  // oz_a[t] by B segment oz_b[t]
+  // sliced operands: product t multiplies A segment oz_a[t] by B segment
+  // oz_b[t]; oz = 1: blockIdx.z = (K chunk, product), each partial one product
+  // (FP64-equivalent GEMM); oz = 2 (FP32-equivalent GEMM): blockIdx.z < z_rest
+  // takes kb_per_split blocks of products 1.., the others kps0 blocks of
+  // product 0
   int oz;
   unsigned char oz_a[32], oz_b[32];
+  int z_rest, kps0;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -187,10 +191,24 @@ __global__ void __launch_bounds__(128, 1)
   const int kb_total = args.terms * args.kb_seg;
   // sliced operands: z = chunk * pairs + pair, so that the pairs of one K chunk
   // (which share operand slices) run close together and hit in L2
-  const int kb0 = args.oz ? (int)(blockIdx.z % args.terms) * args.kb_seg +
-                                (int)(blockIdx.z / args.terms) * args.kb_per_split
-                          : (int)blockIdx.z * args.kb_per_split;
-  const int nkb = max(0, min(kb_total, kb0 + args.kb_per_split) - kb0);
+  const int z = (int)blockIdx.z;
+  int kb0, kb_end;
+  if (args.oz == 1) {
+    kb0 = (z % args.terms) * args.kb_seg + (z / args.terms) * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  } else if (args.oz == 2 && z < args.z_rest) {
+    // products 1.. (the smaller slices): long ranges
+    kb0 = args.kb_seg + z * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  } else if (args.oz == 2) {
+    // product 0 (leading slices): short ranges
+    kb0 = (z - args.z_rest) * args.kps0;
+    kb_end = min(args.kb_seg, kb0 + args.kps0);
+  } else {
+    kb0 = z * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  }
+  const int nkb = max(0, kb_end - kb0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -280,11 +298,11 @@ __global__ void __launch_bounds__(128, 1)
           for (int j = 0; j < 32; j += 2) {
             int b = (n0 + c0 + j) >> 1;
             if (b < args.nb) {
+              // FP32 add with integer format conversions (this pass carries
+              // FP32 accuracy; the FP64 pipe would bound the epilogue)
               double2* h = args.hpsi + (size_t)b * args.ldh + m;
-              double2 o = *h;
-              o.x += (double)v[j];
-              o.y += (double)v[j + 1];
-              *h = o;
+              const float2 o = d2f_rn(*h);
+              *h = f2d(make_float2(o.x + v[j], o.y + v[j + 1]));
             }
           }
         }
@@ -1088,6 +1106,374 @@ static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 al
     k_oz_reduce_nn<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nz, nchunk, M, N, exa, exb,
                                                                   rowscale, alpha, beta, C, ldc);
   PWH_LAUNCH_CHECK();
+}
+
+// ------------------------------------- FP32-equivalent GEMM (3 BF16 slices) --
+// Each real operand value, rounded to FP32, is the exact sum of three BF16
+// values x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = x - x0 - x1:
+// 8 significant bits each, 24 in all, every slice with its own exponent).  The
+// six products with s + t <= 2 run as one BF16 GEMM over the concatenated K
+// segments, accumulating in FP32 tensor memory; the three dropped products are
+// below 2^-26 of |a b|.  Split-K partials are summed in FP64.
+constexpr int X3_S = 3, X3_TERMS = 6;
+
+__device__ __forceinline__ void x3_split(double x, __nv_bfloat16* a) {
+  const float f = d2f_rn(x);
+  a[0] = __float2bfloat16_rn(f);
+  const float r1 = f - __bfloat162float(a[0]);  // exact: at most 16 significant bits
+  a[1] = __float2bfloat16_rn(r1);
+  a[2] = __float2bfloat16_rn(r1 - __bfloat162float(a[1]));  // exact remainder
+}
+
+// Rows 2j (real parts) and 2j+1 (imaginary parts) of the interleaved operand
+// whose row pair j is column j of X (K x J, ld): segment s holds slice s at
+// column s seg + k (zero for K <= k < seg); two K positions per thread.
+__global__ void k_x3_slice_cols(const double2* __restrict__ X, int64_t ld, int K, int seg,
+                                __nv_bfloat16* __restrict__ out, int64_t pitch) {
+  const int j = blockIdx.y;
+  const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (k >= seg) return;
+  const double2* x = X + (size_t)j * ld;
+  const double2 v0 = k < K ? x[k] : make_double2(0.0, 0.0);
+  const double2 v1 = k + 1 < K ? x[k + 1] : make_double2(0.0, 0.0);
+  __nv_bfloat16 r0[X3_S], i0[X3_S], r1[X3_S], i1[X3_S];
+  x3_split(v0.x, r0);
+  x3_split(v0.y, i0);
+  x3_split(v1.x, r1);
+  x3_split(v1.y, i1);
+  __nv_bfloat16* o0 = out + (size_t)(2 * j) * pitch + k;
+  __nv_bfloat16* o1 = o0 + pitch;
+#pragma unroll
+  for (int t = 0; t < X3_S; ++t) {
+    __nv_bfloat162 p, q;
+    p.x = r0[t];
+    p.y = r1[t];
+    q.x = i0[t];
+    q.y = i1[t];
+    *(__nv_bfloat162*)(o0 + (size_t)t * seg) = p;
+    *(__nv_bfloat162*)(o1 + (size_t)t * seg) = q;
+  }
+}
+
+// A2[m][s seg + 2k + c] = slice s of (Re, Im) A[m][k] (A: M x K column-major,
+// zero for 2K <= 2k + c < seg); 32 x 32 tiles transposed through shared memory.
+__global__ void k_x3_slice_rows(const double2* __restrict__ A, int64_t ld, int M, int K, int seg,
+                                __nv_bfloat16* __restrict__ out, int64_t pitch) {
+  __shared__ double2 tile[32][33];
+  const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
+    const int mm = t & 31, kk = t >> 5;
+    const int m = m0 + mm, k = k0 + kk;
+    tile[kk][mm] = (m < M && k < K) ? A[(size_t)k * ld + m] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 1024; t += blockDim.x) {
+    const int kk = t & 31, mm = t >> 5;
+    const int m = m0 + mm, k = k0 + kk;
+    if (m >= M || 2 * k >= seg) continue;
+    const double2 v = tile[kk][mm];
+    __nv_bfloat16 ar[X3_S], ai[X3_S];
+    x3_split(v.x, ar);
+    x3_split(v.y, ai);
+    __nv_bfloat16* r = out + (size_t)m * pitch + 2 * k;
+#pragma unroll
+    for (int s = 0; s < X3_S; ++s) {
+      __nv_bfloat162 p;
+      p.x = ar[s];
+      p.y = ai[s];
+      *(__nv_bfloat162*)(r + (size_t)s * seg) = p;
+    }
+  }
+}
+
+// B operand of the non-conjugated product, rows 2n and 2n+1:
+//     B2[2n][2k] = Re, B2[2n][2k+1] = -Im, B2[2n+1][2k] = Im, B2[2n+1][2k+1] = Re
+// of B[k][n] (B: K x N column-major), each value as its three slices.
+__global__ void k_x3_slice_b2(const double2* __restrict__ B, int64_t ld, int K, int seg,
+                              __nv_bfloat16* __restrict__ out, int64_t pitch) {
+  const int n = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * k >= seg) return;
+  const double2 v = k < K ? B[(size_t)n * ld + k] : make_double2(0.0, 0.0);
+  __nv_bfloat16 ar[X3_S], ai[X3_S];
+  x3_split(v.x, ar);
+  x3_split(v.y, ai);
+  __nv_bfloat16* r0 = out + (size_t)(2 * n) * pitch + 2 * k;
+  __nv_bfloat16* r1 = r0 + pitch;
+#pragma unroll
+  for (int s = 0; s < X3_S; ++s) {
+    __nv_bfloat162 p0, p1;
+    p0.x = ar[s];
+    p0.y = __hneg(ai[s]);
+    p1.x = ai[s];
+    p1.y = ar[s];
+    *(__nv_bfloat162*)(r0 + (size_t)s * seg) = p0;
+    *(__nv_bfloat162*)(r1 + (size_t)s * seg) = p1;
+  }
+}
+
+// Epilogue of the reducers: C = alpha v + beta C with v the FP32 sum of the
+// partials.  beta = 0 or 1 with a real FP32 alpha (every product of the
+// eigensolver) takes FP32 arithmetic and integer format conversions; other
+// coefficients take FP64.
+struct X3Out {
+  double2 alpha, beta;
+  float af;  // alpha.x in FP32
+  int mode;  // 0: beta = 0, real alpha; 1: beta = 1, real alpha; 2: general
+};
+__device__ __forceinline__ void x3_store(const X3Out& o, float re, float im, double2* c) {
+  if (o.mode == 0) {
+    *c = f2d(make_float2(o.af * re, o.af * im));
+  } else if (o.mode == 1) {
+    const double2 v = f2d(make_float2(o.af * re, o.af * im));
+    const double2 c0 = *c;
+    *c = make_double2(c0.x + v.x, c0.y + v.y);
+  } else {
+    const double2 v = f2d(make_float2(re, im));
+    double2 r = make_double2(o.alpha.x * v.x - o.alpha.y * v.y, o.alpha.x * v.y + o.alpha.y * v.x);
+    if (o.beta.x != 0.0 || o.beta.y != 0.0) {
+      const double2 c0 = *c;
+      r.x += o.beta.x * c0.x - o.beta.y * c0.y;
+      r.y += o.beta.x * c0.y + o.beta.y * c0.x;
+    }
+    *c = r;
+  }
+}
+
+// C from the FP32 partials part[z][n'][m'], one thread per output (few
+// partials).  op(A) = A^H: Re = C'[2m][2n] + C'[2m+1][2n+1], Im = C'[2m][2n+1]
+// - C'[2m+1][2n] (M' = 2M, N' = 2N); op(A) = A: (C'[m][2n], C'[m][2n+1]).
+template <bool CONJ>
+__global__ void k_x3_reduce(const float* __restrict__ part, int nz, int M, int N, X3Out o,
+                            double2* __restrict__ C, int64_t ldc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)M * N) return;
+  const int m = (int)(t % M), n = (int)(t / M);
+  float re = 0.f, im = 0.f;
+  if (CONJ) {
+    const int64_t Mr = 2 * (int64_t)M, plane = Mr * 2 * (int64_t)N;
+    const float* p0 = part + (size_t)(2 * n) * Mr + 2 * m;
+    const float* p1 = p0 + Mr;
+    for (int z = 0; z < nz; ++z) {
+      const float2 a = *(const float2*)(p0 + (size_t)z * plane);  // (2m,2n), (2m+1,2n)
+      const float2 b = *(const float2*)(p1 + (size_t)z * plane);  // (2m,2n+1), (2m+1,2n+1)
+      re += a.x + b.y;
+      im += b.x - a.y;
+    }
+  } else {
+    const int64_t plane = (int64_t)M * 2 * N;
+    const float* p0 = part + (size_t)(2 * n) * M + m;
+    for (int z = 0; z < nz; ++z) {
+      re += p0[(size_t)z * plane];
+      im += p0[(size_t)z * plane + M];
+    }
+  }
+  x3_store(o, re, im, C + (size_t)n * ldc + m);
+}
+
+// The same for many partials: a block of 8 warps per 32 consecutive outputs of
+// one column; warp w sums partials z = w mod 8 (four loads in flight per
+// lane, coalesced across the lanes), then the warps' sums are added.
+template <bool CONJ>
+__global__ void __launch_bounds__(256) k_x3_reduce_wide(const float* __restrict__ part, int nz,
+                                                        int M, int N, X3Out o,
+                                                        double2* __restrict__ C, int64_t ldc) {
+  __shared__ float2 acc[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.x * 32 + lane, n = blockIdx.y;
+  float re = 0.f, im = 0.f;
+  if (m < M) {
+    if (CONJ) {
+      const int64_t Mr = 2 * (int64_t)M, plane = Mr * 2 * (int64_t)N;
+      const float* p0 = part + (size_t)(2 * n) * Mr + 2 * m;
+      int z = w;
+      for (; z + 24 < nz; z += 32) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = *(const float2*)(p0 + (size_t)(z + 8 * u) * plane);
+          b[u] = *(const float2*)(p0 + (size_t)(z + 8 * u) * plane + Mr);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          re += a[u].x + b[u].y;
+          im += b[u].x - a[u].y;
+        }
+      }
+      for (; z < nz; z += 8) {
+        const float2 a = *(const float2*)(p0 + (size_t)z * plane);
+        const float2 b = *(const float2*)(p0 + (size_t)z * plane + Mr);
+        re += a.x + b.y;
+        im += b.x - a.y;
+      }
+    } else {
+      const int64_t plane = (int64_t)M * 2 * N;
+      const float* p0 = part + (size_t)(2 * n) * M + m;
+      int z = w;
+      for (; z + 24 < nz; z += 32) {
+        float a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = p0[(size_t)(z + 8 * u) * plane];
+          b[u] = p0[(size_t)(z + 8 * u) * plane + M];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          re += a[u];
+          im += b[u];
+        }
+      }
+      for (; z < nz; z += 8) {
+        re += p0[(size_t)z * plane];
+        im += p0[(size_t)z * plane + M];
+      }
+    }
+  }
+  acc[w][lane] = make_float2(re, im);
+  __syncthreads();
+  if (w != 0 || m >= M) return;
+  re = 0.f;
+  im = 0.f;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    re += acc[v][lane].x;
+    im += acc[v][lane].y;
+  }
+  x3_store(o, re, im, C + (size_t)n * ldc + m);
+}
+
+// FP32 accumulation in tensor memory rounds once per 16-wide MMA and not to
+// nearest, so its error grows with the accumulated length: the leading
+// product runs in partials of kX3Kps0 K blocks (512 real K), the five smaller
+// ones (at most 2^-8 of it) in long partials.  Partials above kX3PartCap run as
+// K segments added into C.
+constexpr int kX3Kps0 = 8;
+constexpr size_t kX3PartCap = (size_t)1 << 30;
+
+struct X3Geom {
+  int64_t Mr, Nr, seg, pitch, tiles;
+  int kb_seg, z_rest, kps_rest, z0;
+  size_t bytes_a, bytes_b, bytes_p;
+};
+static X3Geom x3_geom(bool conjA, int M, int N, int K) {
+  X3Geom g;
+  g.Mr = conjA ? 2 * (int64_t)M : M;
+  g.Nr = 2 * (int64_t)N;
+  const int64_t Kr = conjA ? K : 2 * (int64_t)K;
+  g.seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
+  g.kb_seg = (int)(g.seg / TC_BK);
+  g.pitch = X3_S * g.seg;
+  const int kb_rest = (X3_TERMS - 1) * g.kb_seg;
+  // the long ranges spread over about two waves of output tiles, at least 8
+  // blocks each; every range gets at least one block
+  const int64_t tiles = ((g.Mr + TC_BM - 1) / TC_BM) * ((g.Nr + TC_BN - 1) / TC_BN);
+  g.tiles = tiles;
+  int nz = (int)std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, kb_rest / 8));
+  g.kps_rest = (kb_rest + nz - 1) / nz;
+  g.z_rest = (kb_rest + g.kps_rest - 1) / g.kps_rest;
+  g.z0 = (g.kb_seg + kX3Kps0 - 1) / kX3Kps0;
+  g.bytes_a = align256((size_t)g.Mr * g.pitch * 2);
+  g.bytes_b = align256((size_t)g.Nr * g.pitch * 2);
+  g.bytes_p = (size_t)(g.z_rest + g.z0) * g.Mr * g.Nr * sizeof(float);
+  return g;
+}
+
+static void x3_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alpha,
+                        const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
+                        double2* C, int64_t ldc, cudaStream_t st) {
+  const X3Geom g = x3_geom(conjA, M, N, K);
+  const int64_t Mr = g.Mr, Nr = g.Nr, seg = g.seg, pitch = g.pitch;
+  const int nz = g.z_rest + g.z0;
+  ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
+  char* base = s.ws_oz.p;
+  __nv_bfloat16* pA = (__nv_bfloat16*)base;
+  __nv_bfloat16* pB = (__nv_bfloat16*)(base + g.bytes_a);
+  float* part = (float*)(base + g.bytes_a + g.bytes_b);
+
+  TimedScope ts(s, KF_GEMM_X3, st, 2.0 * X3_TERMS * (double)Mr * Nr * (double)seg,
+                16.0 * ((double)M * K + (double)K * N) + 2.0 * X3_S * ((double)Mr + Nr) * seg * 2.0 +
+                    8.0 * nz * (double)Mr * Nr + 16.0 * (double)M * N);
+  if (conjA) {
+    k_x3_slice_cols<<<dim3((unsigned)((seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg,
+                                                                              pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_x3_slice_cols<<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+                                                                              pB, pitch);
+    PWH_LAUNCH_CHECK();
+  } else {
+    k_x3_slice_rows<<<dim3((M + 31) / 32, (unsigned)((seg / 2 + 31) / 32)), 256, 0, st>>>(
+        A, lda, M, K, (int)seg, pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_x3_slice_b2<<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+                                                                            pB, pitch);
+    PWH_LAUNCH_CHECK();
+  }
+  CUtensorMap ma = make_map(pA, Mr, pitch, pitch, TC_BM);
+  CUtensorMap mb = make_map(pB, Nr, pitch, pitch, TC_BN);
+  TcArgs a{};
+  a.M = (int)Mr;
+  a.N = (int)Nr;
+  a.kb_seg = g.kb_seg;
+  a.terms = X3_TERMS;
+  a.kb_per_split = g.kps_rest;
+  a.z_rest = g.z_rest;
+  a.kps0 = kX3Kps0;
+  a.part = part;
+  a.err = device_error_word(s);
+  a.oz = 2;
+  // slice pairs (s, t) with s + t <= 2, the leading pair first
+  const unsigned char ta[X3_TERMS] = {0, 0, 1, 0, 1, 2}, tb[X3_TERMS] = {0, 1, 0, 2, 1, 0};
+  for (int p = 0; p < X3_TERMS; ++p) {
+    a.oz_a[p] = ta[p];
+    a.oz_b[p] = tb[p];
+  }
+  dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), nz);
+  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  PWH_LAUNCH_CHECK();
+  X3Out o;
+  o.alpha = alpha;
+  o.beta = beta;
+  o.af = (float)alpha.x;
+  const bool ar = alpha.y == 0.0 && (double)o.af == alpha.x;
+  o.mode = ar && beta.x == 0.0 && beta.y == 0.0 ? 0 : ar && beta.x == 1.0 && beta.y == 0.0 ? 1 : 2;
+  const int64_t tot = (int64_t)M * N;
+  if (nz > 8 && N <= 65535) {
+    const dim3 rg((unsigned)((M + 31) / 32), (unsigned)N);
+    if (conjA)
+      k_x3_reduce_wide<true><<<rg, 256, 0, st>>>(part, nz, M, N, o, C, ldc);
+    else
+      k_x3_reduce_wide<false><<<rg, 256, 0, st>>>(part, nz, M, N, o, C, ldc);
+  } else if (conjA) {
+    k_x3_reduce<true><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nz, M, N, o, C, ldc);
+  } else {
+    k_x3_reduce<false><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, nz, M, N, o, C, ldc);
+  }
+  PWH_LAUNCH_CHECK();
+}
+
+void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+             int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+             cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  // K segments of whole 512-wide real ranges (512 complex K for A^H B, 256
+  // for A B) while the partials of the whole product pass the cap
+  int kseg = K;
+  const X3Geom g = x3_geom(conjA, M, N, K);
+  if (g.bytes_p > kX3PartCap) {
+    // one short partial per 512 real K, at most 2 * 152 / tiles long ones
+    const size_t plane = (size_t)g.Mr * g.Nr * sizeof(float);
+    const int64_t units = std::max<int64_t>(1, (int64_t)(kX3PartCap / plane) - (2 * 152 + g.tiles - 1) / g.tiles);
+    kseg = (int)std::min<int64_t>(K, units * (conjA ? 512 : 256));
+  }
+  for (int k0 = 0; k0 == 0 || k0 < K; k0 += kseg) {
+    const int kk = std::min(kseg, K - k0);
+    x3_gemm_seg(s, conjA, M, N, kk, alpha, A + (conjA ? (int64_t)k0 : (int64_t)k0 * lda), lda,
+                B + k0, ldb, k0 == 0 ? beta : make_double2(1, 0), C, ldc, st);
+  }
 }
 
 }  // namespace pwh

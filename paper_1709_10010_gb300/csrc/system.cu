@@ -28,7 +28,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 const char* const kKernelFamilyName[KF_COUNT] = {
     "fft_z_inverse_fp64", "fft_plane_fp64", "fft_z_forward_fp64", "fft_z_inverse_fp32",
     "fft_plane_fp32", "fft_z_forward_fp32", "tc_gemm_becp", "tc_gemm_backproj", "cgemm_fp64",
-    "cgemm_fp32", "jacobi_fp64", "cholqr_fp64", "jacobi_fp32", "zgemm_fp64_tc"};
+    "cgemm_fp32", "jacobi_fp64", "cholqr_fp64", "jacobi_fp32", "zgemm_fp64_tc", "zgemm_fp32_tc"};
 
 cudaEvent_t KernelTimer::get() {
   if (!pool.empty()) {

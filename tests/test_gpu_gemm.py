@@ -79,3 +79,27 @@ def test_gemm_fp64_pieces(env, M, N, K, conj_a):
     scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
     bar = 4e-15 * scale * abs(alpha) + 4e-15 * abs(beta) * np.abs(C0).max()
     assert np.abs(C - ref).max() <= bar, (np.abs(C - ref).max(), bar)
+
+
+# The eigensolver's coefficient pairs (alpha, beta) = (1, 0) and (-1, 1) take
+# the FP32 epilogue of the tensor-core FP32 path; general pairs are covered
+# above.
+@pytest.mark.parametrize("M,N,K,conj_a", [(384, 128, 34265, True), (34265, 128, 384, False),
+                                          (128, 64, 34265, True)])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-1.0, 1.0)])
+def test_gemm_mixed_solver_coefficients(env, M, N, K, conj_a, alpha, beta):
+    torch, s = env
+    rng = np.random.default_rng([M, N, K, int(conj_a), int(beta)])
+    A = cplx(rng, K, M) if conj_a else cplx(rng, M, K)
+    B = cplx(rng, K, N)
+    C0 = cplx(rng, M, N)
+    opA = A.conj().T if conj_a else A
+    ref = alpha * (opA @ B) + beta * C0
+    dev = lambda X: torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    Ct = dev(C0)
+    s.gemm(dev(A), dev(B), Ct, conj_a=conj_a, alpha=alpha, beta=beta, precision="mixed")
+    s.sync()
+    C = Ct.cpu().numpy().T
+    scale = np.sqrt(K) * np.abs(A).max() * np.abs(B).max()
+    bar = 4e-7 * scale + 4e-15 * abs(beta) * np.abs(C0).max()
+    assert np.abs(C - ref).max() <= bar, (np.abs(C - ref).max(), bar)
