@@ -456,6 +456,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     oz_reserve(s, true, s.nproj, nb, (int)npw);
     oz_reserve(s, false, (int)npw, nb, s.nproj);
   }
+  // and of the reduced phase (FP32-equivalent products of the same shapes)
+  if (o.mixed) {
+    x3_reserve(s, true, mmax, mmax, (int)npw);
+    x3_reserve(s, false, (int)npw, nb, mmax);
+  }
   if (o.mixed && o.jd_inner > 0)
     ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);

@@ -45,6 +45,8 @@ void oz_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const do
 void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
              int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
              cudaStream_t st);
+// Grow the workspace x3_gemm shares with oz_gemm for op(A) B of these sizes.
+void x3_reserve(System& s, bool conjA, int M, int N, int K);
 // Products of at least this many flops (8 M N K) take x3_gemm in cgemm_f32.
 constexpr double kX3MinFlops = 4e8;
 

@@ -1451,6 +1451,25 @@ static void x3_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alph
   PWH_LAUNCH_CHECK();
 }
 
+// K per segment: whole 512-wide real ranges (512 complex K for A^H B, 256 for
+// A B) while the partials of the whole product pass the cap.
+static int x3_kseg(bool conjA, int M, int N, int K) {
+  const X3Geom g = x3_geom(conjA, M, N, K);
+  if (g.bytes_p <= kX3PartCap) return K;
+  // one short partial per 512 real K, at most 2 * 152 / tiles long ones
+  const size_t plane = (size_t)g.Mr * g.Nr * sizeof(float);
+  const int64_t units =
+      std::max<int64_t>(1, (int64_t)(kX3PartCap / plane) - (2 * 152 + g.tiles - 1) / g.tiles);
+  return (int)std::min<int64_t>(K, units * (conjA ? 512 : 256));
+}
+
+void x3_reserve(System& s, bool conjA, int M, int N, int K) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  // the first segment is the largest
+  const X3Geom g = x3_geom(conjA, M, N, x3_kseg(conjA, M, N, K));
+  ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
+}
+
 void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
              int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
              cudaStream_t st) {
@@ -1459,16 +1478,7 @@ void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const do
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
   });
-  // K segments of whole 512-wide real ranges (512 complex K for A^H B, 256
-  // for A B) while the partials of the whole product pass the cap
-  int kseg = K;
-  const X3Geom g = x3_geom(conjA, M, N, K);
-  if (g.bytes_p > kX3PartCap) {
-    // one short partial per 512 real K, at most 2 * 152 / tiles long ones
-    const size_t plane = (size_t)g.Mr * g.Nr * sizeof(float);
-    const int64_t units = std::max<int64_t>(1, (int64_t)(kX3PartCap / plane) - (2 * 152 + g.tiles - 1) / g.tiles);
-    kseg = (int)std::min<int64_t>(K, units * (conjA ? 512 : 256));
-  }
+  const int kseg = x3_kseg(conjA, M, N, K);
   for (int k0 = 0; k0 == 0 || k0 < K; k0 += kseg) {
     const int kk = std::min(kseg, K - k0);
     x3_gemm_seg(s, conjA, M, N, kk, alpha, A + (conjA ? (int64_t)k0 : (int64_t)k0 * lda), lda,
