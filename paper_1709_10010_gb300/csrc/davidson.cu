@@ -544,7 +544,19 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       // Newton-Schulz step (complex GEMMs of 8 m^3 each)
       const double sw32 = w.h_idx[4101];
       const int ngemm32 = (warm ? 3 : 0) + (polish ? 0 : 3);
-      s.timer.flops[KF_JACOBI32] += sw32 * (m - 1) * 30.0 * (double)m * m + ngemm32 * 8.0 * (double)m * m * m;
+      double fj;
+      if (w.dense.last_block) {
+        // block Jacobi (b = ceil(m/32)): per round and CTA the inner sweep
+        // ((2b-1) rounds of b^2 2x2 blocks and 2b^2 V updates) and the
+        // column and row updates (2 x 128 b^3 complex MACs); Q from the log:
+        // per round and row 64 b^2 complex MACs
+        const double bb = (double)((m + 31) / 32);
+        const double round = 16.0 * ((2 * bb - 1) * (48.0 * bb * bb + 32.0 * bb * bb) + 2048.0 * bb * bb * bb);
+        fj = sw32 * 31.0 * (round + (double)m * 512.0 * bb * bb);
+      } else {
+        fj = sw32 * (m - 1) * 30.0 * (double)m * m;
+      }
+      s.timer.flops[KF_JACOBI32] += fj + ngemm32 * 8.0 * (double)m * m * m;
     }
     s.timer.resolve();
     S.iters = it;

@@ -8,6 +8,7 @@ struct DenseWs {
   DevBuf<char> jac, chol;
   DevBuf<char> jlog;    // rotation log of the cluster Jacobi
   void* ctl = nullptr;  // barrier words and flags of the Jacobi launch
+  bool last_block = false;  // the last FP32 stage ran the block Jacobi
   ~DenseWs() {
     if (jac.p) cudaFree(jac.p);
     if (chol.p) cudaFree(chol.p);
