@@ -9,7 +9,8 @@
 // (tournament positions c and 31 - c).  In a round every CTA
 //   * takes the 2b x 2b diagonal block S of its pair from the columns it holds
 //     and runs one cyclic Jacobi sweep over S (2b - 1 inner rounds inside the
-//     CTA), accumulating the unitary V with V^H S V nearly diagonal;
+//     CTA), accumulating the unitary V with V^H S V nearly diagonal, then one
+//     Newton-Schulz step on V;
 //   * publishes V; after a cluster barrier it applies A <- J^H A J, J the
 //     direct sum of every pair's V, to its own 2b columns: X <- X V_c, then
 //     for each pair d the rows of d's blocks, X[L_d] <- V_d^H X[L_d];
@@ -179,10 +180,24 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_bjacobi_dsm(BjArgs a) {
         }
         __syncthreads();
       }
-      // (3) publish V (and log it) for the other CTAs
+      // (3) one Newton-Schulz step towards the nearest unitary, V (3I - V^H V)/2
+      //     (the product of 2b - 1 FP32 rotation steps drifts from unitary by
+      //     more than one rotation; a congruence by a non-unitary V would move
+      //     the eigenvalues), published (and logged) for the other CTAs; S,
+      //     free after the inner sweep, holds (3I - V^H V)/2
       for (int e = tid; e < tb2; e += nth) {
-        Vp[(size_t)par * tb2 + e] = V[e];
-        if (t < a.log_rounds) a.logV[((size_t)t * 16 + me) * tb2 + e] = V[e];
+        const int u = e % tb, v = e / tb;
+        float2 g = z;
+        for (int k = 0; k < tb; ++k) g = add<float>(g, mulc<float>(V[k * tb + v], V[k * tb + u]));
+        S[u * ldS + v] = make_float2(((u == v ? 3.f : 0.f) - g.x) * 0.5f, -g.y * 0.5f);
+      }
+      __syncthreads();
+      for (int e = tid; e < tb2; e += nth) {
+        const int u = e / tb, v = e % tb;
+        float2 y = z;
+        for (int k = 0; k < tb; ++k) y = add<float>(y, mul<float>(V[u * tb + k], S[k * ldS + v]));
+        Vp[(size_t)par * tb2 + e] = y;
+        if (t < a.log_rounds) a.logV[((size_t)t * 16 + me) * tb2 + e] = y;
       }
       if (tid == 0 && t < a.log_rounds) a.logB[(size_t)t * 16 + me] = P0 | (P1 << 16);
       cluster.sync();
