@@ -288,6 +288,13 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
 // integer products (oz_gemm); PWH_GEMM_FP64_SIMT=1 in the environment keeps
 // every FP64 product on the FP64 pipe.
 
+// The sliced tensor-core paths launch one block row per column of A (A^H B)
+// and of B along grid y, and K / 64 blocks along grid y of the A B slicing:
+// sizes past those grid limits stay on the SIMT kernels.
+static bool slice_grid_ok(bool conjA, int M, int N, int K) {
+  return N <= 65535 && (conjA ? M <= 65535 : K <= 65535 * 32);
+}
+
 template <typename T>
 void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
            const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
@@ -297,7 +304,8 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
       const char* e = std::getenv("PWH_GEMM_FP64_SIMT");
       return e && e[0] == '1';
     }();
-    if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kOzMinFlops) {
+    if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kOzMinFlops &&
+        slice_grid_ok(conjA, M, N, K)) {
       oz_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
       return;
     }
@@ -324,7 +332,8 @@ void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const 
   // reduction cost more than it saves below about 48 columns of A^H B and 96
   // of A B)
   const int narrow = conjA ? std::min(M, N) : N;
-  if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96)) {
+  if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
+      slice_grid_ok(conjA, M, N, K)) {
     x3_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     return;
   }

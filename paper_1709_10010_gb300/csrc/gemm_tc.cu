@@ -963,7 +963,11 @@ struct OzSplit {
 };
 static OzSplit oz_split_of(bool conjA, int M, int N, int K) {
   OzSplit sp{K, M >= N, M >= N ? M : N};
-  const OzGeom g = oz_geom(conjA, M, N, K);
+  // at most 2048 chunks a segment (28 x chunks partials along grid z): 2^20
+  // real K, in chunks of at least 512 (a divisor of at least 8 blocks)
+  const int kmax = conjA ? (1 << 20) : (1 << 19);
+  if (K > kmax) sp.kseg = kmax;
+  const OzGeom g = oz_geom(conjA, M, N, sp.kseg);
   if (g.bytes_p <= kOzPartCap) return sp;
   const size_t per_chunk = g.bytes_p / (size_t)g.nchunk;
   if (g.nchunk > 1) {
@@ -971,7 +975,7 @@ static OzSplit oz_split_of(bool conjA, int M, int N, int K) {
     // 512 for A B, whose real K is 2K)
     const int64_t c = std::max<int64_t>(1, (int64_t)(kOzPartCap / per_chunk));
     const int64_t kc = conjA ? 1024 : 512;
-    if (c < g.nchunk) sp.kseg = (int)std::min<int64_t>(K, c * kc);
+    if (c < g.nchunk) sp.kseg = (int)std::min<int64_t>(sp.kseg, c * kc);
   }
   const OzGeom gs = oz_geom(conjA, M, N, sp.kseg);
   if (gs.bytes_p <= kOzPartCap) return sp;
