@@ -5,9 +5,10 @@
 One step = one full eigensolve of the medium workload (cubic cell a = 20 bohr,
 64 atoms, 40 Ry: 34,265 plane waves, FFT box 90^3, 576 projectors; lowest 128
 bands from seeded random starting bands to max ||H x - theta x|| <= 1e-8 Ha) in
-mixed precision (FP32 FFT + BF16 tensor-core projector GEMMs, FP64
-Rayleigh-Ritz / Cholesky / final refinement; Jacobi-Davidson corrections from
-the reduced-precision operator near and after the hand-over to FP64).  Every
+mixed precision (a reduced-precision phase of FP32 FFTs, BF16 tensor-core
+projector GEMMs, FP32-equivalent tensor-core subspace GEMMs, FP32 Jacobi and
+Cholesky; then FP64 Rayleigh-Ritz, Cholesky and residuals, with
+Jacobi-Davidson corrections from the reduced-precision operator).  Every
 row of the hot path runs
 inside a step: H|psi> (scatter, FFTs, V, kinetic, becp, D, back-projection),
 subspace overlaps, Cholesky-QR, Jacobi, residuals, preconditioner.
@@ -45,7 +46,7 @@ SWITCH_TOL = 1e-3
 JD_INNER = 20
 MULT = 3
 # Fallback peaks (no measured-peaks file on this machine): HBM copy bandwidth
-# and the derived CUDA-core arithmetic peaks (measurement).
+# and the derived CUDA-core arithmetic peaks (lanes x FMA x clock).
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_ALU_TFLOPS = 1.25     # nominal FP64 rate of the part
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
@@ -132,6 +133,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_over_ranks(dist, elapsed, units, device):
+    """Replicas: the slowest rank's time and the units of all ranks (max and
+    sum over the process group; unchanged without one)."""
+    if dist is None:
+        return elapsed, units
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
 # ------------------------------------------------------------------ ours ----
 def run_ours(a):
     import torch
@@ -206,15 +220,7 @@ def run_ours(a):
     ktimes = s.kernel_times()
     s.set_kernel_timing(False)
     clk = clocks.stop() if clocks else None
-    t_max = elapsed
-    tot_apply = n_apply
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([float(n_apply)], device="cuda")
-        dist.all_reduce(c)
-        tot_apply = float(c.item())
+    t_max, tot_apply = reduce_over_ranks(dist, elapsed, n_apply, "cuda")
     if rank != 0:
         dist.destroy_process_group() if dist is not None else None
         return
