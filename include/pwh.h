@@ -335,8 +335,9 @@ pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t 
  * HOST double[2] (re, im).  precision PWH_FP64: FP64 arithmetic (products of
  * at least 2e8 flops as exact integer-slice products on the tensor cores);
  * PWH_MIXED: operands rounded to FP32, FP32 accumulation (relative error about
- * sqrt(K) 1e-7), result widened (products of at least 4e8 flops as three BF16
- * slices of each FP32 operand, six slice products on the tensor cores).
+ * sqrt(K) 1e-7), result widened (products of at least 4e8 flops and 48
+ * columns of A^H B or 96 of A B as three BF16 slices of each FP32 operand, six
+ * slice products on the tensor cores).
  * Asynchronous on the system's stream; uses the system's workspaces (one GEMM
  * at a time per system). */
 pwh_status pwh_subspace_gemm(pwh_system* sys, int32_t precision, int32_t conj_a, int32_t M,
