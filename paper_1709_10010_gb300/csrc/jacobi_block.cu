@@ -202,9 +202,11 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_bjacobi_dsm(BjArgs a) {
       if (tid == 0 && t < a.log_rounds) a.logB[(size_t)t * 16 + me] = P0 | (P1 << 16);
       cluster.sync();
 
-      // (4) own columns X (N x 2b) <- X V: item (row i, half h) makes the
-      //     outputs v = h b .. h b + b - 1 of row i (2N <= 768 items)
+      // (4) own columns X (N x 2b) <- X V, V the published (refined) copy:
+      //     item (row i, half h) makes the outputs v = h b .. h b + b - 1 of
+      //     row i (2N <= 768 items)
       {
+        const float2* Vc = Vp + (size_t)par * tb2;
         const bool act = tid < 2 * N;
         const int i = act ? tid % N : 0, h = act ? tid / N : 0;
         float2 x[kBjMaxTb];
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_bjacobi_dsm(BjArgs a) {
               float2 y = z;
 #pragma unroll
               for (int u = 0; u < kBjMaxTb; ++u)
-                if (u < tb) y = add<float>(y, mul<float>(x[u], V[u * tb + v]));
+                if (u < tb) y = add<float>(y, mul<float>(x[u], Vc[u * tb + v]));
               col(v)[i] = y;
             }
           }
