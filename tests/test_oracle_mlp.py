@@ -110,3 +110,38 @@ def test_targets_recover_a_planted_diagonal():
     E2[shell == 2, 0] *= -1
     y2, w2 = om.targets_from_corrections(shell, nshell, T, R, E2, eref)
     assert w2.reshape(nb, nshell)[0, 2] == 0.0
+
+
+def test_targets_closed_form_exact_correction():
+    """Pin of the exact correction inside ``targets``: take orthonormal converged
+    bands X* and Ritz vectors X = X* U + eps Z with Z orthogonal to span(X*).
+    The projector on span(X*) maps X to X* U, so the exact correction is
+    e = P* x - x = -eps Z, known in closed form.  With residuals built as
+    R = eps Z / d_g per shell, the best per-shell factor is d_g (> 0), so the
+    targets must equal log d_g - log K_TPA minus the band's weighted mean, with
+    every present shell weighted.  A sign slip (x - P* x), a transposed
+    projector or the projector's complement breaks one of these."""
+    rng = np.random.default_rng(11)
+    nshell, npw, nb, eps = 6, 80, 3, 1e-2
+    shell = np.concatenate([np.arange(nshell), rng.integers(0, nshell, npw - nshell)])
+    T = np.linspace(0.1, 4.0, nshell)
+    M = rng.standard_normal((npw, npw)) + 1j * rng.standard_normal((npw, npw))
+    Qf, _ = np.linalg.qr(M)
+    Xstar = Qf[:, :nb]
+    Z = Qf[:, nb:nb + nb] @ (rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb)))
+    U, _ = np.linalg.qr(rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb)))
+    X = Xstar @ U + eps * Z
+    d = rng.uniform(0.2, 3.0, (nb, nshell))
+    R = eps * Z / d.T[shell]
+    eref = np.array([0.9, 1.4, 2.2])
+    y, w = om.targets(shell, nshell, T, X, R, Xstar, eref)
+    y, w = y.reshape(nb, nshell), w.reshape(nb, nshell)
+    x = T[None, :] / eref[:, None]
+    raw = np.log(d) - np.log(om.tpa(x))
+    for n in range(nb):
+        assert np.all(w[n] > 0)
+        assert abs(w[n].sum() - 1.0) < 1e-12
+        np.testing.assert_allclose(y[n], raw[n] - np.sum(w[n] * raw[n]), atol=1e-10)
+    # the weights are the residual's share per shell
+    den = np.array([[np.sum(np.abs(R[shell == g, n]) ** 2) for g in range(nshell)] for n in range(nb)])
+    np.testing.assert_allclose(w, den / den.sum(axis=1, keepdims=True), rtol=1e-12)
