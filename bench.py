@@ -2,23 +2,28 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one full eigensolve of the medium workload (cubic cell a = 20 bohr,
-64 atoms, 40 Ry: 34,265 plane waves, FFT box 90^3, 576 projectors; lowest 128
-bands from seeded random starting bands to max ||H x - theta x|| <= 1e-8 Ha) in
-mixed precision (a reduced-precision phase of FP32 FFTs, BF16 tensor-core
-projector GEMMs, FP32-equivalent tensor-core subspace GEMMs, FP32 Jacobi and
-Cholesky; then FP64 Rayleigh-Ritz, Cholesky and residuals, with
-Jacobi-Davidson corrections from the reduced-precision operator).  Every
-row of the hot path runs
-inside a step: H|psi> (scatter, FFTs, V, kinetic, becp, D, back-projection),
-subspace overlaps, Cholesky-QR, Jacobi, residuals, preconditioner.
+One step = one full eigensolve of the large workload (cubic cell a = 30 bohr,
+216 atoms, 50 Ry: 161,235 plane waves, FFT box 144^3, 1,944 s,p,d projectors;
+lowest 512 bands from seeded random starting bands to max ||H x - theta x|| <=
+1e-8 Ha) in mixed precision: a reduced-precision phase (FP32 FFTs, BF16
+tensor-core projector GEMMs, FP32-equivalent tensor-core subspace GEMMs, FP32
+Jacobi and Cholesky), then Jacobi-Davidson steps whose Rayleigh-Ritz,
+Cholesky and residuals run in FP64.  Every row of the hot path runs inside a
+step: H|psi> (scatter, FFTs, V, kinetic, becp, D, back-projection), subspace
+overlaps, Cholesky-QR, Jacobi, residuals, preconditioner.
 
-value = band-applies of H per second through the whole solver (all bands to
-which H was applied, in any precision, divided by the solve time); ms_per_step
-is the time-to-1e-8-residual.  The same line carries the plain FP64 GPU solve
-of the same system (mixed vs FP64), H|psi>-only throughputs, the roofline of
-the dominant kernel, the end-to-end number through host buffers, the oracle's
-CPU throughput and the SM clocks seen during the timed region.
+value = band-applies of H per second through the solver (all bands to which H
+was applied, in any precision, divided by the solve time); ms_per_step is the
+time-to-1e-8-residual.  The same line carries:
+  * the plain FP64 GPU solve of the same system (mixed vs FP64);
+  * steady-state H|psi>-only throughput on the 512 resident bands (median of
+    20 CUDA-event-timed applications, FP64 and mixed);
+  * the roofline of the dominant kernel family, from a separate solve with the
+    library's per-family event timer on (not inside the timed region);
+  * the end-to-end solve through the C ABI with host buffers;
+  * the medium cell (34,265 plane waves, 128 bands) and the batched workload as
+    secondary lines;
+  * the oracle's CPU throughput and the SM clocks seen during the timed region.
 
 Multi-GPU (torchrun): independent replicas, one per GPU (different seeds), no
 data-path collective; value sums all ranks' band-applies over the slowest
@@ -40,11 +45,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Hpsi band-applies/s and Davidson time-to-1e-8 residual, mixed vs FP64, 1 GB300"
-WORKLOAD = "medium"
+WORKLOAD = "large"
 TOL = 1e-8
 SWITCH_TOL = 1e-3
 JD_INNER = 20
 MULT = 3
+HPSI_REPS = 20      # H|psi>-only repeats (median reported)
+E2E_STEPS = 3       # end-to-end solves through host buffers
 # Fallback peaks (no measured-peaks file on this machine): HBM copy bandwidth
 # and the derived CUDA-core arithmetic peaks (lanes x FMA x clock).
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
@@ -60,6 +67,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison solve")
     p.add_argument("--skip-batched", action="store_true", help="omit the batched cells x k-points solve")
+    p.add_argument("--skip-medium", action="store_true", help="omit the medium-cell secondary line")
+    p.add_argument("--workload", default=WORKLOAD, choices=["large", "medium"],
+                   help="system of the timed solves (default: the large cell)")
     p.add_argument("--profile", action="store_true",
                    help="for a profiler's launch list: only the warm-up and timed solves, a short "
                         "JSON line (no FP64 solve, H-only, e2e, batched or CPU legs)")
@@ -75,13 +85,6 @@ def peaks():
         except Exception:
             pass
     return dict(FALLBACK), "fallback"
-
-
-def setup_inputs(seed):
-    from paper_1709_10010_gb300 import synthetic as syn
-    cfg = syn.CONFIGS[WORKLOAD]
-    cell = syn.config_cell(WORKLOAD, seed)
-    return cfg, cell
 
 
 class ClockSampler:
@@ -147,6 +150,45 @@ def reduce_over_ranks(dist, elapsed, units, device):
 
 
 # ------------------------------------------------------------------ ours ----
+def make_system(pwh, syn, cell, precision="mixed", stream=None):
+    s = pwh.System.from_cell(cell, precision=precision, stream=stream)
+    v = syn.potential_grid(cell, s.fft)
+    beta = syn.projectors(cell, s.miller())
+    D = syn.d_diagonal(cell)
+    s.set_potential(v)
+    s.set_projectors(beta, D)
+    return s, v, beta, D
+
+
+def timed(torch, stream, fn):
+    """fn() bracketed by CUDA events on the stream; returns (seconds, result)."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3, r
+
+
+def hpsi_only(torch, s, psi0, reps=HPSI_REPS):
+    """Steady-state H|psi> throughput on the resident bands: median over reps
+    CUDA-event-timed applications, per precision."""
+    out = torch.empty_like(psi0)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for prec in ("fp64", "mixed"):
+        s.set_precision(prec)
+        for _ in range(3):
+            s.apply_h(psi0, out)
+        ts = [timed(torch, stream, lambda: s.apply_h(psi0, out))[0] for _ in range(reps)]
+        med = statistics.median(ts)
+        res[prec] = {"band_applies_s": psi0.shape[0] / med, "median_ms": 1e3 * med,
+                     "repeats": reps}
+    s.set_precision("mixed")
+    return res
+
+
 def run_ours(a):
     import torch
     import paper_1709_10010_gb300 as pwh
@@ -170,15 +212,10 @@ def run_ours(a):
 
     from paper_1709_10010_gb300 import build
     build.build()
-    cfg, cell = setup_inputs(seed=rank)
+    cfg = syn.CONFIGS[a.workload]
+    cell = syn.config_cell(a.workload, seed=rank)
     nb = cfg["nb"]
-    s = pwh.System.from_cell(cell, precision="mixed")
-    miller = s.miller()
-    v = syn.potential_grid(cell, s.fft)
-    beta = syn.projectors(cell, miller)
-    D = syn.d_diagonal(cell)
-    s.set_potential(v)
-    s.set_projectors(beta, D)
+    s, v, beta, D = make_system(pwh, syn, cell)
     psi0_h = syn.initial_bands(rank, s.npw, nb)
     psi0 = torch.from_numpy(psi0_h).cuda()
     psi = torch.empty_like(psi0)
@@ -193,16 +230,14 @@ def run_ours(a):
         solve()
     torch.cuda.synchronize()
 
-    # ---- timed region: K full mixed-precision solves
+    # ---- timed region: K full mixed-precision solves to 1e-8 (no kernel timer)
     clocks = ClockSampler(dev) if rank == 0 else None
     if clocks:
         clocks.start()
-    s.set_kernel_timing(True)
     launches0 = pwh.launch_count()
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("bench_timed")
     e0.record(stream)
     n_apply, stats = 0, []
     eig = None
@@ -212,13 +247,10 @@ def run_ours(a):
         n_apply += st["n_apply"]
         stats.append(st)
     e1.record(stream)
-    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier()
     elapsed = e0.elapsed_time(e1) / 1e3
     launches = pwh.launch_count() - launches0
-    ktimes = s.kernel_times()
-    s.set_kernel_timing(False)
     clk = clocks.stop() if clocks else None
     t_max, tot_apply = reduce_over_ranks(dist, elapsed, n_apply, "cuda")
     if rank != 0:
@@ -228,97 +260,93 @@ def run_ours(a):
     if a.profile:
         print(json.dumps({"metric": METRIC, "value": tot_apply / t_max, "unit": "band-applies/s",
                           "ms_per_step": ms_per_step, "steps": a.steps, "warmup": a.warmup,
-                          "profile_run": True, "gpu_launches": int(launches)}))
+                          "profile_run": True, "gpu_launches": int(launches),
+                          "workload": a.workload}))
         return
+
+    # ---- per-family kernel times: one more solve with the library's event
+    # timer on (a separate pass, outside the timed region)
+    s.set_kernel_timing(True)
+    solve()
+    torch.cuda.synchronize()
+    ktimes = s.kernel_times()
+    s.set_kernel_timing(False)
 
     # ---- mixed vs FP64: one plain FP64 solve of the same system
     fp64 = None
     if not a.skip_fp64:
-        psi.copy_(psi0)
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        eig64, st64, status64 = s.davidson(psi, tol=TOL, mult=MULT, mixed=False)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fp64 = {"time_s": f0.elapsed_time(f1) / 1e3, "iters": st64["iters"],
-                "n_apply": st64["n_apply"], "status": status64,
+        t64, (eig64, st64, status64) = timed(torch, stream, lambda: solve(mixed=False))
+        fp64 = {"time_s": t64, "iters": st64["iters"], "n_apply": st64["n_apply"],
+                "status": status64,
                 "max_abs_dlambda_mixed_vs_fp64_ha": float(np.abs(eig - eig64).max())}
 
-    # ---- H|psi> alone (128 bands), FP64 and mixed
-    hpsi_only = {}
-    out = torch.empty_like(psi0)
-    for prec in ("fp64", "mixed"):
-        s.set_precision(prec)
-        for _ in range(3):
-            s.apply_h(psi0, out)
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 10 if prec == "mixed" else 3
-        h0.record(stream)
-        for _ in range(reps):
-            s.apply_h(psi0, out)
-        h1.record(stream)
-        torch.cuda.synchronize()
-        hpsi_only[prec] = nb * reps / (h0.elapsed_time(h1) / 1e3)
-    s.set_precision("mixed")
+    # ---- H|psi> alone on the 512 resident bands, FP64 and mixed
+    hp = hpsi_only(torch, s, psi0)
 
-    # ---- end to end through host buffers (pinned), copies inside the timed region
-    pin_in = torch.from_numpy(psi0_h).pin_memory()
-    pin_out = torch.empty_like(pin_in).pin_memory()
-    dbuf = torch.empty_like(psi0)
-    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_apply = 0
-    torch.cuda.synchronize()
-    ee0.record(stream)
-    for _ in range(a.steps):
-        dbuf.copy_(pin_in, non_blocking=True)
-        eig_e, st_e, status_e = s.davidson(dbuf, tol=TOL, mult=MULT, mixed=True,
-                                           switch_tol=SWITCH_TOL, jd_inner=JD_INNER)
-        pin_out.copy_(dbuf, non_blocking=True)
+    # ---- end to end through the C ABI with host buffers: pwh_davidson_solve_host
+    # copies the pinned starting bands in and the eigenvectors out inside the call
+    pin = torch.from_numpy(psi0_h).pin_memory()
+    pin_np = pin.numpy()
+    e2e_steps = min(a.steps, E2E_STEPS)
+    e2e_apply, e2e_time = 0, 0.0
+    for _ in range(e2e_steps):
+        pin_np[...] = psi0_h
+        t0 = time.perf_counter()
+        _, st_e, status_e = s.davidson_host(pin_np, tol=TOL, mult=MULT, mixed=True,
+                                            switch_tol=SWITCH_TOL, jd_inner=JD_INNER)
+        e2e_time += time.perf_counter() - t0
+        assert status_e == 0, status_e
         e2e_apply += st_e["n_apply"]
-    ee1.record(stream)
-    torch.cuda.synchronize()
-    e2e_time = ee0.elapsed_time(ee1) / 1e3
     bi = psi0_h.nbytes
     bo = psi0_h.nbytes + nb * 8
 
+    # ---- the medium cell (34,265 plane waves, 128 bands) as a secondary line
+    medium = None if (a.skip_medium or a.workload == "medium") else run_medium(pwh, syn, torch)
     # ---- batched workload: 32 cells x 8 k-points solved concurrently
     batched = None if a.skip_batched else run_batched(pwh, syn, torch)
 
-    # ---- roofline of the dominant kernel family of the timed region
-    roof = roofline(ktimes)
+    # ---- roofline of the dominant kernel family of a solve
+    roof = roofline(ktimes, s)
 
     # ---- CPU baseline: the oracle on a bounded sample of the same workload
-    cpu = cpu_baseline(cell, s, v, beta, D, psi0_h)
+    cpu = cpu_baseline(cell, s.npw, s.fft, v, beta, D, psi0_h)
 
     med = stats[len(stats) // 2]
+    ktot = sum(x["ms"] for x in ktimes.values())
     line = {
         "metric": METRIC, "value": tot_apply / t_max, "unit": "band-applies/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
         "data": "synthetic (seeded cell, Gaussian potential and projectors, random start)",
-        "config": {"workload": f"{WORKLOAD}: a=20 bohr cubic, 64 atoms, 40 Ry, npw={s.npw}, "
-                               f"FFT {s.fft[0]}^3, {beta.shape[0]} projectors, lowest {nb} bands "
-                               f"to 1e-8, mixed precision",
+        "config": {"workload": f"{a.workload}: a={cfg['a']:g} bohr cubic, {cfg['natoms']} atoms, "
+                               f"{cfg['ecut_ry']:g} Ry, npw={s.npw}, FFT {s.fft[0]}^3, "
+                               f"{beta.shape[0]} projectors, lowest {nb} bands to max||r|| <= 1e-8, "
+                               f"mixed precision + Jacobi-Davidson",
                    "npw": s.npw, "fft": list(s.fft), "nproj": int(beta.shape[0]), "nb": nb,
                    "tol": TOL, "switch_tol": SWITCH_TOL, "jd_inner": JD_INNER, "m_max": MULT * nb,
-                   "l2": "working set (V, HV: 2 x npw x m_max x 16 B = 421 MB) larger than L2",
+                   "step": "one full eigensolve from the seeded random start to 1e-8",
+                   "l2": f"inputs larger than L2 (V, HV: 2 x npw x m_max x 16 B = "
+                         f"{2 * s.npw * MULT * nb * 16 / 1e9:.1f} GB; FP64 beta {beta.nbytes / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world}"},
-        "time_to_1e-8_s": {"mixed": ms_per_step / 1e3, "fp64": fp64["time_s"] if fp64 else None},
+        "time_to_1e-8_s": {"mixed": ms_per_step / 1e3, "fp64": fp64["time_s"] if fp64 else None,
+                           "fp64_over_mixed": (fp64["time_s"] / (ms_per_step / 1e3)) if fp64 else None},
         "davidson": {"mixed": {k: med[k] for k in ("iters", "n_apply", "n_apply_fp64",
                                                    "switch_iter", "t_mixed_s", "t_fp64_s",
                                                    "max_resid")},
                      "fp64": fp64},
-        "hpsi_only_band_applies_s": hpsi_only,
+        "hpsi_only": hp,
+        "medium": medium,
         "batched": batched,
         "kernels": {k: {"launches": d["launches"], "ms": round(d["ms"], 3),
-                        "share": round(d["ms"] / max(1e-9, sum(x["ms"] for x in ktimes.values())), 4),
+                        "share": round(d["ms"] / max(1e-9, ktot), 4),
                         "frac": (lambda r: None if r is None or r["frac"] is None else round(r["frac"], 4))(
-                            family_roofline(k, d))}
+                            family_roofline(k, d, s))}
                     for k, d in ktimes.items() if d["launches"]},
         "roofline": roof,
         "e2e": {"value": e2e_apply / e2e_time, "unit": "band-applies/s",
                 "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
-                "time_to_1e-8_s": e2e_time / a.steps},
+                "time_to_1e-8_s": e2e_time / e2e_steps, "steps": e2e_steps,
+                "entry_point": "pwh_davidson_solve_host (pinned host bands in and out)"},
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,
         "clocks": clk,
@@ -326,6 +354,36 @@ def run_ours(a):
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_medium(pwh, syn, torch):
+    """The medium cell (a = 20 bohr, 64 atoms, 40 Ry: 34,265 plane waves, 90^3,
+    576 projectors), lowest 128 bands: mixed + Jacobi-Davidson (median of three
+    solves after one warm-up) and one plain FP64 solve, CUDA-event timed."""
+    cell = syn.config_cell("medium", 0)
+    nb = syn.CONFIGS["medium"]["nb"]
+    s, v, beta, D = make_system(pwh, syn, cell)
+    psi0 = torch.from_numpy(syn.initial_bands(0, s.npw, nb)).cuda()
+    psi = torch.empty_like(psi0)
+    stream = torch.cuda.current_stream()
+
+    def solve(mixed):
+        psi.copy_(psi0)
+        return s.davidson(psi, tol=TOL, mult=MULT, mixed=mixed, switch_tol=SWITCH_TOL,
+                          jd_inner=JD_INNER if mixed else 0)
+    solve(True)
+    ts = [timed(torch, stream, lambda: solve(True)) for _ in range(3)]
+    tmix = statistics.median(t for t, _ in ts)
+    eig = ts[-1][1][0]
+    t64, (eig64, st64, _) = timed(torch, stream, lambda: solve(False))
+    hp = hpsi_only(torch, s, psi0)
+    s.close()
+    return {"workload": f"medium: a=20 bohr, 64 atoms, 40 Ry, npw={s.npw}, 90^3, 576 projectors, "
+                        f"{nb} bands", "time_to_1e-8_s": {"mixed": tmix, "fp64": t64},
+            "fp64_over_mixed": t64 / tmix, "iters": {"mixed": ts[-1][1][1]["iters"],
+                                                     "fp64": st64["iters"]},
+            "max_abs_dlambda_mixed_vs_fp64_ha": float(np.abs(eig - eig64).max()),
+            "hpsi_only": hp}
 
 
 def run_batched(pwh, syn, torch, ncells=32, nthreads=16):
@@ -383,7 +441,14 @@ FAMILY_BOUND = {
 }
 
 
-def family_roofline(fam, d):
+# DRAM traffic per unit of work of a kernel family, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum per launch divided by the
+# units that launch processed; summaries and commands under profiles/).
+# Families missing here report traffic null.
+TRAFFIC_PER_UNIT = {}
+
+
+def family_roofline(fam, d, s=None):
     pk, src = peaks()
     bound, counter, key = FAMILY_BOUND[fam]
     if d["launches"] == 0:
@@ -402,77 +467,85 @@ def family_roofline(fam, d):
     else:
         peak, unit, psrc = FP64_ALU_TFLOPS, "TFLOP/s", "nominal FP64 rate"
         achieved = work / sec / 1e12
+    traffic = None
+    if fam in TRAFFIC_PER_UNIT and d.get("units"):
+        traffic = TRAFFIC_PER_UNIT[fam] * d["units"] / d["launches"]
     return {"kernel": fam, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": (achieved / peak) if (peak and work) else None, "traffic": None,
+            "frac": (achieved / peak) if (peak and work) else None, "traffic": traffic,
             "avg_launch_ms": d["ms"] / d["launches"], "peak_source": psrc}
 
 
-def roofline(kt):
-    """Roofline of the kernel family with the largest device time in the timed
-    region (CUDA events on the solver's stream), its algorithmic work per launch
+def roofline(kt, s=None):
+    """Roofline of the kernel family with the largest device time in a solve
+    (CUDA events on the solver's stream), its algorithmic work per launch
     divided by its average launch duration."""
     fams = {k: v for k, v in kt.items() if v["launches"]}
     fam = max(fams, key=lambda k: fams[k]["ms"])
     tot = sum(v["ms"] for v in fams.values())
-    r = family_roofline(fam, fams[fam])
+    r = family_roofline(fam, fams[fam], s)
     r["share_of_timed_kernels"] = fams[fam]["ms"] / tot
     return r
 
 
-def cpu_baseline(cell, s, v, beta, D, psi0_h, iters=1):
-    """The oracle (numpy FP64) on a bounded sample: the first Davidson iteration
-    of the same workload (H applied to the 128 starting bands, Rayleigh-Ritz,
-    residuals)."""
+CPU_SAMPLE_BANDS = 16   # bands per oracle H application in the CPU baseline
+REF_SAMPLE_BANDS = 4    # bands per step of the reference arm
+
+
+def oracle_apply(cell, v, beta, D, psi_h):
+    """The oracle's FP64 H (FFT route) on the host cores; returns seconds."""
     from oracle import basis as ob
-    from oracle import davidson as od
     from oracle import hamiltonian as oh
     b = ob.sphere(cell.lattice, cell.kpoint, cell.ecut_ha)
-    t = time.time()
-    res = od.davidson(lambda X: oh.apply_h(b, v, beta, D, X.T).T, b.kinetic, psi0_h.T,
-                      psi0_h.shape[0], tol=TOL, max_iter=iters, m_max=MULT * psi0_h.shape[0])
-    dt = time.time() - t
-    return {"value": res.n_apply / dt, "unit": "band-applies/s", "cores": len(os.sched_getaffinity(0)),
-            "kind": "oracle", "sample": f"{iters} Davidson iteration(s) of the same workload "
-                                         f"({res.n_apply} band-applies, {dt:.1f} s)"}
+    t = time.perf_counter()
+    oh.apply_h(b, v, beta, D, psi_h)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(cell, npw, fft, v, beta, D, psi0_h, nbands=CPU_SAMPLE_BANDS):
+    """The oracle (numpy FP64) on a bounded sample of the same workload: one
+    application of H to the first `nbands` starting bands (scatter, 3D FFTs,
+    potential, gather, kinetic, projector products), band-applies/s."""
+    dt = oracle_apply(cell, v, beta, D, psi0_h[:nbands])
+    return {"value": nbands / dt, "unit": "band-applies/s", "cores": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": f"H applied to {nbands} of the {psi0_h.shape[0]} starting "
+                                         f"bands of the same workload ({dt:.1f} s)"}
 
 
 # ------------------------------------------------------------- reference ----
 def run_reference(a):
-    """The oracle as the reference arm: each step a bounded sample (one Davidson
-    iteration, 128 band-applies) of the same workload on the host cores."""
+    """The oracle as the reference arm: each step a bounded sample of the same
+    workload on the host cores (H applied to REF_SAMPLE_BANDS bands)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1709_10010_gb300 import synthetic as syn
     from oracle import basis as ob
-    cfg, cell = setup_inputs(seed=0)
+    cfg = syn.CONFIGS[WORKLOAD]
+    cell = syn.config_cell(WORKLOAD, 0)
     b = ob.sphere(cell.lattice, cell.kpoint, cell.ecut_ha)
     v = syn.potential_grid(cell, b.fft)
     beta = syn.projectors(cell, b.miller)
     D = syn.d_diagonal(cell)
     psi0 = syn.initial_bands(0, b.npw, cfg["nb"])
-
-    class S:
-        npw = b.npw
-    for _ in range(a.warmup):
-        cpu_baseline(cell, S, v, beta, D, psi0[:8])
-    vals, t_all, n_all = [], 0.0, 0
-    for _ in range(a.steps):
-        r = cpu_baseline(cell, S, v, beta, D, psi0)
-        vals.append(r["value"])
-        n_all += cfg["nb"]
-        t_all += cfg["nb"] / r["value"]
-    value = n_all / t_all
+    nb = REF_SAMPLE_BANDS
+    for i in range(a.warmup):
+        oracle_apply(cell, v, beta, D, psi0[:1])
+    t_all = 0.0
+    for i in range(a.steps):
+        j = (i * nb) % cfg["nb"]
+        t_all += oracle_apply(cell, v, beta, D, psi0[j:j + nb])
+    value = nb * a.steps / t_all
+    sample = f"H applied to {nb} of the {cfg['nb']} starting bands per step"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "band-applies/s",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * t_all / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: a=20 bohr cubic, 64 atoms, 40 Ry, npw={b.npw}, "
-                                   f"{beta.shape[0]} projectors, 128 bands; bounded sample: "
-                                   f"one Davidson iteration per step"},
+            "config": {"workload": f"large: a=30 bohr cubic, 216 atoms, 50 Ry, npw={b.npw}, "
+                                   f"{beta.shape[0]} projectors, {cfg['nb']} bands; bounded "
+                                   f"sample: {sample}"},
             "cpu_baseline": {"value": value, "unit": "band-applies/s",
                              "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                             "sample": "one Davidson iteration (128 band-applies) per step"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "band-applies/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

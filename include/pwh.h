@@ -213,6 +213,17 @@ typedef struct {
 pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                               int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
 
+/* pwh_davidson_solve with the bands in HOST memory: psi_host holds nb
+ * contiguous columns of length npw (ld = npw, public order, complex128),
+ * starting bands in, eigenvectors out.  The library copies them to a device
+ * buffer it owns (allocated on first use, kept with the system), solves on the
+ * system's stream and copies the eigenvectors back before returning.  Pinned
+ * host memory gives the fastest copies; pageable memory works.  Same status
+ * codes as pwh_davidson_solve; on PWH_ERR_NOT_CONVERGED the results are still
+ * copied back. */
+pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_host,
+                                   double* eig, pwh_davidson_stats* stats);
+
 /* ----------------------------------------------------- learned preconditioner --
  * Not in the paper.  A 4 -> 64 -> 64 -> 1 SiLU network corrects the TPA
  * diagonal per (shell of equal |k+G|, band): K = K_TPA * exp(clip(s, -3, 3)),

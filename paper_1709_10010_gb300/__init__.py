@@ -93,6 +93,8 @@ SIGNATURES = {
     "pwh_launch_count": (_c_i32, [ctypes.POINTER(_c_i64)]),
     "pwh_davidson_solve": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
                                     ctypes.POINTER(DavidsonStats)]),
+    "pwh_davidson_solve_host": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_p,
+                                         ctypes.POINTER(DavidsonStats)]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_subspace_gemm": (_c_i32, [_c_p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_p, _c_p, _c_i64,
                                    _c_p, _c_i64, _c_p, _c_p, _c_i64]),
@@ -414,6 +416,26 @@ class System:
         eig = np.zeros(nb, dtype=np.float64)
         status = lib().pwh_davidson_solve(self._h, ctypes.byref(o), p, ld,
                                           eig.ctypes.data_as(_c_p), ctypes.byref(st))
+        if check and status not in (0,):
+            _check(status)
+        return eig, st.as_dict(), status
+
+    def davidson_host(self, psi: np.ndarray, tol=1e-8, max_iter=200, mult=3, precond="tpa",
+                      mixed=False, switch_tol=1e-5, jd_inner=0, check=True):
+        """davidson() with the bands in host memory: psi (nb, npw) C-contiguous
+        complex128 numpy array (pinned memory copies fastest), starting bands
+        in, eigenvectors out; the copies run inside the library call."""
+        if not (isinstance(psi, np.ndarray) and psi.dtype == np.complex128 and psi.ndim == 2
+                and psi.shape[1] == self.npw and psi.flags.c_contiguous):
+            raise ValueError(f"expected a C-contiguous complex128 array of shape (nb, {self.npw})")
+        nb = int(psi.shape[0])
+        o = DavidsonOpts(nb=nb, max_iter=int(max_iter), max_subspace_mult=int(mult),
+                         precond=PRECOND[precond], mixed=int(bool(mixed)), jd_inner=int(jd_inner),
+                         tol=float(tol), switch_tol=float(max(switch_tol, tol)))
+        st = DavidsonStats()
+        eig = np.zeros(nb, dtype=np.float64)
+        status = lib().pwh_davidson_solve_host(self._h, ctypes.byref(o), psi.ctypes.data_as(_c_p),
+                                               eig.ctypes.data_as(_c_p), ctypes.byref(st))
         if check and status not in (0,):
             _check(status)
         return eig, st.as_dict(), status

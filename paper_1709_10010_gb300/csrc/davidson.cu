@@ -728,3 +728,24 @@ extern "C" pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opt
   });
   return g != PWH_OK ? g : st;
 }
+
+extern "C" pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opts,
+                                              void* psi_host, double* eig,
+                                              pwh_davidson_stats* stats) {
+  pwh_status st = PWH_OK;
+  pwh_status g = guarded([&] {
+    PWH_CHECK_ARG(sys && opts && psi_host && eig, "null argument");
+    System& s = sys->s;
+    PWH_CHECK_ARG(opts->nb >= 1 && opts->nb <= 1024, "nb out of range [1, 1024]");
+    const size_t n = (size_t)s.npw * opts->nb;
+    // the device copy of the bands lives in the library's host-transfer buffer
+    ensure(s.ws_host, n * sizeof(double2));
+    double2* d = (double2*)s.ws_host.p;
+    PWH_CUDA(cudaMemcpyAsync(d, psi_host, n * sizeof(double2), cudaMemcpyHostToDevice, s.stream));
+    st = pwh_davidson_solve(sys, opts, d, s.npw, eig, stats);
+    if (st != PWH_OK && st != PWH_ERR_NOT_CONVERGED) throw Error{st, pwh_last_error()};
+    PWH_CUDA(cudaMemcpyAsync(psi_host, d, n * sizeof(double2), cudaMemcpyDeviceToHost, s.stream));
+    PWH_CUDA(cudaStreamSynchronize(s.stream));
+  });
+  return g != PWH_OK ? g : st;
+}

@@ -604,8 +604,13 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
   unsigned* ctl = (unsigned*)w.ctl;
   PWH_CUDA(cudaMemsetAsync(ctl, 0, 64, st));
-  int* out_buf = (int*)(ctl + 8);  // FP64 stage: result buffer index, sweeps
-  int* ob32 = (int*)(ctl + 10);    // FP32 stage: result buffer index, sweeps
+  // The 16 control words of w.ctl:
+  //   0-2   grid barrier of launch_jacobi (count, generation, abort)
+  //   4-6   FP32 stage: result buffer index, sweeps, rounds logged
+  //   8-9   FP64 stage: result buffer index, sweeps
+  //   12    convergence flag of the grid-wide kernel (launch_jacobi)
+  int* out_buf = (int*)(ctl + 8);
+  int* ob32 = (int*)(ctl + 4);
   const int gq = (int)std::min<int64_t>(1024, ((int64_t)nn + 255) / 256);
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
   const bool warm = warm_m0 > 0 && Qkeep;
