@@ -68,8 +68,12 @@ def parse():
     p.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison solve")
     p.add_argument("--skip-batched", action="store_true", help="omit the batched cells x k-points solve")
     p.add_argument("--skip-medium", action="store_true", help="omit the medium-cell secondary line")
-    p.add_argument("--workload", default=WORKLOAD, choices=["large", "medium"],
+    p.add_argument("--workload", default=WORKLOAD, choices=["large", "medium", "small"],
                    help="system of the timed solves (default: the large cell)")
+    p.add_argument("--mult", type=int, default=MULT, help="m_max = mult x nb")
+    p.add_argument("--hpsi-only", choices=["mixed", "fp64"], default=None,
+                   help="for profilers: W + K applications of H (this precision) to the "
+                        "workload's bands, a short JSON line, nothing else")
     p.add_argument("--profile", action="store_true",
                    help="for a profiler's launch list: only the warm-up and timed solves, a short "
                         "JSON line (no FP64 solve, H-only, e2e, batched or CPU legs)")
@@ -223,8 +227,21 @@ def run_ours(a):
 
     def solve(mixed=True):
         psi.copy_(psi0)
-        return s.davidson(psi, tol=TOL, mult=MULT, mixed=mixed, switch_tol=SWITCH_TOL,
+        return s.davidson(psi, tol=TOL, mult=a.mult, mixed=mixed, switch_tol=SWITCH_TOL,
                           jd_inner=JD_INNER if mixed else 0)
+
+    if a.hpsi_only:
+        s.set_precision(a.hpsi_only)
+        out = torch.empty_like(psi0)
+        for _ in range(a.warmup):
+            s.apply_h(psi0, out)
+        t, _ = timed(torch, stream, lambda: [s.apply_h(psi0, out) for _ in range(a.steps)])
+        s.sync()
+        print(json.dumps({"metric": "H band-applies/s", "value": nb * a.steps / t,
+                          "ms_per_apply": 1e3 * t / a.steps, "precision": a.hpsi_only,
+                          "workload": a.workload, "nb": nb, "steps": a.steps,
+                          "warmup": a.warmup}))
+        return
 
     for _ in range(a.warmup):
         solve()
@@ -292,7 +309,7 @@ def run_ours(a):
     for _ in range(e2e_steps):
         pin_np[...] = psi0_h
         t0 = time.perf_counter()
-        _, st_e, status_e = s.davidson_host(pin_np, tol=TOL, mult=MULT, mixed=True,
+        _, st_e, status_e = s.davidson_host(pin_np, tol=TOL, mult=a.mult, mixed=True,
                                             switch_tol=SWITCH_TOL, jd_inner=JD_INNER)
         e2e_time += time.perf_counter() - t0
         assert status_e == 0, status_e
@@ -323,10 +340,10 @@ def run_ours(a):
                                f"{beta.shape[0]} projectors, lowest {nb} bands to max||r|| <= 1e-8, "
                                f"mixed precision + Jacobi-Davidson",
                    "npw": s.npw, "fft": list(s.fft), "nproj": int(beta.shape[0]), "nb": nb,
-                   "tol": TOL, "switch_tol": SWITCH_TOL, "jd_inner": JD_INNER, "m_max": MULT * nb,
+                   "tol": TOL, "switch_tol": SWITCH_TOL, "jd_inner": JD_INNER, "m_max": a.mult * nb,
                    "step": "one full eigensolve from the seeded random start to 1e-8",
                    "l2": f"inputs larger than L2 (V, HV: 2 x npw x m_max x 16 B = "
-                         f"{2 * s.npw * MULT * nb * 16 / 1e9:.1f} GB; FP64 beta {beta.nbytes / 1e9:.1f} GB)",
+                         f"{2 * s.npw * a.mult * nb * 16 / 1e9:.1f} GB; FP64 beta {beta.nbytes / 1e9:.1f} GB)",
                    "parallelism": f"replicas x{world}"},
         "time_to_1e-8_s": {"mixed": ms_per_step / 1e3, "fp64": fp64["time_s"] if fp64 else None,
                            "fp64_over_mixed": (fp64["time_s"] / (ms_per_step / 1e3)) if fp64 else None},

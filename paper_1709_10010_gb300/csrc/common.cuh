@@ -201,6 +201,8 @@ struct System {
   int32_t* d_stick_col = nullptr;
   int32_t* d_stick_y = nullptr;
   int32_t* d_col_x = nullptr;
+  int32_t* d_stick_at = nullptr;   // ncols x n2: stick of (column, y grid index), -1 if none
+  int16_t* d_xcol = nullptr;       // n1: column of each x grid index, -1 if none
   FftPlan plan[3];
   double2* d_tw64 = nullptr;        // twiddle tables, FP64
   float2* d_tw32 = nullptr;         // same, rounded to FP32

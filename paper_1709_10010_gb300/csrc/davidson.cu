@@ -35,7 +35,6 @@ struct DavWs {
   DevBuf<char> cg;     // Jacobi-Davidson PCG: r, z, p, q (npw x nb each), scalars
   DevBuf<char> mlp;    // learned-preconditioner factors (k x nshell)
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
-  DevBuf<char> xs;     // X sliced for the projections of one correction call
   DenseWs dense;
   double* h_rn = nullptr;  // pinned host mirrors
   int* h_idx = nullptr;
@@ -44,7 +43,6 @@ struct DavWs {
     if (cg.p) cudaFree(cg.p);
     if (mlp.p) cudaFree(mlp.p);
     if (small.p) cudaFree(small.p);
-    if (xs.p) cudaFree(xs.p);
     if (h_rn) cudaFreeHost(h_rn);
     if (h_idx) cudaFreeHost(h_idx);
   }
@@ -300,30 +298,12 @@ struct Layout {
 static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
                   const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
                   double2* C, int64_t ldc, cudaStream_t st);
-// xs (optional): X sliced by x3_slice_a for both products (A^H layout at xs,
-// A layout after it), made once per correction call.
 static void project_out(System& s, const double2* X, int nb, double2* v, int k, double2* W,
-                        cudaStream_t st, const char* xs = nullptr) {
+                        cudaStream_t st) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
   const int64_t npw = s.npw;
-  const char* xn = xs ? xs + x3_a_bytes(true, nb, (int)npw) : nullptr;
-  if (!(xs && x3_gemm_presliced(s, true, nb, k, (int)npw, one, xs, v, npw, zero, W, nb, st)))
-    sgemm(s, PWH_MIXED, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
-  if (!(xn && x3_gemm_presliced(s, false, (int)npw, k, nb, mone, xn, W, nb, one, v, npw, st)))
-    sgemm(s, PWH_MIXED, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
-}
-
-// PWH_JD_PRESLICE=1 in the environment: the projections of a correction call
-// share one slicing of X (FP32-equivalent tensor-core products).
-static bool jd_preslice_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("PWH_JD_PRESLICE");
-    return e && e[0] == '1';
-  }();
-  return on;
-}
-static size_t jd_preslice_bytes(int64_t npw, int nb) {
-  return x3_a_bytes(true, nb, (int)npw) + x3_a_bytes(false, (int)npw, nb);
+  sgemm(s, PWH_MIXED, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
+  sgemm(s, PWH_MIXED, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
 }
 
 // Approximate solution t (npw x k) of (I-XX^H)(H-theta_j)(I-XX^H) t_j = -r_j
@@ -342,18 +322,11 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
   double* rho[2] = {(double*)(q + (size_t)npw * k), (double*)(q + (size_t)npw * k) + k};
   double* pq = rho[1] + k;
   const dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (npw + 255) / 256)), k);
-  const char* xs = nullptr;
-  if (jd_preslice_enabled()) {
-    ensure(w.xs, jd_preslice_bytes(npw, nb));
-    x3_slice_a(s, true, nb, (int)npw, X, npw, w.xs.p, st);
-    x3_slice_a(s, false, (int)npw, nb, X, npw, w.xs.p + x3_a_bytes(true, nb, (int)npw), st);
-    xs = w.xs.p;
-  }
   k_cg_init<<<g2, 256, 0, st>>>(R, npw, npw, idx, r, t);
   PWH_LAUNCH_CHECK();
   k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
   PWH_LAUNCH_CHECK();
-  project_out(s, X, nb, z, k, Wc, st, xs);
+  project_out(s, X, nb, z, k, Wc, st);
   PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[0]);
   PWH_LAUNCH_CHECK();
@@ -363,7 +336,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     *n_apply += k;
     k_cg_shift<<<g2, 256, 0, st>>>(q, p, npw, idx, theta);
     PWH_LAUNCH_CHECK();
-    project_out(s, X, nb, q, k, Wc, st, xs);
+    project_out(s, X, nb, q, k, Wc, st);
     k_col_dot<<<k, 1024, 0, st>>>(p, q, npw, pq);
     PWH_LAUNCH_CHECK();
     k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[cur], pq);
@@ -371,7 +344,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     if (it + 1 == iters) break;
     k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
     PWH_LAUNCH_CHECK();
-    project_out(s, X, nb, z, k, Wc, st, xs);
+    project_out(s, X, nb, z, k, Wc, st);
     k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[cur ^ 1]);
     PWH_LAUNCH_CHECK();
     k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[cur ^ 1], rho[cur]);
@@ -493,7 +466,6 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   }
   if (o.mixed && o.jd_inner > 0) {
     ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
-    if (jd_preslice_enabled()) ensure(w.xs, jd_preslice_bytes(npw, nb));
   }
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
   const int tpa = o.precond == PWH_PRECOND_TPA ? 1 : 0;
@@ -576,18 +548,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       // Newton-Schulz step (complex GEMMs of 8 m^3 each)
       const double sw32 = w.h_idx[4101];
       const int ngemm32 = (warm ? 3 : 0) + (polish ? 0 : 3);
-      double fj;
-      if (w.dense.last_block) {
-        // block Jacobi (b = ceil(m/32)): per round and CTA the inner sweep
-        // ((2b-1) rounds of b^2 2x2 blocks and 2b^2 V updates) and the
-        // column and row updates (2 x 128 b^3 complex MACs); Q from the log:
-        // per round and row 64 b^2 complex MACs
-        const double bb = (double)((m + 31) / 32);
-        const double round = 16.0 * ((2 * bb - 1) * (48.0 * bb * bb + 32.0 * bb * bb) + 2048.0 * bb * bb * bb);
-        fj = sw32 * 31.0 * (round + (double)m * 512.0 * bb * bb);
-      } else {
-        fj = sw32 * (m - 1) * 30.0 * (double)m * m;
-      }
+      const double fj = sw32 * (m - 1) * 30.0 * (double)m * m;
       s.timer.flops[KF_JACOBI32] += fj + ngemm32 * 8.0 * (double)m * m * m;
     }
     s.timer.resolve();

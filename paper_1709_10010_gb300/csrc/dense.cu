@@ -632,9 +632,7 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
     // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
     // convergence) usually finishes.  The whole matrix in one cluster's shared
     // memory when it fits, else through global memory.
-    w.last_block = jacobi32_block_enabled() &&
-                   jacobi32_block(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st);
-    if (!w.last_block && !jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
+    if (!jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
       k_c64_to_c32<<<gq, 256, 0, st>>>(start, ld_start, n, a0);
       PWH_LAUNCH_CHECK();
       k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity
@@ -704,8 +702,6 @@ void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   ensure(w.jac, jacobi_ws_bytes(nn, nmax));
   ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
   if (nmax >= 64 && nmax <= 512) ensure(w.jlog, jacobi32_log_bytes(nmax, 30));
-  if (jacobi32_block_enabled() && nmax >= 64 && nmax <= 384)
-    ensure(w.jlog, jacobi32_block_log_bytes(nmax, 30));
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
 }
 

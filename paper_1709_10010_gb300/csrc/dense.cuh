@@ -8,7 +8,6 @@ struct DenseWs {
   DevBuf<char> jac, chol;
   DevBuf<char> jlog;    // rotation log of the cluster Jacobi
   void* ctl = nullptr;  // barrier words and flags of the Jacobi launch
-  bool last_block = false;  // the last FP32 stage ran the block Jacobi
   ~DenseWs() {
     if (jac.p) cudaFree(jac.p);
     if (chol.p) cudaFree(chol.p);
@@ -46,19 +45,10 @@ bool jacobi32_cluster(System& s, DenseWs& w, const double2* A, int64_t lda, int 
                       cudaStream_t st);
 // Bytes of the rotation log of jacobi32_cluster for an n x n matrix.
 size_t jacobi32_log_bytes(int n, int max_sweeps);
-// The same contract as block Jacobi in one cluster (jacobi_block.cu): 32
-// blocks of ceil(n/32) indices paired by a tournament, one inner Jacobi sweep
-// per block pair and round, 31 cluster rounds a sweep; 64 <= n <= 384.  Off
-// unless PWH_JACOBI_BLOCK=1 is set in the environment.
-bool jacobi32_block(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
-                    int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
-                    cudaStream_t st);
-size_t jacobi32_block_log_bytes(int n, int max_sweeps);
-bool jacobi32_block_enabled();
 
 // Device words holding the number of FP64 / FP32 sweeps of the last jacobi_eigh.
 inline int* jacobi_sweeps_word(DenseWs& w) { return (int*)w.ctl + 9; }
-inline int* jacobi32_sweeps_word(DenseWs& w) { return (int*)w.ctl + 11; }
+inline int* jacobi32_sweeps_word(DenseWs& w) { return (int*)w.ctl + 5; }
 
 // Grow the workspaces for subspaces up to nmax and Cholesky blocks up to kmax
 // (so that no allocation, hence no device-wide synchronisation, happens later).

@@ -318,12 +318,8 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   const double fp = 2.0 * s.n3 * (ncol * 5.0 * s.n2 * l2(s.n2) + s.n2 * 5.0 * s.n1 * l2(s.n1));
   const double bw = cz * (double)s.nsticks * s.n3;                          // one W slice
   const double bv = sizeof(T) * (double)s.n1 * s.n2 * s.n3;                 // V, once per launch
-  // compile-time specialised kernels for cubic boxes of the common sizes
-  // (PWH_FFT_GENERIC=1 in the environment selects the runtime-plan kernels)
-  static const bool use_spec = [] {
-    const char* e = std::getenv("PWH_FFT_GENERIC");
-    return !(e && e[0] == '1');
-  }();
+  // compile-time specialised kernels for cubic boxes of the common sizes,
+  // the runtime-plan kernels for every other box
   for (int b0 = 0; b0 < nb; b0 += batch) {
     int bb = std::min(batch, nb - b0);
     dim3 gz((s.nsticks + spb - 1) / spb, bb);
@@ -331,7 +327,7 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
                       zsmem, rows, psmem, bb, V, tw, st};
     {
       TimedScope ts(s, dp ? KF_FFT_ZINV64 : KF_FFT_ZINV32, st, bb * fz, bb * (16.0 * s.npw + bw));
-      if (!(use_spec && spec_pass<T>(SPEC_ZINV, s, pa))) {
+      if (!spec_pass<T>(SPEC_ZINV, s, pa)) {
         k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
                                            s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
         PWH_LAUNCH_CHECK();
@@ -340,7 +336,7 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
     dim3 gp(s.n3, bb);
     {
       TimedScope ts(s, dp ? KF_FFT_PLANE64 : KF_FFT_PLANE32, st, bb * fp, bb * 2.0 * bw + bv);
-      if (!(use_spec && spec_pass<T>(SPEC_PLANE, s, pa))) {
+      if (!spec_pass<T>(SPEC_PLANE, s, pa)) {
         k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
                                             s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
         PWH_LAUNCH_CHECK();
@@ -349,7 +345,7 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
     {
       TimedScope ts(s, dp ? KF_FFT_ZFWD64 : KF_FFT_ZFWD32, st, bb * fz,
                     bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw));
-      if (!(use_spec && spec_pass<T>(SPEC_ZFWD, s, pa))) {
+      if (!spec_pass<T>(SPEC_ZFWD, s, pa)) {
         k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
                                            s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp,
                                            ldp, hpsi + (size_t)b0 * ldh, ldh, spb);

@@ -224,58 +224,184 @@ __global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, 
   }
 }
 
-template <typename T, int N>
-__global__ void __launch_bounds__(512) ks_plane(cx<T>* __restrict__ W, int64_t wband, int nsticks,
-                                                int ncols, const int32_t* __restrict__ stick_col,
-                                                const int32_t* __restrict__ stick_y,
-                                                const int32_t* __restrict__ col_x,
-                                                const T* __restrict__ V, int tw_off,
-                                                int perm_off, const cx<T>* __restrict__ tw_g,
-                                                const int16_t* __restrict__ perm_g, int rows) {
+// ---- the plane pass: per (z-plane, band) the y transforms on the columns
+// that hold sticks, the x transforms on every row with V(r) applied between
+// them, each 1D transform the four-step N = N1 N2 of fft_nat written out as
+// two register passes whose loads and stores do the data movement too:
+//   y inverse  pass 1 loads the plane's sticks from W through stick_at (zero
+//              where no stick), pass 2 in place in C[column][y];
+//   x inverse  pass 1 loads the columns of C through xcol (zero elsewhere),
+//              pass 2 in place in R[row][x] times V(r) before the store;
+//   x forward  pass 1 in place, pass 2 stores only the columns back into C;
+//   y forward  pass 1 in place, pass 2 stores only the sticks back into W.
+// No zero fill, scatter or gather pass of its own; row chunks of `rows` rows
+// bound the shared memory.
+
+// Four-step pass 1 on registers: v[n1] = x[N2 n1 + n2] -> w^(n2 k1) DFT_N1(v)[k1]
+// (w = e^{+-2 pi i/N}), natural order out.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fs_pass1(cx<T>* v, int n2, const cx<T>* tw) {
+  constexpr int N1 = fft_factor(N);
+  const T sg = INV ? (T)1 : (T)-1;
+  dft_reg<T, N1, INV, N>(v, tw);
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) {
+    cx<T> w = tw[n2 * k1];
+    w.y *= sg;
+    v[k1] = mul<T>(v[k1], w);
+  }
+}
+
+// Four-step pass 2 in place on nf transforms of shared memory (transform f at
+// data + f ld): x[N2 k1 + n2] -> x[k1 + N1 k2], rounds of whole transforms,
+// each round loads, synchronises, then stores; `post(f, x, value)` maps an
+// output before it is stored.  Ends with __syncthreads().
+template <typename T, int N, int NT, bool INV, class Post>
+__device__ __forceinline__ void fs_pass2_inplace(cx<T>* data, int nf, int ld, const cx<T>* tw,
+                                                 Post post) {
+  constexpr int N1 = fft_factor(N), N2 = N / N1;
+  constexpr int per = NT / N1;
+  const int fl = threadIdx.x / N1, k1 = threadIdx.x - fl * N1;
+  for (int f0 = 0; f0 < nf; f0 += per) {
+    const int f = f0 + fl;
+    const bool act = fl < per && f < nf;
+    cx<T> w[N2];
+    if (act) {
+      const cx<T>* xf = data + f * ld + N2 * k1;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) w[n2] = xf[n2];
+      dft_reg<T, N2, INV, N>(w, tw);
+    }
+    __syncthreads();
+    if (act) {
+      cx<T>* xf = data + f * ld + k1;
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) xf[N1 * k2] = post(f, k1 + N1 * k2, w[k2]);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, int NT>
+__global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wband, int nsticks,
+                                               int ncols, const int32_t* __restrict__ stick_at,
+                                               const int16_t* __restrict__ xcol_g,
+                                               const T* __restrict__ V, int tw_off,
+                                               const cx<T>* __restrict__ tw_g, int rows) {
+  constexpr int N1 = fft_factor(N), N2 = N / N1, LD = N + 1;
+  static_assert(N1 > 1 && N1 <= 16 && N2 <= 16, "factor");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int ld = N + 1;
-  cx<T>* C = (cx<T>*)smem_raw;           // ncols x ld
-  cx<T>* Rw = C + (size_t)ncols * ld;    // rows x ld
-  cx<T>* tw = Rw + (size_t)rows * ld;
-  int16_t* irev = (int16_t*)(tw + N);
+  cx<T>* C = (cx<T>*)smem_raw;             // ncols x LD: columns along y
+  cx<T>* R = C + (size_t)ncols * LD;       // rows x LD: rows along x
+  cx<T>* tw = R + (size_t)rows * LD;       // e^{2 pi i t/N}
+  int16_t* xcol = (int16_t*)(tw + N);      // column of each x, -1 if none
   const int z = blockIdx.x, b = blockIdx.y;
   cx<T>* plane = W + (size_t)b * wband + (size_t)z * nsticks;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+  for (int t = threadIdx.x; t < N; t += NT) {
     tw[t] = tw_g[tw_off + t];
-    irev[t] = perm_g[perm_off + t];
+    xcol[t] = xcol_g[t];
   }
-  for (int t = threadIdx.x; t < ncols * ld; t += blockDim.x) C[t] = mk<T>(0, 0);
   __syncthreads();
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
-    C[stick_col[s] * ld + stick_y[s]] = plane[s];
+  const cx<T> zero = mk<T>(0, 0);
+
+  // ---- y inverse: sticks -> C
+  for (int t = threadIdx.x; t < ncols * N2; t += NT) {
+    const int c = t / N2, n2 = t - c * N2;
+    const int32_t* sa = stick_at + (size_t)c * N + n2;
+    cx<T> v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+      const int st = sa[N2 * n1];
+      v[n1] = st >= 0 ? plane[st] : zero;
+    }
+    fs_pass1<T, N, true>(v, n2, tw);
+    cx<T>* cc = C + c * LD + n2;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) cc[N2 * k1] = v[k1];
+  }
   __syncthreads();
-  fft_nat<T, true, N>(C, ncols, ld, tw);
+  fs_pass2_inplace<T, N, NT, true>(C, ncols, LD, tw, [](int, int, cx<T> v) { return v; });
+
+  // ---- rows: x inverse, times V, x forward; keep the columns
   const T* Vz = V + (size_t)z * N * N;
   for (int y0 = 0; y0 < N; y0 += rows) {
     const int nr = min(rows, N - y0);
-    for (int t = threadIdx.x; t < nr * ld; t += blockDim.x) Rw[t] = mk<T>(0, 0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
-      const int r = t / ncols, c = t - r * ncols;
-      Rw[r * ld + col_x[c]] = C[c * ld + y0 + r];
+    for (int t = threadIdx.x; t < nr * N2; t += NT) {
+      const int r = t / N2, n2 = t - r * N2;
+      cx<T> v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) {
+        const int c = xcol[N2 * n1 + n2];
+        v[n1] = c >= 0 ? C[c * LD + y0 + r] : zero;
+      }
+      fs_pass1<T, N, true>(v, n2, tw);
+      cx<T>* rr = R + r * LD + n2;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
     }
     __syncthreads();
-    fft_nat<T, true, N>(Rw, nr, ld, tw);
-    for (int t = threadIdx.x; t < nr * N; t += blockDim.x) {
-      const int r = t / N, x = t - r * N;
-      Rw[r * ld + x] = scl<T>(Rw[r * ld + x], Vz[(size_t)(y0 + r) * N + x]);
+    const T* Vy = Vz + (size_t)y0 * N;
+    fs_pass2_inplace<T, N, NT, true>(R, nr, LD, tw, [Vy](int r, int x, cx<T> v) {
+      return scl<T>(v, Vy[(size_t)r * N + x]);
+    });
+    for (int t = threadIdx.x; t < nr * N2; t += NT) {
+      const int r = t / N2, n2 = t - r * N2;
+      cx<T>* rr = R + r * LD + n2;
+      cx<T> v[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) v[n1] = rr[N2 * n1];
+      fs_pass1<T, N, false>(v, n2, tw);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
     }
     __syncthreads();
-    fft_nat<T, false, N>(Rw, nr, ld, tw);
-    for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
-      const int r = t / ncols, c = t - r * ncols;
-      C[c * ld + y0 + r] = Rw[r * ld + col_x[c]];
+    for (int t = threadIdx.x; t < nr * N1; t += NT) {
+      const int r = t / N1, k1 = t - r * N1;
+      const cx<T>* rr = R + r * LD + N2 * k1;
+      cx<T> w[N2];
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) w[n2] = rr[n2];
+      dft_reg<T, N2, false, N>(w, tw);
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int c = xcol[k1 + N1 * k2];
+        if (c >= 0) C[c * LD + y0 + r] = w[k2];
+      }
     }
     __syncthreads();
   }
-  fft_nat<T, false, N>(C, ncols, ld, tw);
-  for (int s = threadIdx.x; s < nsticks; s += blockDim.x)
-    plane[s] = C[stick_col[s] * ld + stick_y[s]];
+
+  // ---- y forward: C -> sticks
+  for (int t = threadIdx.x; t < ncols * N2; t += NT) {
+    const int c = t / N2, n2 = t - c * N2;
+    cx<T>* cc = C + c * LD + n2;
+    cx<T> v[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) v[n1] = cc[N2 * n1];
+    fs_pass1<T, N, false>(v, n2, tw);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) cc[N2 * k1] = v[k1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncols * N1; t += NT) {
+    const int c = t / N1, k1 = t - c * N1;
+    const cx<T>* cc = C + c * LD + N2 * k1;
+    cx<T> w[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) w[n2] = cc[n2];
+    dft_reg<T, N2, false, N>(w, tw);
+    const int32_t* sa = stick_at + (size_t)c * N + k1;
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+      const int st = sa[N1 * k2];
+      if (st >= 0) plane[st] = w[k2];
+    }
+  }
+}
+
+// Shared memory of the plane pass for `rows` rows per chunk.
+template <typename T, int N> constexpr size_t ks_plane_smem(int ncols, int rows) {
+  return ((size_t)(ncols + rows) * (N + 1) + N) * sizeof(cx<T>) + N * sizeof(int16_t);
 }
 
 template <typename T, int N>
@@ -323,7 +449,7 @@ template <typename T, int N> void spec_launch(SpecPass pass, System& s, const Pa
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(ks_zinv<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(ks_plane<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(ks_plane<T, N, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     cudaFuncSetAttribute(ks_zfwd<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   const cx<T>* tw = (const cx<T>*)a.tw;
@@ -335,11 +461,24 @@ template <typename T, int N> void spec_launch(SpecPass pass, System& s, const Pa
                                                  s.nsticks, s.plan[2].tw_off, s.plan[2].perm_off, tw,
                                                  s.d_perm, W, a.wband, a.spb);
       break;
-    case SPEC_PLANE:
-      ks_plane<T, N><<<dim3(N, a.bb), 512, a.psmem, a.st>>>(
-          W, a.wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y, s.d_col_x, (const T*)a.V,
-          s.plan[0].tw_off, s.plan[0].perm_off, tw, s.d_perm, a.rows);
+    case SPEC_PLANE: {
+      // rows per chunk: equal chunks, as many rows as keep two blocks per SM
+      // (110 KB each) if that leaves at least 32 rows, else one block per SM
+      int rows = N;
+      for (size_t cap : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+        int r = N;
+        while (r > 1 && ks_plane_smem<T, N>(s.ncols, r) > cap) --r;
+        const int chunks = (N + r - 1) / r;
+        rows = (N + chunks - 1) / chunks;
+        if (ks_plane_smem<T, N>(s.ncols, rows) <= cap && (rows >= 32 || rows == N)) break;
+      }
+      const size_t smem = ks_plane_smem<T, N>(s.ncols, rows);
+      if (smem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
+      ks_plane<T, N, 512><<<dim3(N, a.bb), 512, smem, a.st>>>(
+          W, a.wband, s.nsticks, s.ncols, s.d_stick_at, s.d_xcol, (const T*)a.V, s.plan[0].tw_off,
+          tw, rows);
       break;
+    }
     case SPEC_ZFWD:
       ks_zfwd<T, N><<<gz, 256, a.zsmem, a.st>>>(W, a.wband, s.d_stick_off, s.d_stick_of, s.d_zpos,
                                                  s.nsticks, s.plan[2].tw_off, s.plan[2].perm_off, tw,

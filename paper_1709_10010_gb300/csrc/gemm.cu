@@ -285,8 +285,7 @@ static void cgemm_impl(System& s, bool conjA, int M, int N, int K, cx<TS> alpha,
 }
 
 // FP64 products of at least kOzMinFlops go to the tensor cores as sliced
-// integer products (oz_gemm); PWH_GEMM_FP64_SIMT=1 in the environment keeps
-// every FP64 product on the FP64 pipe.
+// integer products (oz_gemm).
 
 // The sliced tensor-core paths launch one block row per column of A (A^H B)
 // and of B along grid y, and K / 64 blocks along grid y of the A B slicing:
@@ -300,11 +299,7 @@ void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>*
            const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
            const double* rowscale) {
   if constexpr (sizeof(T) == 8) {
-    static const bool simt_only = [] {
-      const char* e = std::getenv("PWH_GEMM_FP64_SIMT");
-      return e && e[0] == '1';
-    }();
-    if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kOzMinFlops &&
+    if (K > 0 && 8.0 * M * (double)N * K >= kOzMinFlops &&
         slice_grid_ok(conjA, M, N, K)) {
       oz_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, rowscale);
       return;
@@ -322,17 +317,12 @@ void cgemm_f32_simt(System& s, bool conjA, int M, int N, int K, double2 alpha, c
 void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st) {
-  // large products run on the tensor cores as three-slice BF16 products;
-  // PWH_GEMM_FP32_SIMT=1 in the environment keeps them on the FP32 pipe
-  static const bool simt_only = [] {
-    const char* e = std::getenv("PWH_GEMM_FP32_SIMT");
-    return e && e[0] == '1';
-  }();
+  // large products run on the tensor cores as three-slice BF16 products
   // (narrow products stay on the FP32 pipe: the tensor-core path's slicing and
   // reduction cost more than it saves below about 48 columns of A^H B and 96
   // of A B)
   const int narrow = conjA ? std::min(M, N) : N;
-  if (!simt_only && K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
+  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
       slice_grid_ok(conjA, M, N, K)) {
     x3_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     return;

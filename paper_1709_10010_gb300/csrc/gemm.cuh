@@ -47,16 +47,6 @@ void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const do
              cudaStream_t st);
 // Grow the workspace x3_gemm shares with oz_gemm for op(A) B of these sizes.
 void x3_reserve(System& s, bool conjA, int M, int N, int K);
-// The A operand of x3_gemm sliced once for several products with the same A
-// (conjA, M, K): x3_a_bytes bytes at out (256-byte aligned device memory).
-size_t x3_a_bytes(bool conjA, int M, int K);
-void x3_slice_a(System& s, bool conjA, int M, int K, const double2* A, int64_t lda, void* out,
-                cudaStream_t st);
-// x3_gemm with A given by those slices; false (nothing launched) when the
-// product would need K segments or more than 65,535 columns.
-bool x3_gemm_presliced(System& s, bool conjA, int M, int N, int K, double2 alpha,
-                       const void* Aslices, const double2* B, int64_t ldb, double2 beta,
-                       double2* C, int64_t ldc, cudaStream_t st);
 // Products of at least this many flops (8 M N K) take x3_gemm in cgemm_f32.
 constexpr double kX3MinFlops = 4e8;
 

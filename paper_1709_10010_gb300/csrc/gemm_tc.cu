@@ -1382,37 +1382,23 @@ static X3Geom x3_geom(bool conjA, int M, int N, int K) {
   return g;
 }
 
-// One K segment.  preA (optional): the slices of A, made by x3_slice_a for the
-// same (conjA, M, K); A is then not read.
+// One K segment.
 static void x3_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alpha,
                         const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
-                        double2* C, int64_t ldc, cudaStream_t st,
-                        const __nv_bfloat16* preA = nullptr) {
+                        double2* C, int64_t ldc, cudaStream_t st) {
   const X3Geom g = x3_geom(conjA, M, N, K);
   const int64_t Mr = g.Mr, Nr = g.Nr, seg = g.seg, pitch = g.pitch;
   const int nz = g.z_rest + g.z0;
-  const __nv_bfloat16* pA;
-  __nv_bfloat16* pB;
-  float* part;
-  if (!preA) {
-    ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
-    char* base = s.ws_oz.p;
-    pA = (__nv_bfloat16*)base;
-    pB = (__nv_bfloat16*)(base + g.bytes_a);
-    part = (float*)(base + g.bytes_a + g.bytes_b);
-  } else {
-    ensure(s.ws_oz, g.bytes_b + g.bytes_p);
-    char* base = s.ws_oz.p;
-    pA = preA;
-    pB = (__nv_bfloat16*)base;
-    part = (float*)(base + g.bytes_b);
-  }
+  ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
+  char* base = s.ws_oz.p;
+  const __nv_bfloat16* pA = (__nv_bfloat16*)base;
+  __nv_bfloat16* pB = (__nv_bfloat16*)(base + g.bytes_a);
+  float* part = (float*)(base + g.bytes_a + g.bytes_b);
 
   TimedScope ts(s, KF_GEMM_X3, st, 2.0 * X3_TERMS * (double)Mr * Nr * (double)seg,
-                (preA ? 0.0 : 16.0 * (double)M * K) + 16.0 * (double)K * N +
-                    2.0 * X3_S * ((double)Mr + Nr) * seg * (preA ? 1.0 : 2.0) +
+                16.0 * (double)M * K + 16.0 * (double)K * N + 4.0 * X3_S * ((double)Mr + Nr) * seg +
                     8.0 * nz * (double)Mr * Nr + 16.0 * (double)M * N);
-  if (!preA) {
+  {
     __nv_bfloat16* wA = (__nv_bfloat16*)s.ws_oz.p;
     if (conjA)
       k_x3_slice_cols<<<dim3((unsigned)((seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg,
@@ -1491,37 +1477,6 @@ void x3_reserve(System& s, bool conjA, int M, int N, int K) {
   // the first segment is the largest
   const X3Geom g = x3_geom(conjA, M, N, x3_kseg(conjA, M, N, K));
   ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
-}
-
-size_t x3_a_bytes(bool conjA, int M, int K) { return x3_geom(conjA, M, 1, K).bytes_a; }
-
-void x3_slice_a(System& s, bool conjA, int M, int K, const double2* A, int64_t lda, void* out,
-                cudaStream_t st) {
-  if (M <= 0) return;
-  const X3Geom g = x3_geom(conjA, M, 1, K);
-  __nv_bfloat16* o = (__nv_bfloat16*)out;
-  TimedScope ts(s, KF_GEMM_X3, st, 0.0, 16.0 * (double)M * K + 2.0 * X3_S * (double)g.Mr * g.seg);
-  if (conjA)
-    k_x3_slice_cols<<<dim3((unsigned)((g.seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K,
-                                                                                (int)g.seg, o, g.pitch);
-  else
-    k_x3_slice_rows<<<dim3((M + 31) / 32, (unsigned)((g.seg / 2 + 31) / 32)), 256, 0, st>>>(
-        A, lda, M, K, (int)g.seg, o, g.pitch);
-  PWH_LAUNCH_CHECK();
-}
-
-bool x3_gemm_presliced(System& s, bool conjA, int M, int N, int K, double2 alpha,
-                       const void* Aslices, const double2* B, int64_t ldb, double2 beta,
-                       double2* C, int64_t ldc, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return true;
-  if (K <= 0 || N > 65535 || x3_kseg(conjA, M, N, K) != K) return false;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-  });
-  x3_gemm_seg(s, conjA, M, N, K, alpha, nullptr, 0, B, ldb, beta, C, ldc, st,
-              (const __nv_bfloat16*)Aslices);
-  return true;
 }
 
 void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,

@@ -437,12 +437,7 @@ bool jacobi32_cluster(System& s, DenseWs& w, const double2* A, int64_t lda, int 
                       int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
                       cudaStream_t st) {
   (void)s;
-  // PWH_JACOBI_GLOBAL=1 in the environment selects the global-memory kernel
-  static const bool off = [] {
-    const char* e = std::getenv("PWH_JACOBI_GLOBAL");
-    return e && e[0] == '1';
-  }();
-  if (off || n < 64) return false;  // at least two pairs per CTA
+  if (n < 64) return false;  // at least two pairs per CTA
   const int np = n + (n & 1), P = np / 2;
   const int PP = (P + kDsmCluster - 1) / kDsmCluster;
   const size_t smem = jdsm_smem_bytes(n, P, PP);

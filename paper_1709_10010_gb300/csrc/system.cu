@@ -76,7 +76,7 @@ System::~System() {
   if (stream) cudaStreamSynchronize(stream);
   free_davidson_ws(dav);
   void* ptrs[] = {d_int_to_pub, d_kin, d_stick_off, d_stick_of, d_zpos, d_stick_col,
-                  d_stick_y, d_col_x, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
+                  d_stick_y, d_col_x, d_stick_at, d_xcol, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
                   ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp};
@@ -244,6 +244,13 @@ static void upload_basis(System& s) {
   s.d_stick_col = upload(s.stick_col, st);
   s.d_stick_y = upload(s.stick_y, st);
   s.d_col_x = upload(s.col_x, st);
+  std::vector<int32_t> stick_at((size_t)s.ncols * s.n2, -1);
+  for (int st_i = 0; st_i < s.nsticks; ++st_i)
+    stick_at[(size_t)s.stick_col[st_i] * s.n2 + s.stick_y[st_i]] = st_i;
+  std::vector<int16_t> xcol(s.n1, -1);
+  for (int c = 0; c < s.ncols; ++c) xcol[s.col_x[c]] = (int16_t)c;
+  s.d_stick_at = upload(stick_at, st);
+  s.d_xcol = upload(xcol, st);
   std::vector<int32_t> shell_int(s.npw);
   for (int64_t i = 0; i < s.npw; ++i) shell_int[i] = s.shell_pub[s.int_to_pub[i]];
   s.d_shell = upload(shell_int, st);
