@@ -213,6 +213,22 @@ typedef struct {
 pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                               int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
 
+/* Per-iteration record of the last pwh_davidson_solve on this system (a
+ * diagnostic; the solver keeps it on the host, no device work). */
+typedef struct {
+  int32_t iter;        /* Rayleigh-Ritz step, from 1 */
+  int32_t fp64;        /* 1 if the step ran in the FP64 phase */
+  int32_t m;           /* subspace size of the step */
+  int32_t n_above;     /* bands whose residual is above the phase's target */
+  double max_resid;    /* max ||r_n||_2 after the step */
+  double t_s;          /* seconds since the solve started (host clock) */
+} pwh_davidson_trace_entry;
+
+/* Copies up to cap entries of that record to out (host) and stores the number
+ * of iterations recorded in *count (which may exceed cap). */
+pwh_status pwh_get_davidson_trace(const pwh_system* sys, int32_t cap,
+                                  pwh_davidson_trace_entry* out, int32_t* count);
+
 /* pwh_davidson_solve with the bands in HOST memory: psi_host holds nb
  * contiguous columns of length npw (ld = npw, public order, complex128),
  * starting bands in, eigenvectors out.  The library copies them to a device

@@ -51,6 +51,11 @@ class DavidsonStats(ctypes.Structure):
 PRECOND = {"tpa": 0, "mlp": 1, "none": 2}
 
 
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("iter", _c_i32), ("fp64", _c_i32), ("m", _c_i32), ("n_above", _c_i32),
+                ("max_resid", _c_d), ("t_s", _c_d)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", _c_i64), ("total_ms", _c_d),
                 ("flops", _c_d), ("bytes", _c_d)]
@@ -95,6 +100,7 @@ SIGNATURES = {
                                     ctypes.POINTER(DavidsonStats)]),
     "pwh_davidson_solve_host": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_p,
                                          ctypes.POINTER(DavidsonStats)]),
+    "pwh_get_davidson_trace": (_c_i32, [_c_p, _c_i32, _c_p, ctypes.POINTER(_c_i32)]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_subspace_gemm": (_c_i32, [_c_p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_p, _c_p, _c_i64,
                                    _c_p, _c_i64, _c_p, _c_p, _c_i64]),
@@ -419,6 +425,15 @@ class System:
         if check and status not in (0,):
             _check(status)
         return eig, st.as_dict(), status
+
+    def davidson_trace(self):
+        """Per-iteration record of the last solve: a list of dicts (iter, fp64,
+        m, n_above, max_resid, t_s)."""
+        n = _c_i32()
+        _check(lib().pwh_get_davidson_trace(self._h, 0, None, ctypes.byref(n)))
+        arr = (TraceEntry * max(1, n.value))()
+        _check(lib().pwh_get_davidson_trace(self._h, n.value, arr, ctypes.byref(n)))
+        return [{k: getattr(arr[i], k) for k, _ in TraceEntry._fields_} for i in range(n.value)]
 
     def davidson_host(self, psi: np.ndarray, tol=1e-8, max_iter=200, mult=3, precond="tpa",
                       mixed=False, switch_tol=1e-5, jd_inner=0, check=True):

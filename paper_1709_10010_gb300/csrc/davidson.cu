@@ -36,6 +36,7 @@ struct DavWs {
   DevBuf<char> mlp;    // learned-preconditioner factors (k x nshell)
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
   DenseWs dense;
+  std::vector<pwh_davidson_trace_entry> trace;  // per Rayleigh-Ritz step of the last solve
   double* h_rn = nullptr;  // pinned host mirrors
   int* h_idx = nullptr;
   ~DavWs() {
@@ -386,8 +387,14 @@ static Layout carve(System& s, DavWs& w, int nb, int mmax) {
   return L;
 }
 
+// Blocks of at least this many columns take the Newton-Schulz second pass.
+constexpr int kNsMinCols = 128;
+
 // Orthonormalise T (npw x k, ld npw, in place) by two Cholesky-QR passes; the
-// first also drops columns whose norm fell below drop_rel * t0.  Returns the
+// first also drops columns whose norm fell below drop_rel * t0.  For blocks
+// of kNsMinCols columns or more the second pass is the symmetric (Loewdin)
+// orthonormalisation T S^{-1/2} by Newton-Schulz when S is close enough to
+// the identity (same span, orthonormal to the same precision).  Returns the
 // number of surviving columns (now the first ones of T).
 static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
                   const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
@@ -405,6 +412,22 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   // T Tr stays a combination of T's columns in the GEMM's precision
   cholqr_factor(s, w.dense, L.S, k, t0, drop_rel, L.Tr, L.kk, st, true);
   sgemm(s, p1, false, (int)npw, k, k, one, T, npw, L.Tr, k, zero, L.Tw, npw, st);
+  if (k >= kNsMinCols) {
+    // the kept columns (the first kk of Tw) are orthonormal to the first
+    // pass's rounding: the second pass as T = Tw S^{-1/2} (k x k GEMMs on the
+    // whole GPU instead of a factorisation on one SM) when S is that close
+    // to the identity
+    PWH_CUDA(cudaMemcpyAsync(w.h_idx + 4096, L.kk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PWH_CUDA(cudaStreamSynchronize(st));
+    const int kk = w.h_idx[4096];
+    if (kk > 0) {
+      sgemm(s, prec, true, kk, kk, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, kk, st);
+      if (ns_inv_sqrt(s, w.dense, L.S, kk, kk, prec == PWH_FP64, L.Tr, st)) {
+        sgemm(s, prec, false, (int)npw, kk, kk, one, L.Tw, npw, L.Tr, kk, zero, T, npw, st);
+        return kk;
+      }
+    }
+  }
   sgemm(s, prec, true, k, k, (int)npw, one, L.Tw, npw, L.Tw, npw, zero, L.S, k, st);
   cholqr_factor(s, w.dense, L.S, k, nullptr, 0.0, L.Tr, L.kk, st, prec != PWH_FP64);
   sgemm(s, prec, false, (int)npw, k, k, one, L.Tw, npw, L.Tr, k, zero, T, npw, st);
@@ -473,6 +496,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   S.switch_iter = -1;
   const double t_start = now_s();
   double t_phase = t_start;
+  w.trace.clear();
   int phase_prec = o.mixed ? (s.precision == PWH_FP64 ? PWH_MIXED : s.precision) : PWH_FP64;
 
   auto applyH = [&](const double2* in, double2* out, int k) {
@@ -558,6 +582,12 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     for (int b = 0; b < nb; ++b) {
       if (!std::isfinite(w.h_rn[b])) finite = false;
       maxr = std::max(maxr, w.h_rn[b]);
+    }
+    {
+      const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
+      int above = 0;
+      for (int b = 0; b < nb; ++b) above += w.h_rn[b] > thr;
+      w.trace.push_back({it, phase_prec == PWH_FP64 ? 1 : 0, m, above, maxr, now_s() - t_start});
     }
     if (!finite) {
       result = PWH_ERR_NONFINITE;
@@ -709,4 +739,16 @@ extern "C" pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidso
     PWH_CUDA(cudaStreamSynchronize(s.stream));
   });
   return g != PWH_OK ? g : st;
+}
+
+extern "C" pwh_status pwh_get_davidson_trace(const pwh_system* sys, int32_t cap,
+                                             pwh_davidson_trace_entry* out, int32_t* count) {
+  return guarded([&] {
+    PWH_CHECK_ARG(sys && count, "null argument");
+    PWH_CHECK_ARG(cap >= 0 && (cap == 0 || out), "cap < 0 or null output with cap > 0");
+    const System& s = sys->s;
+    const int n = s.dav ? (int)s.dav->trace.size() : 0;
+    *count = n;
+    for (int i = 0; i < std::min(n, (int)cap); ++i) out[i] = s.dav->trace[i];
+  });
 }

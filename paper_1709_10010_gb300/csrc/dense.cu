@@ -504,6 +504,297 @@ __global__ void k_ns_rhs(const double2* __restrict__ G, int n, double2* __restri
   }
 }
 
+// ---- FP32 Jacobi over the whole GPU in tournament-position order --------
+// For subspaces too large for one cluster's shared memory.  The matrix is
+// stored by tournament position instead of by index: pair k of every round
+// is positions (2k, 2k+1), so a round reads each 2 x 2 block (rows of pair k,
+// columns of pair l) as two contiguous 16-byte runs.  The circle method moves
+// the players between rounds along one cycle (position 0 stays; 2 -> 4 ->
+// ... -> np-2 -> np-1 -> np-3 -> ... -> 1 -> 2), and each round writes every
+// rotated element straight to its position of the next round, in the other
+// buffer, so the move costs no extra pass.  After np - 1 rounds every player
+// is back where it started: at a sweep boundary position = index.  Blocks
+// are taken in tiles of kPjTile x kPjTile pairs; only tiles on or above the
+// diagonal are computed and their mirror is written (conjugated) through a
+// shared-memory transpose, so A stays exactly Hermitian and every store is a
+// contiguous run.  The rotations go to a log in index form, (s, c, p | q <<
+// 16) per pair and round, from which k_jacobi_qlog_rows forms Q afterwards.
+constexpr int kPjTile = 16;
+constexpr int kPjThreads = kPjTile * kPjTile;
+constexpr int kQlogRowsL = 8;
+
+// next position of the player at x (np even)
+__device__ __forceinline__ int pj_next(int x, int np) {
+  if (x == 0 || np == 2) return x;
+  if (x == 1) return 2;
+  if ((x & 1) == 0) return x == np - 2 ? np - 1 : x + 2;
+  return x - 2;
+}
+// index standing at position x in round r (0 <= r < np - 1) of a sweep
+__device__ __forceinline__ int pj_index(int x, int r, int np) {
+  if (x == 0) return 0;
+  const int P = np / 2, L = np - 1;
+  const int c = (x & 1) ? P - 1 + (np - 1 - x) / 2 : x / 2 - 1;  // place on the cycle
+  int c0 = c - r;
+  if (c0 < 0) c0 += L;
+  return c0 <= P - 2 ? 2 * c0 + 2 : np - 1 - 2 * (c0 - (P - 1));
+}
+
+struct PjArgs {
+  float2* A[2];       // np x np, column-major, by position; A[0] holds the start
+  float4* log;        // round t, pair k at [t P + k]: (s.x, s.y, c, p | q << 16)
+  int64_t log_rounds;
+  double* diag;       // out: final diagonal, by index
+  int* info;          // out: [0] buffer of the final matrix, [1] sweeps, [2] rounds logged
+  unsigned* red;      // 2 words per sweep (max off-diagonal, max diagonal; float bits), zeroed
+  int n, np, P, T, max_sweeps;
+  float tol;
+  GridBar gb;
+};
+
+__global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
+  extern __shared__ __align__(16) unsigned char pjs[];
+  constexpr int E = 2 * kPjTile;            // elements per tile side
+  float4* rot = (float4*)pjs;               // P rotations (s.x, s.y, c, -)
+  float2* mir = (float2*)(rot + a.P);       // E x (E + 1) mirror tile
+  __shared__ float s_red[2][kPjThreads / 32];
+  const int np = a.np, P = a.P, T = a.T, n = a.n;
+  const int ntiles = T * (T + 1) / 2;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  int cur = 0, sweep = 0, rounds = 0;
+  bool done = false;
+  while (sweep < a.max_sweeps && !done) {
+    for (int r = 0; r < np - 1; ++r) {
+      const float2* A = cur ? a.A[1] : a.A[0];
+      float2* An = cur ? a.A[0] : a.A[1];
+      for (int k = threadIdx.x; k < P; k += blockDim.x) {
+        const size_t d = (size_t)(2 * k) * np + 2 * k;
+        float c;
+        float2 sv;
+        jacobi_rotation<float>(A[d + np], A[d].x, A[d + np + 1].x, c, sv);
+        rot[k] = make_float4(sv.x, sv.y, c, 0.f);
+        if (blockIdx.x == 0 && rounds < a.log_rounds) {
+          const int p = pj_index(2 * k, r, np), q = pj_index(2 * k + 1, r, np);
+          a.log[(size_t)rounds * P + k] = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 16)));
+        }
+      }
+      __syncthreads();
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int I = 0, rem = tile;  // upper-triangle tile (I, J), I <= J, row by row
+        while (rem >= T - I) {
+          rem -= T - I;
+          ++I;
+        }
+        const int J = I + rem;
+        const int kl = threadIdx.x % kPjTile, ll = threadIdx.x / kPjTile;
+        const int k = I * kPjTile + kl, l = J * kPjTile + ll;
+        if (k < P && l < P && (I != J || kl <= ll)) {
+          const float4 rk = rot[k], rl = rot[l];
+          const float4 c0 = *(const float4*)(A + (size_t)(2 * l) * np + 2 * k);      // a00, a10
+          const float4 c1 = *(const float4*)(A + (size_t)(2 * l + 1) * np + 2 * k);  // a01, a11
+          float2 y00, y01, y10, y11;
+          jacobi_block<float>(make_float2(c0.x, c0.y), make_float2(c1.x, c1.y),
+                              make_float2(c0.z, c0.w), make_float2(c1.z, c1.w), rk.z,
+                              make_float2(rk.x, rk.y), rl.z, make_float2(rl.x, rl.y), y00, y01,
+                              y10, y11);
+          if (k == l) {
+            // the rotated diagonal block: real diagonal, zeroed pair element
+            y00.y = 0.f;
+            y11.y = 0.f;
+            y01 = make_float2(0.f, 0.f);
+            y10 = y01;
+          }
+          const int i0 = pj_next(2 * k, np), i1 = pj_next(2 * k + 1, np);
+          const int j0 = pj_next(2 * l, np), j1 = pj_next(2 * l + 1, np);
+          An[(size_t)j0 * np + i0] = y00;
+          An[(size_t)j0 * np + i1] = y10;
+          An[(size_t)j1 * np + i0] = y01;
+          An[(size_t)j1 * np + i1] = y11;
+          if (k != l) {
+            // mirror (row of the l side, column of the k side), conjugated
+            mir[(2 * kl) * (E + 1) + 2 * ll] = make_float2(y00.x, -y00.y);
+            mir[(2 * kl) * (E + 1) + 2 * ll + 1] = make_float2(y01.x, -y01.y);
+            mir[(2 * kl + 1) * (E + 1) + 2 * ll] = make_float2(y10.x, -y10.y);
+            mir[(2 * kl + 1) * (E + 1) + 2 * ll + 1] = make_float2(y11.x, -y11.y);
+          }
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+          const int rl = e % E, cl = e / E;  // mirror row (l side) fastest
+          const int kk = I * kPjTile + cl / 2, lk = J * kPjTile + rl / 2;
+          if (kk < P && lk < P && (I != J || cl / 2 < rl / 2)) {
+            const int row = pj_next(2 * J * kPjTile + rl, np), col = pj_next(2 * I * kPjTile + cl, np);
+            An[(size_t)col * np + row] = mir[cl * (E + 1) + rl];
+          }
+        }
+        __syncthreads();
+      }
+      ++rounds;
+      cur ^= 1;
+      if (!grid_sync(a.gb)) return;
+    }
+    // convergence of the current matrix (position = index again): grid-wide
+    // maxima of |A_ij| (i < j) and |A_ii|, every block takes the same decision
+    {
+      const float2* A = cur ? a.A[1] : a.A[0];
+      float off = 0.f, dm = 0.f;
+      for (int64_t t = gtid; t < (int64_t)n * n; t += nth) {
+        const int i = (int)(t % n), j = (int)(t / n);
+        const float2 v = A[(size_t)j * np + i];
+        if (i == j) dm = fmaxf(dm, fabsf(v.x));
+        else if (i < j) off = fmaxf(off, sqrtf(v.x * v.x + v.y * v.y));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        s_red[0][threadIdx.x >> 5] = off;
+        s_red[1][threadIdx.x >> 5] = dm;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < kPjThreads / 32; ++w) {
+          off = fmaxf(s_red[0][0], s_red[0][w]);
+          s_red[0][0] = off;
+          s_red[1][0] = fmaxf(s_red[1][0], s_red[1][w]);
+        }
+        atomicMax(a.red + 2 * sweep, __float_as_uint(s_red[0][0]));
+        atomicMax(a.red + 2 * sweep + 1, __float_as_uint(s_red[1][0]));
+      }
+      if (!grid_sync(a.gb)) return;
+      const float offg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep));
+      const float dmg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep + 1));
+      done = offg <= a.tol * fmaxf(dmg, 1e-30f);
+    }
+    ++sweep;
+  }
+  if (gtid == 0) {
+    a.info[0] = cur;
+    a.info[1] = sweep;
+    a.info[2] = (int)min((int64_t)rounds, a.log_rounds);
+  }
+  const float2* Af = cur ? a.A[1] : a.A[0];
+  for (int i = gtid; i < n; i += nth) a.diag[i] = (double)Af[(size_t)i * np + i].x;
+}
+
+// FP64 start (n x n, ld lda) -> FP32 np x np by position (= index), zero padded.
+__global__ void k_to_pos32(const double2* __restrict__ A, int64_t lda, int n, int np,
+                           float2* __restrict__ out) {
+  const int64_t tot = (int64_t)np * np;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % np), j = (int)(t / np);
+    const double2 z = (i < n && j < n) ? A[(size_t)j * lda + i] : make_double2(0.0, 0.0);
+    out[t] = make_float2((float)z.x, (float)z.y);
+  }
+}
+
+// Q = J_0 J_1 ... J_{R-1} from the log of k_jacobi_pos (R = info[2]): the rows
+// of Q evolve independently, `rows` rows a block in shared memory (starting
+// as rows of the identity), every round applied to them in order.
+__global__ void __launch_bounds__(1024) k_jacobi_qlog_rows(const float4* __restrict__ log,
+                                                           const int* __restrict__ info, int n,
+                                                           int P, int rows, double2* __restrict__ Q,
+                                                           int64_t ldq) {
+  extern __shared__ __align__(16) unsigned char qrs[];
+  float2* qs = (float2*)qrs;  // [rows][n]
+  const int i0 = blockIdx.x * rows;
+  const int nr = min(rows, n - i0);
+  for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
+    const int r = t / n, c = t - r * n;
+    qs[t] = make_float2((r < nr && i0 + r == c) ? 1.f : 0.f, 0.f);
+  }
+  const int R = info[2];
+  __syncthreads();
+  for (int rd = 0; rd < R; ++rd) {
+    const float4* lr = log + (size_t)rd * P;
+    for (int it = threadIdx.x; it < nr * P; it += blockDim.x) {
+      const int k = it % P, r = it / P;
+      const float4 cur = __ldg(lr + k);
+      const int pq = __float_as_int(cur.w);
+      const int p = pq & 0xffff, q = pq >> 16;
+      if (p < n && q < n) {
+        const float c = cur.z;
+        const float2 sv = make_float2(cur.x, cur.y);
+        float2* row = qs + (size_t)r * n;
+        const float2 q0 = row[p], q1 = row[q];
+        row[p] = add<float>(scl<float>(q0, c), mul<float>(q1, make_float2(-sv.x, sv.y)));
+        row[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
+    const int c = t / nr, rr = t - c * nr;
+    const float2 v = qs[(size_t)rr * n + c];
+    Q[(size_t)c * ldq + i0 + rr] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+static size_t pj_log_bytes(int n, int max_sweeps) {
+  const int np = n + (n & 1);
+  return (size_t)max_sweeps * (np - 1) * (np / 2) * sizeof(float4) + 256;
+}
+static size_t pj_buf_bytes(int n) {
+  const int np = n + (n & 1);
+  return 2 * (size_t)np * np * sizeof(float2) + 1024;
+}
+
+// FP32 stage for large n (contract of jacobi32_cluster; info = [buffer,
+// sweeps, rounds]).  Returns false, launching nothing, outside its range.
+static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
+                         int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
+                         cudaStream_t st) {
+  if (n <= 512 || n > 4096 || max_sweeps > 64) return false;
+  const int np = n + (n & 1), P = np / 2, T = (P + kPjTile - 1) / kPjTile;
+  ensure(w.pj, pj_buf_bytes(n));
+  ensure(w.jlog, pj_log_bytes(n, max_sweeps));
+  float2* A0 = (float2*)w.pj.p;
+  float2* A1 = A0 + (size_t)np * np;
+  unsigned* red = (unsigned*)(A1 + (size_t)np * np);
+  PWH_CUDA(cudaMemsetAsync(red, 0, 2 * max_sweeps * sizeof(unsigned), st));
+  unsigned* ctl = (unsigned*)w.ctl;
+  PWH_CUDA(cudaMemsetAsync(ctl, 0, 3 * sizeof(unsigned), st));  // barrier words
+  k_to_pos32<<<(int)std::min<int64_t>(2048, ((int64_t)np * np + 255) / 256), 256, 0, st>>>(A, lda, n,
+                                                                                          np, A0);
+  PWH_LAUNCH_CHECK();
+  PjArgs a;
+  a.A[0] = A0;
+  a.A[1] = A1;
+  a.log = (float4*)w.jlog.p;
+  a.log_rounds = (int64_t)max_sweeps * (np - 1);
+  a.diag = diag;
+  a.info = info;
+  a.red = red;
+  a.n = n; a.np = np; a.P = P; a.T = T; a.max_sweeps = max_sweeps;
+  a.tol = (float)tol;
+  a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
+  a.gb.err = device_error_word(s);
+  const size_t smem = (size_t)P * sizeof(float4) + (size_t)(2 * kPjTile) * (2 * kPjTile + 1) * sizeof(float2);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_jacobi_pos, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    cudaFuncSetAttribute(k_jacobi_qlog_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  int dev = 0, nsm = 0, per_sm = 0;
+  PWH_CUDA(cudaGetDevice(&dev));
+  PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_pos, kPjThreads, smem));
+  if (per_sm < 1) return false;
+  const int ntiles = T * (T + 1) / 2;
+  const int blocks = std::max(1, std::min(ntiles, nsm * std::min(per_sm, 2)));
+  void* args[] = {&a};
+  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_pos, blocks, kPjThreads, args, smem, st));
+  note_launch();
+  // Q rows per block: kQlogRowsL, fewer where n rows would not fit in 220 KB
+  const int qrows = (int)std::max<int64_t>(1, std::min<int64_t>(kQlogRowsL, (220 << 10) / ((int64_t)n * 8)));
+  const size_t qsm = (size_t)qrows * n * sizeof(float2);
+  k_jacobi_qlog_rows<<<(n + qrows - 1) / qrows, 1024, qsm, st>>>(a.log, info, n, P, qrows, Q, ldq);
+  PWH_LAUNCH_CHECK();
+  return true;
+}
+
 template <typename T>
 static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0, cx<T>* Q1, int n,
                           double tol, int max_sweeps, int* out_buf, cudaStream_t st) {
@@ -632,7 +923,8 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
     // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
     // convergence) usually finishes.  The whole matrix in one cluster's shared
     // memory when it fits, else through global memory.
-    if (!jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
+    if (!jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st) &&
+        !jacobi32_pos(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
       k_c64_to_c32<<<gq, 256, 0, st>>>(start, ld_start, n, a0);
       PWH_LAUNCH_CHECK();
       k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity
@@ -701,7 +993,12 @@ void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   const size_t nn = (size_t)nmax * nmax;
   ensure(w.jac, jacobi_ws_bytes(nn, nmax));
   ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
+  ensure(w.ns, (size_t)4 * kmax * kmax * sizeof(double2) + 64);
   if (nmax >= 64 && nmax <= 512) ensure(w.jlog, jacobi32_log_bytes(nmax, 30));
+  if (nmax > 512 && nmax <= 4096) {
+    ensure(w.jlog, pj_log_bytes(nmax, 30));
+    ensure(w.pj, pj_buf_bytes(nmax));
+  }
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
 }
 
@@ -731,6 +1028,79 @@ static void cholqr_launch(DenseWs& w, const double2* S, int k, const double* t0,
     k_cholqr<T, false><<<1, 1024, 0, st>>>(S, k, t0, drop_rel, piv_tol, (cx<T>*)w.chol.p, Tr, kk);
   }
   PWH_LAUNCH_CHECK();
+}
+
+// ||S - I||_F^2 of the leading k x k block of S (ld lds), one block.
+__global__ void k_dev_identity_f2(const double2* __restrict__ S, int64_t lds, int k,
+                                  double* __restrict__ out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < (int64_t)k * k; t += blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double2 v = S[(size_t)j * lds + i];
+    const double re = v.x - (i == j ? 1.0 : 0.0);
+    acc += re * re + v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    *out = tot;
+  }
+}
+// dst (k x k, ld k) = leading k x k block of src (ld lds); identity when src is null
+__global__ void k_copy_square(const double2* __restrict__ src, int64_t lds, int k,
+                              double2* __restrict__ dst) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)k * k;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    dst[t] = src ? src[(size_t)j * lds + i] : make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+bool ns_inv_sqrt(System& s, DenseWs& w, const double2* S, int64_t lds, int k, bool fp64,
+                 double2* Z, cudaStream_t st) {
+  if (k < 1) return false;
+  ensure(w.ns, (size_t)4 * k * k * sizeof(double2) + 64);
+  if (!w.h_word) PWH_CUDA(cudaMallocHost((void**)&w.h_word, 64));
+  double2* Y = (double2*)w.ns.p;
+  double2* Zc = Y + (size_t)k * k;
+  double2* M = Zc + (size_t)k * k;
+  double2* Tm = M + (size_t)k * k;
+  double* dev = (double*)(Tm + (size_t)k * k);
+  k_dev_identity_f2<<<1, 1024, 0, st>>>(S, lds, k, dev);
+  PWH_LAUNCH_CHECK();
+  PWH_CUDA(cudaMemcpyAsync(w.h_word, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PWH_CUDA(cudaStreamSynchronize(st));
+  const double e0 = std::sqrt(w.h_word[0]);
+  // coupled iteration: ||Z_j Y_j - I|| ~ (3/4) ||Z_{j-1} Y_{j-1} - I||^2
+  if (!(e0 <= 1e-2)) return false;
+  const int its = e0 <= 1e-4 ? 2 : 3;
+  const int gq = (int)std::min<int64_t>(1024, ((int64_t)k * k + 255) / 256);
+  k_copy_square<<<gq, 256, 0, st>>>(S, lds, k, Y);
+  PWH_LAUNCH_CHECK();
+  k_copy_square<<<gq, 256, 0, st>>>(nullptr, 0, k, Zc);
+  PWH_LAUNCH_CHECK();
+  const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
+  auto gemm = [&](const double2* A, const double2* B, double2* C) {
+    if (fp64)
+      cgemm<double>(s, false, k, k, k, one, A, k, B, k, zero, C, k, st);
+    else
+      cgemm_f32(s, false, k, k, k, one, A, k, B, k, zero, C, k, st);
+  };
+  for (int it = 0; it < its; ++it) {
+    gemm(Zc, Y, Tm);                       // Z Y
+    k_ns_rhs<<<gq, 256, 0, st>>>(Tm, k, M);  // M = (3I - Z Y) / 2
+    PWH_LAUNCH_CHECK();
+    gemm(Y, M, Tm);                        // Y <- Y M
+    std::swap(Y, Tm);
+    gemm(M, Zc, Tm);                       // Z <- M Z
+    std::swap(Zc, Tm);
+  }
+  PWH_CUDA(cudaMemcpyAsync(Z, Zc, (size_t)k * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  return true;
 }
 
 void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,

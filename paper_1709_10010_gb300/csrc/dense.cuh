@@ -6,12 +6,18 @@ namespace pwh {
 
 struct DenseWs {
   DevBuf<char> jac, chol;
-  DevBuf<char> jlog;    // rotation log of the cluster Jacobi
+  DevBuf<char> jlog;    // rotation log of the cluster and position-order Jacobi
+  DevBuf<char> pj;      // position-order Jacobi: two FP32 matrices, reduction words
+  DevBuf<char> ns;      // Newton-Schulz inverse square root: four k x k matrices
+  double* h_word = nullptr;  // pinned host word for small device results
   void* ctl = nullptr;  // barrier words and flags of the Jacobi launch
   ~DenseWs() {
     if (jac.p) cudaFree(jac.p);
     if (chol.p) cudaFree(chol.p);
     if (jlog.p) cudaFree(jlog.p);
+    if (pj.p) cudaFree(pj.p);
+    if (ns.p) cudaFree(ns.p);
+    if (h_word) cudaFreeHost(h_word);
     if (ctl) cudaFree(ctl);
   }
 };
@@ -63,5 +69,14 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st);
 // FP32 arithmetic (for a Gram matrix that is itself FP32-accurate), else FP64.
 void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double* t0,
                    double drop_rel, double2* Tr, int* kk, cudaStream_t st, bool fp32 = false);
+
+// Z = S^{-1/2} (k x k, ld k) of a Hermitian S (leading k x k block, ld lds)
+// close to the identity, by the coupled Newton-Schulz iteration Y_0 = S,
+// Z_0 = I, M = (3I - Z Y)/2, Y <- Y M, Z <- M Z, in FP64 (fp64) or FP32
+// arithmetic.  Returns false, leaving Z untouched, unless ||S - I||_F <= 1e-2
+// (then two or three steps reach the arithmetic's rounding).  Synchronises
+// the stream once (to read ||S - I||_F).
+bool ns_inv_sqrt(System& s, DenseWs& w, const double2* S, int64_t lds, int k, bool fp64,
+                 double2* Z, cudaStream_t st);
 
 }  // namespace pwh

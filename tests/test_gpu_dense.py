@@ -1,7 +1,8 @@
 """Subspace diagonalisation (device Jacobi, FP32 sweeps + FP64 polish) against
 LAPACK (numpy.linalg.eigh): random, structured, degenerate and diagonal
-matrices, odd and even sizes, on both FP32 stages (the 16-CTA cluster kernel
-up to n of about 440, the global-memory kernel beyond).  Bar: eigenvalues
+matrices, odd and even sizes, on every FP32 stage (the 16-CTA cluster kernel
+for 64 <= n <= 512, the position-order kernel over the whole GPU beyond, the
+small cluster kernel below 64).  Bar: eigenvalues
 within 1e-12 of max |lambda|, eigenvectors orthonormal and with residual
 <= 1e-11 max |lambda|.  The FP32 result (precision="mixed"): eigenvalues within
 2e-6 max |lambda|, orthonormality 2e-6, residual 2e-5 max |lambda| (about 30
@@ -33,7 +34,10 @@ def degenerate(n, seed):
 
 CASES = [("random", 12), ("random", 7), ("random", 96), ("random", 257), ("degenerate", 12),
          ("degenerate", 40), ("degenerate", 131), ("diagonal", 33), ("kinetic", 60),
-         ("random", 384), ("degenerate", 384), ("kinetic", 383), ("random", 440), ("random", 450)]
+         ("random", 384), ("degenerate", 384), ("kinetic", 383), ("random", 440), ("random", 450),
+         # the position-order kernel over the whole GPU (n > 512): odd (a dummy
+         # player), partial tiles, degenerate and Davidson-like spectra
+         ("random", 513), ("degenerate", 640), ("kinetic", 1031), ("random", 1536)]
 
 # bars: (eigenvalue, orthonormality, residual), relative to max |lambda| where scaled
 BARS = {"fp64": (1e-12, 1e-12, 1e-11), "mixed": (2e-6, 2e-6, 2e-5)}
@@ -74,7 +78,8 @@ def test_subspace_eigh_vs_lapack(env, kind, n, precision):
 
 @pytest.mark.parametrize("kind,m0,n", [("random", 30, 40), ("degenerate", 24, 36),
                                        ("kinetic", 64, 96), ("random", 7, 13),
-                                       ("kinetic", 256, 384)])
+                                       ("kinetic", 256, 384), ("kinetic", 512, 768),
+                                       ("random", 600, 901)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_subspace_eigh_warm_start(env, kind, m0, n, precision):
     """Second call on a matrix whose leading m0 x m0 block was diagonalised by the
