@@ -228,6 +228,7 @@ struct System {
 
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
+  DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
   DevBuf<char> ws_oz;               // sliced operands and partials of the FP64-equivalent GEMM
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
@@ -298,13 +299,16 @@ template <typename F> pwh_status guarded(F&& f) {
 
 // internal launchers (defined in the .cu files)
 void build_fft_plans(System& s);
+// hpsi = (kinetic + local) psi [+ vnl, an FP32 nonlocal term in the same
+// layout, ld ldv, when given]
 template <typename T>
 void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
-                   int64_t ldh, cudaStream_t st);
+                   int64_t ldh, cudaStream_t st, const float2* vnl = nullptr, int64_t ldv = 0);
 void nonlocal_fp64(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                    int64_t ldh, cudaStream_t st);
-void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
-                    int64_t ldh, cudaStream_t st, int terms);
+// vnl (FP32, ld ldv) = sum_ij beta_i D_ij <beta_j|psi> on the BF16 tensor cores
+void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, float2* vnl,
+                    int64_t ldv, cudaStream_t st, int terms);
 int* device_error_word(System& s);
 void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                     int64_t ldh, int precision);

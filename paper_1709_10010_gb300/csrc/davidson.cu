@@ -18,6 +18,7 @@
 // Mixed mode runs the same loop with the reduced-precision H until
 // max ||r|| <= switch_tol, then restarts from the Ritz vectors with the FP64 H
 // (the FP64 phase recomputes every residual in FP64).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -52,6 +53,29 @@ struct DavWs {
 void free_davidson_ws(DavWs* w) { delete w; }
 
 // ----------------------------------------------------------------- kernels --
+// Starting vectors of the buffer bands: pseudo-random coefficients (two
+// splitmix64 draws per entry, Steele, Lea and Flood 2014, uniform in [-1, 1)
+// for the real and imaginary part) damped by 1/(1 + T_G), so that they start
+// mostly on low kinetic energy.  V: npw x nbuf, column-major, internal order.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void k_buffer_start(double2* __restrict__ V, int64_t npw, int nbuf,
+                               const double* __restrict__ kin, uint64_t seed) {
+  const int64_t tot = npw * nbuf;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = t % npw;
+    const uint64_t a = splitmix64(seed + 0x9e3779b97f4a7c15ull * (uint64_t)(2 * t + 1));
+    const uint64_t b = splitmix64(seed + 0x9e3779b97f4a7c15ull * (uint64_t)(2 * t + 2));
+    const double d = 1.0 / (1.0 + kin[g]);
+    V[t] = make_double2(((double)(a >> 11) * 0x1.0p-53 * 2.0 - 1.0) * d,
+                        ((double)(b >> 11) * 0x1.0p-53 * 2.0 - 1.0) * d);
+  }
+}
+
 // R = HX - X theta per band; rn[b] = ||r_b||, eref[b] = <x|T|x>/<x|x> (the
 // band's kinetic energy, the reference energy of the TPA preconditioner).
 __global__ void k_residual(const double2* __restrict__ X, const double2* __restrict__ HX,
@@ -463,9 +487,19 @@ static void check_err(System& s) {
 
 pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, int64_t ldpsi,
                           double* eig, pwh_davidson_stats* stats) {
-  const int nb = o.nb;
-  const int mmax = o.max_subspace_mult * nb;
   const int64_t npw = s.npw;
+  // Buffer bands: the solver iterates nbt + nbuf Ritz pairs and requires the
+  // tolerance only of the lowest nbt (the bands asked for); the others are
+  // converged to a looser threshold.  Without them, a requested band whose
+  // near-degenerate partner lies just outside the subspace converges slowly
+  // (the Jacobi-Davidson correction equation then has an eigenvalue close to
+  // zero on the complement of X); with them that partner is inside X.
+  const int nbt = o.nb;
+  const int64_t nbuf_cap[] = {(int64_t)std::max(2, (nbt + 15) / 16), 64, 1024 - (int64_t)nbt,
+                              npw - nbt, 4096 / o.max_subspace_mult - (int64_t)nbt};
+  const int nbuf = (int)std::max<int64_t>(0, *std::min_element(nbuf_cap, nbuf_cap + 5));
+  const int nb = nbt + nbuf;
+  const int mmax = o.max_subspace_mult * nb;
   if (!s.dav) s.dav = new DavWs();
   DavWs& w = *s.dav;
   Layout L = carve(s, w, nb, mmax);
@@ -482,7 +516,9 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     oz_reserve(s, true, s.nproj, nb, (int)npw);
     oz_reserve(s, false, (int)npw, nb, s.nproj);
   }
-  // and of the reduced phase (FP32-equivalent products of the same shapes)
+  // and of the reduced phase (FP32-equivalent products of the same shapes,
+  // the FP32 nonlocal term of the reduced-precision H)
+  if (o.mixed && s.nproj > 0) ensure(s.ws_vnl, (size_t)npw * nb * sizeof(float2));
   if (o.mixed) {
     x3_reserve(s, true, mmax, mmax, (int)npw);
     x3_reserve(s, false, (int)npw, nb, mmax);
@@ -505,9 +541,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     if (phase_prec == PWH_FP64) S.n_apply_fp64 += k;
   };
 
-  // starting block: public -> internal order, orthonormalise, apply H
-  k_perm_in<<<grid1d(npw * nb), 256, 0, st>>>(psi, ldpsi, npw, nb, s.d_int_to_pub, L.V, npw);
+  // starting block: public -> internal order (and the buffer bands),
+  // orthonormalise, apply H
+  k_perm_in<<<grid1d(npw * nbt), 256, 0, st>>>(psi, ldpsi, npw, nbt, s.d_int_to_pub, L.V, npw);
   PWH_LAUNCH_CHECK();
+  if (nbuf > 0) {
+    k_buffer_start<<<grid1d(npw * nbuf), 256, 0, st>>>(L.V + (size_t)nbt * npw, npw, nbuf, s.d_kin,
+                                                       0x9e3779b97f4a7c15ull ^ (uint64_t)nbt);
+    PWH_LAUNCH_CHECK();
+  }
   int k0 = cholqr2(s, w, L, L.V, nb, nullptr, 0.0, st);
   if (k0 < nb) throw Error{PWH_ERR_ARG, "starting bands are linearly dependent"};
   applyH(L.V, L.HV, nb);
@@ -515,6 +557,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   int hs_valid = 0;  // leading columns of Hs that match the current V, HV
   pwh_status result = PWH_ERR_NOT_CONVERGED;
   double maxr = 0.0;
+  double maxr_target = 0.0;  // over the requested bands, at the last iteration
   auto restart_from_ritz = [&](bool recompute_hx) {
     k_copy_cols<<<grid1d(npw * nb), 256, 0, st>>>(L.X, npw, L.V, npw, npw, nb);
     PWH_LAUNCH_CHECK();
@@ -577,17 +620,28 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     }
     s.timer.resolve();
     S.iters = it;
+    // maxr: over every band (reduced-phase decisions); maxr_t: over the
+    // requested ones (termination, reported residual)
     maxr = 0.0;
+    double maxr_t = 0.0;
     bool finite = true;
     for (int b = 0; b < nb; ++b) {
       if (!std::isfinite(w.h_rn[b])) finite = false;
       maxr = std::max(maxr, w.h_rn[b]);
+      if (b < nbt) maxr_t = std::max(maxr_t, w.h_rn[b]);
     }
+    maxr_target = maxr_t;
+    // this phase's target of band b: the requested bands to tol (FP64 phase)
+    // or switch_tol (reduced phase); buffer bands to switch_tol in the reduced
+    // phase and to 1e3 tol (at most switch_tol) in the FP64 phase
+    const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
+    const double thr_buf = phase_prec == PWH_FP64 ? std::max(o.tol, std::min(1e3 * o.tol, o.switch_tol))
+                                                  : o.switch_tol;
+    auto above = [&](int b) { return w.h_rn[b] > (b < nbt ? thr : thr_buf); };
     {
-      const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
-      int above = 0;
-      for (int b = 0; b < nb; ++b) above += w.h_rn[b] > thr;
-      w.trace.push_back({it, phase_prec == PWH_FP64 ? 1 : 0, m, above, maxr, now_s() - t_start});
+      int n_above = 0;
+      for (int b = 0; b < nb; ++b) n_above += above(b);
+      w.trace.push_back({it, phase_prec == PWH_FP64 ? 1 : 0, m, n_above, maxr_t, now_s() - t_start});
     }
     if (!finite) {
       result = PWH_ERR_NONFINITE;
@@ -603,16 +657,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       restart_from_ritz(true);
       continue;
     }
-    if (phase_prec == PWH_FP64 && maxr <= o.tol) {
+    if (phase_prec == PWH_FP64 && maxr_t <= o.tol) {
       result = PWH_OK;
       break;
     }
     if (it >= o.max_iter) break;
     // bands still above this phase's target get a new direction
-    const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
     int k = 0;
     for (int b = 0; b < nb; ++b)
-      if (w.h_rn[b] > thr) w.h_idx[k++] = b;
+      if (above(b)) w.h_idx[k++] = b;
     PWH_CUDA(cudaMemcpyAsync(L.idx, w.h_idx, k * sizeof(int), cudaMemcpyHostToDevice, st));
     // Jacobi-Davidson steps in the FP64 phase, and in the reduced-precision
     // phase once its residuals are within 100x of the hand-over target
@@ -667,9 +720,10 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     applyH(T, L.HV + (size_t)m * npw, kn);
     m += kn;
   }
-  // outputs: eigenvalues (host), eigenvectors (public order, caller's buffer)
-  PWH_CUDA(cudaMemcpyAsync(eig, L.theta, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-  k_perm_out<<<grid1d(npw * nb), 256, 0, st>>>(L.X, npw, npw, nb, s.d_int_to_pub, psi, ldpsi);
+  // outputs: the requested bands' eigenvalues (host) and eigenvectors
+  // (public order, caller's buffer)
+  PWH_CUDA(cudaMemcpyAsync(eig, L.theta, nbt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  k_perm_out<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, npw, nbt, s.d_int_to_pub, psi, ldpsi);
   PWH_LAUNCH_CHECK();
   PWH_CUDA(cudaStreamSynchronize(st));
   check_err(s);
@@ -681,7 +735,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   else
     S.t_fp64_s = t_end - t_phase;
   S.t_total_s = t_end - t_start;
-  S.max_resid = maxr;
+  S.max_resid = maxr_target;
   if (stats) *stats = S;
   return result;
 }

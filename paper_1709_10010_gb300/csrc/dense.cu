@@ -970,6 +970,17 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
   PWH_LAUNCH_CHECK();
   cgemm_f32_simt(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
+  // one FP64 step leaves ~(3/4) e^2 of the FP32 basis' deviation e from
+  // unitary (e grows like sqrt(n) FP32 roundings): a second step above n = 512
+  // (into the buffer of the FP32-stage vectors, Q0 or A0, free by now)
+  if (n > 512) {
+    cgemm<double>(s, true, n, n, n, one, Qo, n, Qo, n, zero, G, n, st);
+    k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
+    PWH_LAUNCH_CHECK();
+    double2* Qn = (Qo == Q0) ? A0 : Q0;
+    cgemm<double>(s, false, n, n, n, one, Qo, n, A1, n, zero, Qn, n, st);
+    Qo = Qn;
+  }
   cgemm<double>(s, true, n, n, n, one, Qo, n, Qo, n, zero, G, n, st);
   k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
   PWH_LAUNCH_CHECK();

@@ -242,7 +242,8 @@ __global__ void __launch_bounds__(256) k_zfwd(const cx<T>* __restrict__ W, int64
                                               const int16_t* __restrict__ perm_g,
                                               const double* __restrict__ kin,
                                               const double2* __restrict__ psi, int64_t ldp,
-                                              double2* __restrict__ hpsi, int64_t ldh, int spb) {
+                                              double2* __restrict__ hpsi, int64_t ldh, int spb,
+                                              const float2* __restrict__ vnl, int64_t ldv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n3 = pl3.n, ld = n3 + 1;
   cx<T>* buf = (cx<T>*)smem_raw;
@@ -265,12 +266,19 @@ __global__ void __launch_bounds__(256) k_zfwd(const cx<T>* __restrict__ W, int64
   const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
   const double2* pb = psi + (size_t)b * ldp;
   double2* hb = hpsi + (size_t)b * ldh;
+  const float2* vb = vnl ? vnl + (size_t)b * ldv : nullptr;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     int s = stick_of[i] - s0;
     cx<T> v = buf[s * ld + irev[zpos[i]]];
     double2 p = pb[i];
     double k = kin[i];
-    hb[i] = kin_plus<T>(k, p, v);
+    double2 h = kin_plus<T>(k, p, v);
+    if (vb) {
+      const float2 u = vb[i];
+      h.x += (double)u.x;
+      h.y += (double)u.y;
+    }
+    hb[i] = h;
   }
 }
 
@@ -285,7 +293,7 @@ static size_t plane_smem(const System& s, int rows) {
 
 template <typename T>
 void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
-                   cudaStream_t st) {
+                   cudaStream_t st, const float2* vnl, int64_t ldv) {
   if (nb <= 0) return;
   const int64_t wband = (int64_t)s.n3 * s.nsticks;
   // batch so that the stick buffer stays around 64 MB (L2-resident between passes)
@@ -323,8 +331,9 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   for (int b0 = 0; b0 < nb; b0 += batch) {
     int bb = std::min(batch, nb - b0);
     dim3 gz((s.nsticks + spb - 1) / spb, bb);
+    const float2* vb = vnl ? vnl + (size_t)b0 * ldv : nullptr;
     const PassArgs pa{psi + (size_t)b0 * ldp, ldp, hpsi + (size_t)b0 * ldh, ldh, W, wband, spb,
-                      zsmem, rows, psmem, bb, V, tw, st};
+                      zsmem, rows, psmem, bb, V, tw, st, vb, ldv};
     {
       TimedScope ts(s, dp ? KF_FFT_ZINV64 : KF_FFT_ZINV32, st, bb * fz, bb * (16.0 * s.npw + bw));
       if (!spec_pass<T>(SPEC_ZINV, s, pa)) {
@@ -344,11 +353,11 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
     }
     {
       TimedScope ts(s, dp ? KF_FFT_ZFWD64 : KF_FFT_ZFWD32, st, bb * fz,
-                    bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw));
+                    bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw + (vb ? 8.0 * s.npw : 0.0)));
       if (!spec_pass<T>(SPEC_ZFWD, s, pa)) {
         k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
                                            s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp,
-                                           ldp, hpsi + (size_t)b0 * ldh, ldh, spb);
+                                           ldp, hpsi + (size_t)b0 * ldh, ldh, spb, vb, ldv);
         PWH_LAUNCH_CHECK();
       }
     }
@@ -356,9 +365,9 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
 }
 
 template void local_kinetic<double>(System&, int, const double2*, int64_t, double2*, int64_t,
-                                    cudaStream_t);
+                                    cudaStream_t, const float2*, int64_t);
 template void local_kinetic<float>(System&, int, const double2*, int64_t, double2*, int64_t,
-                                   cudaStream_t);
+                                   cudaStream_t, const float2*, int64_t);
 
 // ------------------------------------------- allocation-free entry point ----
 // Scratch for pwh_apply_local_noalloc: the stick buffer of the FFT passes lives
@@ -420,7 +429,7 @@ static void local_kinetic_noalloc(System& s, int nb, const double2* psi, int64_t
     PWH_LAUNCH_CHECK();
     k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
                                        s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp, ldp,
-                                       hpsi + (size_t)b0 * ldh, ldh, spb);
+                                       hpsi + (size_t)b0 * ldh, ldh, spb, nullptr, 0);
     PWH_LAUNCH_CHECK();
   }
 }

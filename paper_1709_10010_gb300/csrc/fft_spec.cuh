@@ -23,6 +23,8 @@ struct PassArgs {
   const void* V;
   const void* tw;
   cudaStream_t st;
+  const float2* vnl;  // FP32 nonlocal term added by the z-forward pass (or null)
+  int64_t ldv;
 };
 
 enum SpecPass { SPEC_ZINV = 0, SPEC_PLANE = 1, SPEC_ZFWD = 2 };

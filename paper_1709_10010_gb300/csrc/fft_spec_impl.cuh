@@ -238,15 +238,16 @@ __global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, 
 // bound the shared memory.
 
 // Four-step pass 1 on registers: v[n1] = x[N2 n1 + n2] -> w^(n2 k1) DFT_N1(v)[k1]
-// (w = e^{+-2 pi i/N}), natural order out.
+// (w = e^{+-2 pi i/N}), natural order out.  tw4[k1 N2 + n2] = e^{2 pi i n2 k1/N}:
+// threads with consecutive n2 read consecutive entries (no bank conflicts).
 template <typename T, int N, bool INV>
-__device__ __forceinline__ void fs_pass1(cx<T>* v, int n2, const cx<T>* tw) {
-  constexpr int N1 = fft_factor(N);
+__device__ __forceinline__ void fs_pass1(cx<T>* v, int n2, const cx<T>* tw, const cx<T>* tw4) {
+  constexpr int N1 = fft_factor(N), N2 = N / N1;
   const T sg = INV ? (T)1 : (T)-1;
   dft_reg<T, N1, INV, N>(v, tw);
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) {
-    cx<T> w = tw[n2 * k1];
+    cx<T> w = tw4[k1 * N2 + n2];
     w.y *= sg;
     v[k1] = mul<T>(v[k1], w);
   }
@@ -255,16 +256,20 @@ __device__ __forceinline__ void fs_pass1(cx<T>* v, int n2, const cx<T>* tw) {
 // Four-step pass 2 in place on nf transforms of shared memory (transform f at
 // data + f ld): x[N2 k1 + n2] -> x[k1 + N1 k2], rounds of whole transforms,
 // each round loads, synchronises, then stores; `post(f, x, value)` maps an
-// output before it is stored.  Ends with __syncthreads().
-template <typename T, int N, int NT, bool INV, class Post>
+// output before it is stored.  FFAST: neighbouring threads take neighbouring
+// transforms (odd ld: conflict-free shared-memory access), else neighbouring
+// k1 (neighbouring x, for coalesced global reads in post).  Ends with
+// __syncthreads().
+template <typename T, int N, int NT, bool INV, bool FFAST, class Post>
 __device__ __forceinline__ void fs_pass2_inplace(cx<T>* data, int nf, int ld, const cx<T>* tw,
                                                  Post post) {
   constexpr int N1 = fft_factor(N), N2 = N / N1;
   constexpr int per = NT / N1;
-  const int fl = threadIdx.x / N1, k1 = threadIdx.x - fl * N1;
+  const int fl = FFAST ? (int)threadIdx.x % per : (int)threadIdx.x / N1;
+  const int k1 = FFAST ? (int)threadIdx.x / per : (int)threadIdx.x - fl * N1;
   for (int f0 = 0; f0 < nf; f0 += per) {
     const int f = f0 + fl;
-    const bool act = fl < per && f < nf;
+    const bool act = fl < per && k1 < N1 && f < nf;
     cx<T> w[N2];
     if (act) {
       const cx<T>* xf = data + f * ld + N2 * k1;
@@ -294,11 +299,13 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
   cx<T>* C = (cx<T>*)smem_raw;             // ncols x LD: columns along y
   cx<T>* R = C + (size_t)ncols * LD;       // rows x LD: rows along x
   cx<T>* tw = R + (size_t)rows * LD;       // e^{2 pi i t/N}
-  int16_t* xcol = (int16_t*)(tw + N);      // column of each x, -1 if none
+  cx<T>* tw4 = tw + N;                     // [k1][n2]: e^{2 pi i n2 k1/N}
+  int16_t* xcol = (int16_t*)(tw4 + N);     // column of each x, -1 if none
   const int z = blockIdx.x, b = blockIdx.y;
   cx<T>* plane = W + (size_t)b * wband + (size_t)z * nsticks;
   for (int t = threadIdx.x; t < N; t += NT) {
     tw[t] = tw_g[tw_off + t];
+    tw4[t] = tw_g[tw_off + (t % N2) * (t / N2)];
     xcol[t] = xcol_g[t];
   }
   __syncthreads();
@@ -314,13 +321,13 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
       const int st = sa[N2 * n1];
       v[n1] = st >= 0 ? plane[st] : zero;
     }
-    fs_pass1<T, N, true>(v, n2, tw);
+    fs_pass1<T, N, true>(v, n2, tw, tw4);
     cx<T>* cc = C + c * LD + n2;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) cc[N2 * k1] = v[k1];
   }
   __syncthreads();
-  fs_pass2_inplace<T, N, NT, true>(C, ncols, LD, tw, [](int, int, cx<T> v) { return v; });
+  fs_pass2_inplace<T, N, NT, true, true>(C, ncols, LD, tw, [](int, int, cx<T> v) { return v; });
 
   // ---- rows: x inverse, times V, x forward; keep the columns
   const T* Vz = V + (size_t)z * N * N;
@@ -334,14 +341,14 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
         const int c = xcol[N2 * n1 + n2];
         v[n1] = c >= 0 ? C[c * LD + y0 + r] : zero;
       }
-      fs_pass1<T, N, true>(v, n2, tw);
+      fs_pass1<T, N, true>(v, n2, tw, tw4);
       cx<T>* rr = R + r * LD + n2;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
     }
     __syncthreads();
     const T* Vy = Vz + (size_t)y0 * N;
-    fs_pass2_inplace<T, N, NT, true>(R, nr, LD, tw, [Vy](int r, int x, cx<T> v) {
+    fs_pass2_inplace<T, N, NT, true, false>(R, nr, LD, tw, [Vy](int r, int x, cx<T> v) {
       return scl<T>(v, Vy[(size_t)r * N + x]);
     });
     for (int t = threadIdx.x; t < nr * N2; t += NT) {
@@ -350,13 +357,13 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
       cx<T> v[N1];
 #pragma unroll
       for (int n1 = 0; n1 < N1; ++n1) v[n1] = rr[N2 * n1];
-      fs_pass1<T, N, false>(v, n2, tw);
+      fs_pass1<T, N, false>(v, n2, tw, tw4);
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nr * N1; t += NT) {
-      const int r = t / N1, k1 = t - r * N1;
+      const int r = t % nr, k1 = t / nr;  // neighbouring rows: conflict-free
       const cx<T>* rr = R + r * LD + N2 * k1;
       cx<T> w[N2];
 #pragma unroll
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
     cx<T> v[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) v[n1] = cc[N2 * n1];
-    fs_pass1<T, N, false>(v, n2, tw);
+    fs_pass1<T, N, false>(v, n2, tw, tw4);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) cc[N2 * k1] = v[k1];
   }
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
 
 // Shared memory of the plane pass for `rows` rows per chunk.
 template <typename T, int N> constexpr size_t ks_plane_smem(int ncols, int rows) {
-  return ((size_t)(ncols + rows) * (N + 1) + N) * sizeof(cx<T>) + N * sizeof(int16_t);
+  return ((size_t)(ncols + rows) * (N + 1) + 2 * N) * sizeof(cx<T>) + N * sizeof(int16_t);
 }
 
 template <typename T, int N>
@@ -414,7 +421,8 @@ __global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int6
                                                const int16_t* __restrict__ perm_g,
                                                const double* __restrict__ kin,
                                                const double2* __restrict__ psi, int64_t ldp,
-                                               double2* __restrict__ hpsi, int64_t ldh, int spb) {
+                                               double2* __restrict__ hpsi, int64_t ldh, int spb,
+                                               const float2* __restrict__ vnl, int64_t ldv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int ld = N + 1;
   cx<T>* buf = (cx<T>*)smem_raw;
@@ -437,11 +445,18 @@ __global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int6
   const int i0 = stick_off[s0], i1 = stick_off[s0 + ns];
   const double2* pb = psi + (size_t)b * ldp;
   double2* hb = hpsi + (size_t)b * ldh;
+  const float2* vb = vnl ? vnl + (size_t)b * ldv : nullptr;
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const cx<T> v = buf[(stick_of[i] - s0) * ld + zpos[i]];
     const double2 p = pb[i];
     const double k = kin[i];
-    hb[i] = kin_plus<T>(k, p, v);
+    double2 h = kin_plus<T>(k, p, v);
+    if (vb) {
+      const float2 u = vb[i];
+      h.x += (double)u.x;
+      h.y += (double)u.y;
+    }
+    hb[i] = h;
   }
 }
 
@@ -482,7 +497,8 @@ template <typename T, int N> void spec_launch(SpecPass pass, System& s, const Pa
     case SPEC_ZFWD:
       ks_zfwd<T, N><<<gz, 256, a.zsmem, a.st>>>(W, a.wband, s.d_stick_off, s.d_stick_of, s.d_zpos,
                                                  s.nsticks, s.plan[2].tw_off, s.plan[2].perm_off, tw,
-                                                 s.d_perm, s.d_kin, a.psi, a.ldp, a.hpsi, a.ldh, a.spb);
+                                                 s.d_perm, s.d_kin, a.psi, a.ldp, a.hpsi, a.ldh, a.spb,
+                                                 a.vnl, a.ldv);
       break;
   }
   PWH_LAUNCH_CHECK();

@@ -54,8 +54,8 @@ struct TcArgs {
   int terms;         // 1: hi*hi; 3: hi*hi + hi*lo + lo*hi
   int kb_per_split;  // logical K blocks per blockIdx.z
   float* part;       // mode 0: FP32 out[z][n][m]
-  double2* hpsi;     // mode 1: hpsi[b*ldh + m] += (C[m][2b], C[m][2b+1])
-  int64_t ldh;
+  float2* vnl;       // mode 1: vnl[b*ldv + m] = (C[m][2b], C[m][2b+1])
+  int64_t ldv;
   int nb;
   int* err;          // device error word
   // sliced operands: product t multiplies A segment oz_a[t] by B segment
@@ -294,16 +294,13 @@ __global__ void __launch_bounds__(128, 1)
             if (n < args.N) args.part[((size_t)blockIdx.z * args.N + n) * args.M + m] = v[j];
           }
         } else {
+          // the nonlocal term of band b at plane wave m, FP32 (the z-forward
+          // FFT pass adds it into H psi): plain stores, one 256-byte run per
+          // band and warp
 #pragma unroll
           for (int j = 0; j < 32; j += 2) {
-            int b = (n0 + c0 + j) >> 1;
-            if (b < args.nb) {
-              // FP32 add with integer format conversions (this pass carries
-              // FP32 accuracy; the FP64 pipe would bound the epilogue)
-              double2* h = args.hpsi + (size_t)b * args.ldh + m;
-              const float2 o = d2f_rn(*h);
-              *h = f2d(make_float2(o.x + v[j], o.y + v[j + 1]));
-            }
+            const int b = (n0 + c0 + j) >> 1;
+            if (b < args.nb) args.vnl[(size_t)b * args.ldv + m] = make_float2(v[j], v[j + 1]);
           }
         }
       }
@@ -496,7 +493,7 @@ static void launch_tc(System& s, int mode, const CUtensorMap& ma, const CUtensor
   const double kk = (double)a.terms * a.kb_seg * TC_BK;
   TimedScope ts(s, mode == 0 ? KF_TC_BECP : KF_TC_BACK, st, 2.0 * a.M * (double)a.N * kk,
                 2.0 * ((double)a.M + a.N) * kk + (mode == 0 ? 4.0 * gz * (double)a.M * a.N
-                                                            : 32.0 * a.M * (a.N / 2)));
+                                                            : 8.0 * a.M * (a.N / 2)));
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
     cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -512,7 +509,7 @@ static void launch_tc(System& s, int mode, const CUtensorMap& ma, const CUtensor
 
 int* device_error_word(System& s);  // davidson.cu / hpsi.cu
 
-void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
+void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, float2* vnl, int64_t ldv,
                     cudaStream_t st, int terms) {
   if (s.nproj == 0 || nb <= 0) return;
   const int P = s.nproj;
@@ -568,14 +565,14 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, double2*
   k_pack_becp<<<rb, 256, 0, st>>>(becp, P, nb, B2, g.pitch2, g.seg2);
   PWH_LAUNCH_CHECK();
 
-  // ---- back-projection GEMM, accumulated into hpsi
+  // ---- back-projection GEMM into the FP32 buffer vnl
   const int gm2 = (int)((s.npw + TC_BM - 1) / TC_BM), gn2 = (2 * nb + TC_BN - 1) / TC_BN;
   const int kbs2 = (int)(g.seg2 / TC_BK);
   CUtensorMap ma2 = make_map(s.d_beta_bf16_t, s.npw, 2 * g.seg2, g.pitch2, TC_BM);
   CUtensorMap mb2 = make_map(B2, 2 * nb, 2 * g.seg2, g.pitch2, TC_BN);
   TcArgs a2{};
   a2.M = (int)s.npw; a2.N = 2 * nb; a2.kb_seg = kbs2; a2.terms = terms;
-  a2.kb_per_split = terms * kbs2; a2.hpsi = hpsi; a2.ldh = ldh; a2.nb = nb;
+  a2.kb_per_split = terms * kbs2; a2.vnl = vnl; a2.ldv = ldv; a2.nb = nb;
   a2.err = device_error_word(s);
   launch_tc(s, 1, ma2, mb2, a2, gm2, gn2, 1, st);
 }

@@ -70,8 +70,14 @@ void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2*
     local_kinetic<double>(s, nb, psi, ldp, hpsi, ldh, s.stream);
     nonlocal_fp64(s, nb, psi, ldp, hpsi, ldh, s.stream);
   } else {
-    local_kinetic<float>(s, nb, psi, ldp, hpsi, ldh, s.stream);
-    nonlocal_mixed(s, nb, psi, ldp, hpsi, ldh, s.stream, precision == PWH_MIXED_FAST ? 1 : 3);
+    // the nonlocal term first, into an FP32 buffer that the last FFT pass adds
+    float2* vnl = nullptr;
+    if (s.nproj > 0) {
+      ensure(s.ws_vnl, (size_t)s.npw * nb * sizeof(float2));
+      vnl = (float2*)s.ws_vnl.p;
+      nonlocal_mixed(s, nb, psi, ldp, vnl, s.npw, s.stream, precision == PWH_MIXED_FAST ? 1 : 3);
+    }
+    local_kinetic<float>(s, nb, psi, ldp, hpsi, ldh, s.stream, vnl, s.npw);
   }
 }
 
