@@ -220,14 +220,16 @@ __global__ void k_cg_init(const double2* __restrict__ R, int64_t ld, int64_t npw
 // z = K(T_G / eref[idx[j]]) (.) r  (Teter-Payne-Allan diagonal)
 __global__ void k_cg_precond(const double2* __restrict__ r, int64_t npw, const int* __restrict__ idx,
                              const double* __restrict__ eref, const double* __restrict__ kin,
-                             double2* __restrict__ z) {
+                             double2* __restrict__ z, const float* __restrict__ sfac,
+                             const int32_t* __restrict__ shell, int nshell) {
   const int j = blockIdx.y;
   const double e = eref[idx[j]];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npw;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double x = kin[i] / e;
     const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
-    const double k = p / (p + 16.0 * x * x * x * x);
+    double k = p / (p + 16.0 * x * x * x * x);
+    if (sfac) k *= exp((double)sfac[(size_t)j * nshell + shell[i]]);
     const double2 v = r[(size_t)j * npw + i];
     z[(size_t)j * npw + i] = make_double2(k * v.x, k * v.y);
   }
@@ -333,11 +335,12 @@ static void project_out(System& s, const double2* X, int nb, double2* v, int k, 
 
 // Approximate solution t (npw x k) of (I-XX^H)(H-theta_j)(I-XX^H) t_j = -r_j
 // for the bands idx[0..k), by `iters` steps of CG preconditioned with the TPA
-// diagonal, H applied in reduced precision.
+// diagonal (times the learned factor exp(s) per shell and band when sfac is
+// given), H applied in reduced precision.
 static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const double2* R,
                           const int* idx, int k, const double* theta, const double* eref,
                           int iters, int prec, double2* t, double2* Wc, int* n_apply,
-                          cudaStream_t st) {
+                          cudaStream_t st, const float* sfac = nullptr) {
   const int64_t npw = s.npw;
   ensure(w.cg, (size_t)4 * npw * k * sizeof(double2) + 8 * (size_t)k * sizeof(double) + 256);
   double2* r = (double2*)w.cg.p;
@@ -349,7 +352,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
   const dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (npw + 255) / 256)), k);
   k_cg_init<<<g2, 256, 0, st>>>(R, npw, npw, idx, r, t);
   PWH_LAUNCH_CHECK();
-  k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
+  k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z, sfac, s.d_shell, s.nshell);
   PWH_LAUNCH_CHECK();
   project_out(s, X, nb, z, k, Wc, st);
   PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -367,7 +370,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[cur], pq);
     PWH_LAUNCH_CHECK();
     if (it + 1 == iters) break;
-    k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z);
+    k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z, sfac, s.d_shell, s.nshell);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, z, k, Wc, st);
     k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[cur ^ 1]);
@@ -519,6 +522,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   // and of the reduced phase (FP32-equivalent products of the same shapes,
   // the FP32 nonlocal term of the reduced-precision H)
   if (o.mixed && s.nproj > 0) ensure(s.ws_vnl, (size_t)npw * nb * sizeof(float2));
+  if (o.precond == PWH_PRECOND_MLP) ensure(w.mlp, (size_t)nb * s.nshell * sizeof(float));
   if (o.mixed) {
     x3_reserve(s, true, mmax, mmax, (int)npw);
     x3_reserve(s, false, (int)npw, nb, mmax);
@@ -684,8 +688,14 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     if (jd) {
       // Jacobi-Davidson step: corrections from the reduced-precision operator
       const int red = s.precision == PWH_FP64 ? PWH_MIXED : s.precision;
+      float* sfac = nullptr;
+      if (o.precond == PWH_PRECOND_MLP) {
+        ensure(w.mlp, (size_t)k * s.nshell * sizeof(float));
+        sfac = (float*)w.mlp.p;
+        mlp_factors(s, L.idx, k, L.theta, L.rn, L.eref, sfac, st);
+      }
       jd_correction(s, w, L.X, nb, L.R, L.idx, k, L.theta, L.eref, o.jd_inner, red, T, L.Wc,
-                    &S.n_apply, st);
+                    &S.n_apply, st, sfac);
       k_col_dot<<<k, 1024, 0, st>>>(T, T, npw, L.t0);
       PWH_LAUNCH_CHECK();
       k_sqrt<<<1, 256, 0, st>>>(L.t0, k);

@@ -947,12 +947,21 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
       // unitary, Q (3I - Q^H Q)/2 in FP32 arithmetic; eigenvalues as Rayleigh
       // quotients q^H H q of those vectors (the FP32 diagonal drifts by the
       // accumulated non-unitarity of FP32 rotations, about n sweeps x 1e-7)
+      // (above n = 512 the FP32 GEMMs' own rounding, ~sqrt(n) FP32 units,
+      // would exceed the FP32 basis' deviation: the step then runs on the
+      // FP64-equivalent GEMM)
       double2* Qo = (Q == Q0) ? A0 : Q0;
-      cgemm_f32_simt(s, true, n, n, n, one, Q, n, Q, n, zero, G, n, st);
+      auto g3 = [&](bool cj, const double2* A, int64_t lda, const double2* B, double2* C) {
+        if (n > 512)
+          cgemm<double>(s, cj, n, n, n, one, A, lda, B, n, zero, C, n, st);
+        else
+          cgemm_f32_simt(s, cj, n, n, n, one, A, lda, B, n, zero, C, n, st);
+      };
+      g3(true, Q, n, Q, G);
       k_ns_rhs<<<gq, 256, 0, st>>>(G, n, A1);
       PWH_LAUNCH_CHECK();
-      cgemm_f32_simt(s, false, n, n, n, one, Q, n, A1, n, zero, Qo, n, st);
-      cgemm_f32_simt(s, false, n, n, n, one, H, ldh, Qo, n, zero, G, n, st);
+      g3(false, Q, n, A1, Qo);
+      g3(false, H, ldh, Qo, G);
       k_rayleigh<<<n, 128, 0, st>>>(Qo, G, n, dg);
       PWH_LAUNCH_CHECK();
       const int sb = (int)std::min<int64_t>(64, ((int64_t)nn + 1023) / 1024);

@@ -97,7 +97,59 @@ def load_system(cell, precision="mixed"):
     return s
 
 
+def evaluate(blob, seeds, nb=128, modes=("mixed", "mixed_jd")):
+    """Held-out comparison: for every seed, the same cell and start solved to
+    1e-8 with the TPA and with the learned preconditioner, per solver mode.
+    Returns one dict per seed (iterations, H applications, seconds, status,
+    final residual, max |dlambda| between the two)."""
+    import time
+
+    import torch
+
+    from . import synthetic as syn
+    kws = {"mixed": dict(mixed=True, switch_tol=1e-5, jd_inner=0),
+           "mixed_jd": dict(mixed=True, switch_tol=1e-3, jd_inner=20)}
+    res = []
+    for seed in seeds:
+        s = load_system(workload_cell(seed))
+        s.set_mlp(blob)
+        psi0 = torch.from_numpy(syn.initial_bands(seed, s.npw, nb)).cuda()
+        row = {"seed": int(seed), "npw": s.npw}
+        eigs = {}
+        for mode in modes:
+            for pc in ("tpa", "mlp"):
+                psi = psi0.clone()
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                eig, st, status = s.davidson(psi, tol=1e-8, precond=pc, check=False, **kws[mode])
+                torch.cuda.synchronize()
+                row[f"{pc}_{mode}"] = {"iters": st["iters"], "n_apply": st["n_apply"],
+                                       "time_s": time.perf_counter() - t, "status": status,
+                                       "resid": st["max_resid"]}
+                eigs[f"{pc}_{mode}"] = eig
+            row[f"max_dlambda_{mode}"] = float(np.abs(eigs[f"tpa_{mode}"] - eigs[f"mlp_{mode}"]).max())
+        res.append(row)
+        s.close()
+    return res
+
+
+def summarize(res, modes=("mixed", "mixed_jd")):
+    out = {}
+    for mode in modes:
+        it = {pc: sum(r[f"{pc}_{mode}"]["iters"] for r in res) for pc in ("tpa", "mlp")}
+        tm = {pc: sum(r[f"{pc}_{mode}"]["time_s"] for r in res) for pc in ("tpa", "mlp")}
+        out[mode] = {"iters_total": it, "time_total_s": tm,
+                     "all_converged": all(r[f"{pc}_{mode}"]["status"] == 0
+                                          for r in res for pc in ("tpa", "mlp")),
+                     "max_dlambda_ha": max(r[f"max_dlambda_{mode}"] for r in res)}
+    return out
+
+
 def main():
+    """The learned-preconditioner protocol: training rows from FP64 Davidson
+    trajectories on --train cells (seeds 1000..), a random subset of about
+    --rows rows, full-batch Adam on the GPU, then TPA vs MLP on --test
+    held-out cells (seeds 2000..).  Prints one JSON record."""
     import argparse
     import json
     import time
@@ -105,50 +157,45 @@ def main():
     import torch
 
     from . import synthetic as syn
-    ap = argparse.ArgumentParser(description="train the learned preconditioner on GPU and "
-                                             "compare it with TPA on held-out cells")
-    ap.add_argument("--train", type=int, default=32)
-    ap.add_argument("--test", type=int, default=8)
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=20)
     ap.add_argument("--nb", type=int, default=128)
+    ap.add_argument("--rows", type=int, default=1_000_000)
     ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--out", default="mlp_blob.npy")
+    ap.add_argument("--out", default=None, help="save the trained blob (.npy)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     t0 = time.time()
-    parts = []
+    parts, nrows = [], 0
     s = None
     for seed in range(1000, 1000 + a.train):
         s = load_system(workload_cell(seed))
         psi0 = torch.from_numpy(syn.initial_bands(seed, s.npw, a.nb)).cuda()
-        parts.append(harvest(s, psi0, snapshots=(2, 5, 10)))
-    rows = tuple(torch.cat([p[i] for p in parts]) for i in range(3))
+        F, y, w = harvest(s, psi0, snapshots=(2, 5, 10))
+        keep = torch.nonzero(w > 0).flatten()
+        parts.append((F[keep], y[keep], w[keep]))
+        nrows += int(keep.numel())
+        s.close()
+    F = torch.cat([p[0] for p in parts])
+    y = torch.cat([p[1] for p in parts])
+    w = torch.cat([p[2] for p in parts])
+    if F.shape[0] > a.rows:
+        g = torch.Generator(device="cuda").manual_seed(0)
+        pick = torch.randperm(F.shape[0], device="cuda", generator=g)[:a.rows]
+        F, y, w = F[pick], y[pick], w[pick]
     t_data = time.time() - t0
-    blob, hist = train(s, rows, steps=a.steps, lr=2e-3, log_every=500)
+    s = load_system(workload_cell(1000))
+    blob, hist = train(s, (F, y, w), steps=a.steps, lr=2e-3, log_every=500)
+    s.close()
     t_train = time.time() - t0 - t_data
-    np.save(a.out, blob)
-    res = []
-    for seed in range(2000, 2000 + a.test):
-        s = load_system(workload_cell(seed))
-        s.set_mlp(blob)
-        psi0 = torch.from_numpy(syn.initial_bands(seed, s.npw, a.nb)).cuda()
-        row = {"seed": seed, "npw": s.npw}
-        for pc in ("tpa", "mlp"):
-            for mode, kw in (("mixed", dict(mixed=True, switch_tol=1e-5, jd_inner=0)),
-                             ("mixed_jd", dict(mixed=True, switch_tol=1e-3, jd_inner=20))):
-                psi = psi0.clone()
-                torch.cuda.synchronize()
-                t = time.time()
-                eig, st, status = s.davidson(psi, tol=1e-8, precond=pc, check=False, **kw)
-                row[f"{pc}_{mode}"] = {"iters": st["iters"], "n_apply": st["n_apply"],
-                                       "time_s": time.time() - t, "status": status,
-                                       "resid": st["max_resid"], "eig0": float(eig[0])}
-                row.setdefault("eigs", {})[f"{pc}_{mode}"] = eig
-        row["max_dlambda_tpa_vs_mlp"] = float(np.abs(row["eigs"]["tpa_mixed"] - row["eigs"]["mlp_mixed"]).max())
-        del row["eigs"]
-        res.append(row)
-    summary = {"train_cells": a.train, "test_cells": a.test, "rows": int(rows[0].shape[0]),
-               "data_s": t_data, "train_s": t_train, "loss_history": hist, "held_out": res}
-    print(json.dumps(summary))
+    if a.out:
+        np.save(a.out, blob)
+    res = evaluate(blob, range(2000, 2000 + a.test), nb=a.nb)
+    print(json.dumps({"train_cells": a.train, "test_cells": a.test, "nb": a.nb,
+                      "rows_harvested": nrows, "rows_trained": int(F.shape[0]),
+                      "data_s": t_data, "train_s": t_train, "loss_history": hist,
+                      "summary": summarize(res), "held_out": res}))
 
 
 if __name__ == "__main__":
