@@ -15,6 +15,9 @@ eye against the method's definitions:
                   potential's DFT) and by the FFT route; the dense H matrix
 * ``davidson``    block Davidson with the Teter-Payne-Allan preconditioner
 * ``mlp``         the learned preconditioner's network, loss, gradients and Adam
+* ``scf``         the SCF steps around H: density of a set of bands, Hartree
+                  potential by the Fourier-space Poisson solution, LDA
+                  exchange-correlation (Slater + Perdew-Zunger)
 
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``) tie each function
 to closed forms, invariants, brute force or library routines, never to itself.
