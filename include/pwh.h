@@ -240,6 +240,32 @@ pwh_status pwh_get_davidson_trace(const pwh_system* sys, int32_t cap,
 pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_host,
                                    double* eig, pwh_davidson_stats* stats);
 
+/* ------------------------------------------------------------- SCF steps --
+ * The steps either side of H|psi> in a self-consistent Kohn-Sham calculation
+ * (Sec. "Introduction"): the density of the occupied bands, then the new local
+ * potential.  Hartree atomic units, FP64, grids in the layout of
+ * pwh_set_potential (N1*N2*N3 doubles, C order, i3 fastest, point (i1,i2,i3) at
+ * r = sum_d (i_d/N_d) a_d), all DEVICE pointers on the system's stream. */
+
+/* rho(r) = sum_n occ[n] |psi_n(r)|^2 with psi_n(r) = Omega^{-1/2} sum_G
+ * c_n(G) e^{i(k+G).r}, on the system's FFT grid.  psi: nb bands, public order,
+ * ld_psi >= npw; occ: HOST double[nb]; rho: output grid.  The integral of rho
+ * (grid sum times Omega/N) is sum_n occ[n] ||c_n||^2.  Synchronous. */
+pwh_status pwh_density(pwh_system* sys, int32_t nb, const void* psi, int64_t ld_psi,
+                       const double* occ, double* rho);
+
+/* v_out = v_ion + V_H + v_xc from the density rho (v_ion may be NULL):
+ * V_H(G) = 4 pi rho(G)/|G|^2, the Fourier-space solution of the Poisson
+ * equation on the FFT box (the Hartree kernel of the exact-exchange pair
+ * densities, Sec. "Advanced implementation of exact (Fock) exchange"), with
+ * G = 0 (neutralising background) and the Nyquist planes of even N_d set to
+ * zero; v_xc: local-density exchange (Slater) and correlation
+ * (Perdew-Zunger, Phys. Rev. B 23, 5048 (1981)); points with rho <= 1e-20
+ * get none.  energies (HOST double[3], may be NULL): E_H = 1/2 int V_H rho,
+ * E_xc = int rho eps_xc, int v_xc rho.  v_out may alias v_ion.  Synchronous. */
+pwh_status pwh_hartree_xc(pwh_system* sys, const double* rho, const double* v_ion, double* v_out,
+                          double* energies);
+
 /* ----------------------------------------------------- learned preconditioner --
  * Not in the paper.  A 4 -> 64 -> 64 -> 1 SiLU network corrects the TPA
  * diagonal per (shell of equal |k+G|, band): K = K_TPA * exp(clip(s, -3, 3)),

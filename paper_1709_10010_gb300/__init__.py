@@ -101,6 +101,8 @@ SIGNATURES = {
     "pwh_davidson_solve_host": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_p,
                                          ctypes.POINTER(DavidsonStats)]),
     "pwh_get_davidson_trace": (_c_i32, [_c_p, _c_i32, _c_p, ctypes.POINTER(_c_i32)]),
+    "pwh_density": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_p]),
+    "pwh_hartree_xc": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_subspace_gemm": (_c_i32, [_c_p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_p, _c_p, _c_i64,
                                    _c_p, _c_i64, _c_p, _c_p, _c_i64]),
@@ -348,6 +350,36 @@ class System:
         _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
                                       hpsi.ctypes.data_as(_c_p)))
         return hpsi
+
+    # ------------------------------------------------------------ SCF steps
+    def density(self, psi, occ):
+        """rho on the FFT grid (CUDA float64 tensor of shape fft) from bands psi
+        ((nb, npw) CUDA complex128, public order) with occupations occ."""
+        torch = _torch()
+        nb = int(psi.shape[0])
+        rho = torch.empty(self.fft, dtype=torch.float64, device="cuda")
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        assert occ.size == nb
+        if nb:
+            p, ld = _band_ptr(psi, self.npw)
+        else:
+            p, ld = None, self.npw
+        _check(lib().pwh_density(self._h, nb, p, ld, occ.ctypes.data_as(_c_p),
+                                 ctypes.c_void_p(rho.data_ptr())))
+        return rho
+
+    def hartree_xc(self, rho, v_ion=None):
+        """(v_ion + V_H + v_xc as a CUDA float64 grid, dict of E_H, E_xc and
+        int v_xc rho) from the density rho (CUDA float64 grid)."""
+        torch = _torch()
+        rho = rho.contiguous()
+        assert rho.dtype == torch.float64 and rho.numel() == int(np.prod(self.fft))
+        out = torch.empty_like(rho)
+        vi = ctypes.c_void_p(v_ion.contiguous().data_ptr()) if v_ion is not None else None
+        en = np.zeros(3, dtype=np.float64)
+        _check(lib().pwh_hartree_xc(self._h, ctypes.c_void_p(rho.data_ptr()), vi,
+                                    ctypes.c_void_p(out.data_ptr()), en.ctypes.data_as(_c_p)))
+        return out, {"e_hartree": float(en[0]), "e_xc": float(en[1]), "int_vxc_rho": float(en[2])}
 
     # ----------------------------------------------------- learned precond
     def shells(self):

@@ -229,6 +229,7 @@ struct System {
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)
+  DevBuf<char> ws_grid;             // SCF steps: a real and a complex full-box grid
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
   DevBuf<char> ws_oz;               // sliced operands and partials of the FP64-equivalent GEMM
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for
@@ -312,7 +313,15 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, float2* 
 int* device_error_word(System& s);
 void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi,
                     int64_t ldh, int precision);
-void permute_public_to_internal(System& s, const double2* src, double2* dst, int nb);
+void permute_public_to_internal(System& s, const double2* src, double2* dst, int nb,
+                                int64_t lds = 0);
+// rho_int ([i3][i2][i1], unscaled) += sum_b occ_b |psi_b(r)|^2 for bands in
+// internal order (ld npw), occ on the device.
+void density_accumulate(System& s, int nb, const double2* psi_int, const double* occ_dev,
+                        double* rho_int);
+// In-place unscaled 3D FFT of the full box (complex FP64, C order i3 fastest):
+// forward exp(-i G.r), inverse exp(+i G.r).
+void box_fft(System& s, double2* box, bool inverse);
 void mlp_factors(System& s, const int* idx, int k, const double* theta, const double* rn,
                  const double* eref, float* out, cudaStream_t st);
 

@@ -369,6 +369,180 @@ template void local_kinetic<double>(System&, int, const double2*, int64_t, doubl
 template void local_kinetic<float>(System&, int, const double2*, int64_t, double2*, int64_t,
                                    cudaStream_t, const float2*, int64_t);
 
+// ------------------------------------------------ SCF: density, full box ----
+// Density of a set of bands (FP64): per z-plane and slice of bands, the
+// y-inverse FFT on the stick columns and the x-inverse FFT on every row of each
+// band (the first half of k_plane), then rho[z][y][x] += occ_b |psi_b|^2
+// (atomic: the slices of one plane add into the same points).  W holds the
+// z-inverse-transformed sticks of the batch (k_zinv).  rho: internal layout
+// [i3][i2][i1], unscaled.
+__global__ void __launch_bounds__(512) k_density_plane(const double2* __restrict__ W, int64_t wband,
+                                                       int nsticks, int ncols,
+                                                       const int32_t* __restrict__ stick_col,
+                                                       const int32_t* __restrict__ stick_y,
+                                                       const int32_t* __restrict__ col_x, FftPlan pl1,
+                                                       FftPlan pl2, const double2* __restrict__ tw_g,
+                                                       const int16_t* __restrict__ perm_g,
+                                                       const double* __restrict__ occ, int nbands,
+                                                       int per_slice, double* __restrict__ rho,
+                                                       int rows) {
+  using T = double;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = pl1.n, n2 = pl2.n;
+  const int ld2 = n2 + 1, ld1 = n1 + 1;
+  cx<T>* C = (cx<T>*)smem_raw;
+  cx<T>* Rw = C + (size_t)ncols * ld2;
+  cx<T>* tw1 = Rw + (size_t)rows * ld1;
+  cx<T>* tw2 = tw1 + n1;
+  int16_t* irev1 = (int16_t*)(tw2 + n2);
+  int16_t* irev2 = irev1 + n1;
+  const int z = blockIdx.x;
+  const int bb0 = blockIdx.y * per_slice, bb1 = min(nbands, bb0 + per_slice);
+  for (int t = threadIdx.x; t < n1; t += blockDim.x) {
+    tw1[t] = tw_g[pl1.tw_off + t];
+    irev1[t] = perm_g[pl1.perm_off + t];
+  }
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    tw2[t] = tw_g[pl2.tw_off + t];
+    irev2[t] = perm_g[pl2.perm_off + t];
+  }
+  double* rz = rho + (size_t)z * n1 * n2;
+  for (int b = bb0; b < bb1; ++b) {
+    const double f = occ[b];
+    const cx<T>* plane = W + (size_t)b * wband + (size_t)z * nsticks;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ncols * ld2; t += blockDim.x) C[t] = mk<T>(0, 0);
+    __syncthreads();
+    for (int st = threadIdx.x; st < nsticks; st += blockDim.x)
+      C[stick_col[st] * ld2 + irev2[stick_y[st]]] = plane[st];
+    __syncthreads();
+    fft_block<T, true>(C, ncols, ld2, 1, pl2, tw2);
+    for (int y0 = 0; y0 < n2; y0 += rows) {
+      const int nr = min(rows, n2 - y0);
+      for (int t = threadIdx.x; t < nr * ld1; t += blockDim.x) Rw[t] = mk<T>(0, 0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < nr * ncols; t += blockDim.x) {
+        const int r = t / ncols, c = t - r * ncols;
+        Rw[r * ld1 + irev1[col_x[c]]] = C[c * ld2 + y0 + r];
+      }
+      __syncthreads();
+      fft_block<T, true>(Rw, nr, ld1, 1, pl1, tw1);
+      for (int t = threadIdx.x; t < nr * n1; t += blockDim.x) {
+        const int r = t / n1, x = t - r * n1;
+        const cx<T> v = Rw[r * ld1 + x];
+        atomicAdd(rz + (size_t)(y0 + r) * n1 + x, f * (v.x * v.x + v.y * v.y));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// 1D FFTs of the full n1 x n2 x n3 box (complex FP64, C order: i3 fastest)
+// along one axis: lines of `axis` (0, 1, 2 for i1, i2, i3), `lines` of them a
+// block, chosen consecutive in the fastest other index so that loads and
+// stores are contiguous runs.  Forward: exp(-i), natural order in and out
+// (unscaled); inverse: exp(+i), unscaled.
+__global__ void __launch_bounds__(256) k_box_fft_axis(double2* __restrict__ box, int n1, int n2,
+                                                      int n3, int axis, int inverse, FftPlan pl,
+                                                      const double2* __restrict__ tw_g,
+                                                      const int16_t* __restrict__ perm_g, int lines) {
+  using T = double;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = pl.n, ld = n + 1;
+  cx<T>* buf = (cx<T>*)smem_raw;
+  cx<T>* tw = buf + (size_t)lines * ld;
+  int16_t* irev = (int16_t*)(tw + n);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    tw[t] = tw_g[pl.tw_off + t];
+    irev[t] = perm_g[pl.perm_off + t];
+  }
+  // the two other axes: slow (os) and fast (of) with their strides
+  const int64_t s1 = (int64_t)n2 * n3, s2 = n3;
+  int64_t es, ss, fs;
+  int nslow, nfast;
+  if (axis == 2) { es = 1; ss = s1; nslow = n1; fs = s2; nfast = n2; }
+  else if (axis == 1) { es = s2; ss = s1; nslow = n1; fs = 1; nfast = n3; }
+  else { es = s1; ss = s2; nslow = n2; fs = 1; nfast = n3; }
+  const int64_t nlines = (int64_t)nslow * nfast;
+  const int64_t l0 = (int64_t)blockIdx.x * lines;
+  const int nl = (int)min((int64_t)lines, nlines - l0);
+  __syncthreads();
+  // element e of local line j: consecutive threads walk j first when the
+  // line axis is strided (contiguous runs along the fast axis), e first else
+  for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+    const int j = axis == 2 ? t / n : t % nl, e = axis == 2 ? t % n : t / nl;
+    const int64_t L = l0 + j;
+    const double2 v = box[(L / nfast) * ss + (L % nfast) * fs + e * es];
+    buf[j * ld + (inverse ? irev[e] : e)] = v;
+  }
+  __syncthreads();
+  if (inverse)
+    fft_block<T, true>(buf, nl, ld, 1, pl, tw);
+  else
+    fft_block<T, false>(buf, nl, ld, 1, pl, tw);
+  for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+    const int j = axis == 2 ? t / n : t % nl, e = axis == 2 ? t % n : t / nl;
+    const int64_t L = l0 + j;
+    box[(L / nfast) * ss + (L % nfast) * fs + e * es] = buf[j * ld + (inverse ? e : irev[e])];
+  }
+}
+
+void density_accumulate(System& s, int nb, const double2* psi_int, const double* occ_dev,
+                        double* rho_int) {
+  using T = double;
+  const int64_t wband = (int64_t)s.n3 * s.nsticks;
+  const int64_t per = wband * (int64_t)sizeof(cx<T>);
+  const int batch = (int)std::max<int64_t>(1, std::min<int64_t>(nb, (64ll << 20) / std::max<int64_t>(per, 1)));
+  ensure(s.ws_fft, (size_t)(batch * per));
+  cx<T>* W = (cx<T>*)s.ws_fft.p;
+  const int spb = stick_block(s.n3);
+  const size_t zsmem = ((size_t)spb * (s.n3 + 1) + s.n3) * sizeof(cx<T>) + s.n3 * sizeof(int16_t);
+  int rows = s.n2;
+  while (rows > 1 && plane_smem<T>(s, rows) > 100 * 1024) rows = (rows + 1) / 2;
+  const size_t psmem = plane_smem<T>(s, rows);
+  if (psmem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_density_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_zinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  cudaStream_t st = s.stream;
+  for (int b0 = 0; b0 < nb; b0 += batch) {
+    const int bb = std::min(batch, nb - b0);
+    dim3 gz((s.nsticks + spb - 1) / spb, bb);
+    k_zinv<T><<<gz, 256, zsmem, st>>>(psi_int + (size_t)b0 * s.npw, s.npw, s.d_stick_off,
+                                       s.d_stick_of, s.d_zpos, s.nsticks, s.plan[2], s.d_tw64,
+                                       s.d_perm, W, wband, spb);
+    PWH_LAUNCH_CHECK();
+    // slices of bands per plane: enough blocks to fill the GPU
+    const int slices = std::max(1, std::min(bb, (2 * 152 + s.n3 - 1) / s.n3));
+    const int per_slice = (bb + slices - 1) / slices;
+    k_density_plane<<<dim3(s.n3, (bb + per_slice - 1) / per_slice), 512, psmem, st>>>(
+        W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y, s.d_col_x, s.plan[0], s.plan[1],
+        s.d_tw64, s.d_perm, occ_dev + b0, bb, per_slice, rho_int, rows);
+    PWH_LAUNCH_CHECK();
+  }
+}
+
+void box_fft(System& s, double2* box, bool inverse) {
+  const int n[3] = {s.n1, s.n2, s.n3};
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_box_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  for (int axis = 2; axis >= 0; --axis) {
+    const FftPlan& pl = s.plan[axis];
+    const int64_t nlines = (int64_t)n[0] * n[1] * n[2] / n[axis];
+    // lines a block: 16 (a 256-byte run of the fast axis), fewer if n is large
+    int lines = 16;
+    while (lines > 1 && ((size_t)lines * (pl.n + 1) + pl.n) * sizeof(double2) > 96 * 1024) lines /= 2;
+    const size_t smem = ((size_t)lines * (pl.n + 1) + pl.n) * sizeof(double2) + pl.n * sizeof(int16_t);
+    k_box_fft_axis<<<(unsigned)((nlines + lines - 1) / lines), 256, smem, s.stream>>>(
+        box, s.n1, s.n2, s.n3, axis, inverse ? 1 : 0, pl, s.d_tw64, s.d_perm, lines);
+    PWH_LAUNCH_CHECK();
+  }
+}
+
 // ------------------------------------------- allocation-free entry point ----
 // Scratch for pwh_apply_local_noalloc: the stick buffer of the FFT passes lives
 // in this fixed device array instead of a cudaMalloc'ed workspace.  Every GPU

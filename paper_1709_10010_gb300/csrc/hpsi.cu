@@ -38,9 +38,10 @@ static int grid_for(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(152 * 16, (n + 255) / 256));
 }
 
-void permute_public_to_internal(System& s, const double2* src, double2* dst, int nb) {
+void permute_public_to_internal(System& s, const double2* src, double2* dst, int nb, int64_t lds) {
   const int64_t n = s.npw * (int64_t)nb;
-  k_permute_in<<<grid_for(n), 256, 0, s.stream>>>(src, s.npw, s.npw, nb, s.d_int_to_pub, dst, s.npw);
+  k_permute_in<<<grid_for(n), 256, 0, s.stream>>>(src, lds > 0 ? lds : s.npw, s.npw, nb,
+                                                  s.d_int_to_pub, dst, s.npw);
   PWH_LAUNCH_CHECK();
 }
 
