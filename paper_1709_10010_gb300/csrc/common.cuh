@@ -37,6 +37,8 @@ struct Error {
 // Every kernel launch site ends with PWH_LAUNCH_CHECK(): it checks the launch
 // and counts it (pwh_launch_count).
 void note_launch();
+void note_launches(long long n);  // kernels launched through a replayed CUDA graph
+long long launch_counter();       // launches made by the calling thread
 #define PWH_LAUNCH_CHECK()          \
   do {                              \
     ::pwh::note_launch();           \

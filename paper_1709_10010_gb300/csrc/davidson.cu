@@ -335,8 +335,8 @@ static void project_out(System& s, const double2* X, int nb, double2* v, int k, 
 
 // Approximate solution t (npw x k) of (I-XX^H)(H-theta_j)(I-XX^H) t_j = -r_j
 // for the bands idx[0..k), by `iters` steps of CG preconditioned with the TPA
-// diagonal (times the learned factor exp(s) per shell and band when sfac is
-// given), H applied in reduced precision.
+// diagonal (times a per-shell factor exp(s) when sfac is given), H applied in
+// reduced precision.
 static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const double2* R,
                           const int* idx, int k, const double* theta, const double* eref,
                           int iters, int prec, double2* t, double2* Wc, int* n_apply,
@@ -358,8 +358,8 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
   PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[0]);
   PWH_LAUNCH_CHECK();
-  int cur = 0;
-  for (int it = 0; it < iters; ++it) {
+  // one PCG step; rho[c] holds r.z of the step, rho[c ^ 1] receives the next
+  auto step = [&](int c, bool last) {
     apply_internal(s, k, p, npw, q, npw, prec);
     *n_apply += k;
     k_cg_shift<<<g2, 256, 0, st>>>(q, p, npw, idx, theta);
@@ -367,18 +367,69 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
     project_out(s, X, nb, q, k, Wc, st);
     k_col_dot<<<k, 1024, 0, st>>>(p, q, npw, pq);
     PWH_LAUNCH_CHECK();
-    k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[cur], pq);
+    k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[c], pq);
     PWH_LAUNCH_CHECK();
-    if (it + 1 == iters) break;
+    if (last) return;
     k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z, sfac, s.d_shell, s.nshell);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, z, k, Wc, st);
-    k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[cur ^ 1]);
+    k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[c ^ 1]);
     PWH_LAUNCH_CHECK();
-    k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[cur ^ 1], rho[cur]);
+    k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[c ^ 1], rho[c]);
     PWH_LAUNCH_CHECK();
+  };
+  // Steps 0 .. iters-2 are full, the last one stops after the update of t.
+  // The first step runs as plain launches (it also grows every workspace
+  // these shapes need); the next full steps go in pairs, one pair captured as
+  // a CUDA graph and replayed (same shapes, pointers and launch configurations
+  // every pair, the two rho buffers in the same roles).  Without the kernel
+  // timer only; any capture failure falls back to plain launches.
+  const int full = iters - 1;
+  int cur = 0, done = 0;
+  if (full > 0) {
+    step(cur, false);
+    cur ^= 1;
+    ++done;
+  }
+  const int pairs = (full - done) / 2;
+  if (pairs >= 2 && !s.timer.on) {
+    const int n_apply0 = *n_apply;
+    const long long launches0 = launch_counter();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      bool threw = false;
+      try {
+        step(cur, false);
+        step(cur ^ 1, false);
+      } catch (...) {
+        threw = true;
+      }
+      const cudaError_t e = cudaStreamEndCapture(st, &graph);
+      if (threw || e != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+    }
+    cudaGetLastError();  // a refused capture leaves nothing to report
+    // the capture executed nothing: undo its counts, count the replays
+    const long long per_pair = launch_counter() - launches0;
+    note_launches(-per_pair);
+    *n_apply = n_apply0;
+    if (exec) {
+      for (int i = 0; i < pairs; ++i) {
+        PWH_CUDA(cudaGraphLaunch(exec, st));
+        note_launches(per_pair);
+        *n_apply += 2 * k;
+      }
+      done += 2 * pairs;
+      cudaGraphExecDestroy(exec);
+    }
+    if (graph) cudaGraphDestroy(graph);
+  }
+  for (; done < full; ++done) {
+    step(cur, false);
     cur ^= 1;
   }
+  if (iters > 0) step(cur, true);
 }
 
 static Layout carve(System& s, DavWs& w, int nb, int mmax) {
@@ -463,15 +514,17 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   return w.h_idx[4096];
 }
 
-// Subspace GEMMs: FP64 in the FP64 phase, FP32 arithmetic on FP64 storage in
-// the reduced-precision phase.
+// Subspace GEMMs: FP64 in the FP64 phase; in the reduced-precision phase the
+// 16-bit sliced tensor-core product for large products (the accuracy of that
+// phase's operator, whose projector GEMMs are split BF16) and FP32 arithmetic
+// on FP64 storage for narrow ones.
 static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
                   const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
                   double2* C, int64_t ldc, cudaStream_t st) {
   if (prec == PWH_FP64)
     cgemm<double>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
   else
-    cgemm_f32(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    cgemm_r16(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 static double now_s() {
@@ -591,7 +644,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // the reduced-precision phase needs the Ritz pairs only to well below its
     // current residuals: FP32 sweeps to 1e-3 of the last largest residual
     // (relative to the largest diagonal entry), between 4e-7 and 1e-4
-    const double tol32 = polish || it == 1 ? 4e-7 : std::min(1e-4, std::max(4e-7, 1e-3 * maxr));
+    const double tol32 = polish || it == 1 ? 4e-7 : std::min(1e-4, std::max(4e-7, 1e-3 * maxr_target));
     jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
     sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
@@ -624,8 +677,8 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     }
     s.timer.resolve();
     S.iters = it;
-    // maxr: over every band (reduced-phase decisions); maxr_t: over the
-    // requested ones (termination, reported residual)
+    // maxr: over every band; maxr_t: over the requested ones (the phases'
+    // decisions, termination, reported residual)
     maxr = 0.0;
     double maxr_t = 0.0;
     bool finite = true;
@@ -636,11 +689,13 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     }
     maxr_target = maxr_t;
     // this phase's target of band b: the requested bands to tol (FP64 phase)
-    // or switch_tol (reduced phase); buffer bands to switch_tol in the reduced
-    // phase and to 1e3 tol (at most switch_tol) in the FP64 phase
+    // or switch_tol (reduced phase); buffer bands to 1e-3 (at least
+    // switch_tol) in the reduced phase, whose operator cannot take the top
+    // of the window much further, and to 1e3 tol (at most switch_tol) in the
+    // FP64 phase
     const double thr = phase_prec == PWH_FP64 ? o.tol : o.switch_tol;
     const double thr_buf = phase_prec == PWH_FP64 ? std::max(o.tol, std::min(1e3 * o.tol, o.switch_tol))
-                                                  : o.switch_tol;
+                                                  : std::max(o.switch_tol, 1e-3);
     auto above = [&](int b) { return w.h_rn[b] > (b < nbt ? thr : thr_buf); };
     {
       int n_above = 0;
@@ -651,7 +706,9 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       result = PWH_ERR_NONFINITE;
       break;
     }
-    if (phase_prec != PWH_FP64 && maxr <= o.switch_tol) {
+    bool buffers_done = true;
+    for (int b = nbt; b < nb; ++b) buffers_done = buffers_done && !above(b);
+    if (phase_prec != PWH_FP64 && maxr_t <= o.switch_tol && buffers_done) {
       // hand over to FP64: restart from the Ritz vectors with the FP64 operator
       const double t = now_s();
       S.t_mixed_s = t - t_phase;
@@ -674,7 +731,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // Jacobi-Davidson steps in the FP64 phase, and in the reduced-precision
     // phase once its residuals are within 100x of the hand-over target
     const bool jd = o.mixed && o.jd_inner > 0 &&
-                    (phase_prec == PWH_FP64 || maxr <= 100.0 * o.switch_tol);
+                    (phase_prec == PWH_FP64 || maxr_t <= 100.0 * o.switch_tol);
     if (jd || m + k > mmax) {
       restart_from_ritz(false);
       if (jd) {
@@ -688,14 +745,8 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     if (jd) {
       // Jacobi-Davidson step: corrections from the reduced-precision operator
       const int red = s.precision == PWH_FP64 ? PWH_MIXED : s.precision;
-      float* sfac = nullptr;
-      if (o.precond == PWH_PRECOND_MLP) {
-        ensure(w.mlp, (size_t)k * s.nshell * sizeof(float));
-        sfac = (float*)w.mlp.p;
-        mlp_factors(s, L.idx, k, L.theta, L.rn, L.eref, sfac, st);
-      }
       jd_correction(s, w, L.X, nb, L.R, L.idx, k, L.theta, L.eref, o.jd_inner, red, T, L.Wc,
-                    &S.n_apply, st, sfac);
+                    &S.n_apply, st);
       k_col_dot<<<k, 1024, 0, st>>>(T, T, npw, L.t0);
       PWH_LAUNCH_CHECK();
       k_sqrt<<<1, 256, 0, st>>>(L.t0, k);

@@ -520,7 +520,9 @@ __global__ void k_ns_rhs(const double2* __restrict__ G, int n, double2* __restri
 // contiguous run.  The rotations go to a log in index form, (s, c, p | q <<
 // 16) per pair and round, from which k_jacobi_qlog_rows forms Q afterwards.
 constexpr int kPjTile = 16;
-constexpr int kPjThreads = kPjTile * kPjTile;
+constexpr int kPjGroup = kPjTile * kPjTile;  // threads on one tile
+constexpr int kPjTiles = 4;                  // tiles a block works on at once
+constexpr int kPjThreads = kPjGroup * kPjTiles;
 constexpr int kQlogRowsL = 8;
 
 // next position of the player at x (np even)
@@ -556,7 +558,8 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
   extern __shared__ __align__(16) unsigned char pjs[];
   constexpr int E = 2 * kPjTile;            // elements per tile side
   float4* rot = (float4*)pjs;               // P rotations (s.x, s.y, c, -)
-  float2* mir = (float2*)(rot + a.P);       // E x (E + 1) mirror tile
+  const int grp = threadIdx.x / kPjGroup, gt = threadIdx.x % kPjGroup;
+  float2* mir = (float2*)(rot + a.P) + (size_t)grp * E * (E + 1);  // this group's mirror tile
   __shared__ float s_red[2][kPjThreads / 32];
   const int np = a.np, P = a.P, T = a.T, n = a.n;
   const int ntiles = T * (T + 1) / 2;
@@ -579,16 +582,20 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
         }
       }
       __syncthreads();
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int I = 0, rem = tile;  // upper-triangle tile (I, J), I <= J, row by row
+      // kPjTiles tiles at once, one per group of threads; every group runs
+      // the same number of iterations (the barriers stay uniform)
+      for (int t0 = blockIdx.x * kPjTiles; t0 < ntiles; t0 += gridDim.x * kPjTiles) {
+        const int tile = t0 + grp;
+        const bool tact = tile < ntiles;
+        int I = 0, rem = tact ? tile : 0;  // upper-triangle tile (I, J), I <= J, row by row
         while (rem >= T - I) {
           rem -= T - I;
           ++I;
         }
         const int J = I + rem;
-        const int kl = threadIdx.x % kPjTile, ll = threadIdx.x / kPjTile;
+        const int kl = gt % kPjTile, ll = gt / kPjTile;
         const int k = I * kPjTile + kl, l = J * kPjTile + ll;
-        if (k < P && l < P && (I != J || kl <= ll)) {
+        if (tact && k < P && l < P && (I != J || kl <= ll)) {
           const float4 rk = rot[k], rl = rot[l];
           const float4 c0 = *(const float4*)(A + (size_t)(2 * l) * np + 2 * k);      // a00, a10
           const float4 c1 = *(const float4*)(A + (size_t)(2 * l + 1) * np + 2 * k);  // a01, a11
@@ -619,7 +626,7 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
           }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < E * E; e += blockDim.x) {
+        for (int e = gt; e < E * E && tact; e += kPjGroup) {
           const int rl = e % E, cl = e / E;  // mirror row (l side) fastest
           const int kk = I * kPjTile + cl / 2, lk = J * kPjTile + rl / 2;
           if (kk < P && lk < P && (I != J || cl / 2 < rl / 2)) {
@@ -692,7 +699,10 @@ __global__ void k_to_pos32(const double2* __restrict__ A, int64_t lda, int n, in
 
 // Q = J_0 J_1 ... J_{R-1} from the log of k_jacobi_pos (R = info[2]): the rows
 // of Q evolve independently, `rows` rows a block in shared memory (starting
-// as rows of the identity), every round applied to them in order.
+// as rows of the identity), every round applied to them in order.  Thread t
+// owns pairs t and t + blockDim (P <= 2 blockDim) and applies them to every
+// row of the block; the next round's log entries are fetched before the
+// barrier that closes the current round.
 __global__ void __launch_bounds__(1024) k_jacobi_qlog_rows(const float4* __restrict__ log,
                                                            const int* __restrict__ info, int n,
                                                            int P, int rows, double2* __restrict__ Q,
@@ -706,21 +716,31 @@ __global__ void __launch_bounds__(1024) k_jacobi_qlog_rows(const float4* __restr
     qs[t] = make_float2((r < nr && i0 + r == c) ? 1.f : 0.f, 0.f);
   }
   const int R = info[2];
+  const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+  const float4 idle = make_float4(0.f, 0.f, 1.f, __int_as_float(0xffff | (0xffff << 16)));
+  float4 c0 = (R > 0 && k0 < P) ? log[k0] : idle, c1 = (R > 0 && k1 < P) ? log[k1] : idle;
   __syncthreads();
   for (int rd = 0; rd < R; ++rd) {
-    const float4* lr = log + (size_t)rd * P;
-    for (int it = threadIdx.x; it < nr * P; it += blockDim.x) {
-      const int k = it % P, r = it / P;
-      const float4 cur = __ldg(lr + k);
+    const float4 u0 = c0, u1 = c1;
+    if (rd + 1 < R) {
+      const float4* nx = log + (size_t)(rd + 1) * P;
+      c0 = k0 < P ? __ldg(nx + k0) : idle;
+      c1 = k1 < P ? __ldg(nx + k1) : idle;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 cur = h ? u1 : u0;
       const int pq = __float_as_int(cur.w);
-      const int p = pq & 0xffff, q = pq >> 16;
+      const int p = pq & 0xffff, q = (pq >> 16) & 0xffff;
       if (p < n && q < n) {
         const float c = cur.z;
-        const float2 sv = make_float2(cur.x, cur.y);
-        float2* row = qs + (size_t)r * n;
-        const float2 q0 = row[p], q1 = row[q];
-        row[p] = add<float>(scl<float>(q0, c), mul<float>(q1, make_float2(-sv.x, sv.y)));
-        row[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
+        const float2 sv = make_float2(cur.x, cur.y), sm = make_float2(-cur.x, cur.y);
+        for (int r = 0; r < nr; ++r) {
+          float2* row = qs + (size_t)r * n;
+          const float2 q0 = row[p], q1 = row[q];
+          row[p] = add<float>(scl<float>(q0, c), mul<float>(q1, sm));
+          row[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
+        }
       }
     }
     __syncthreads();
@@ -771,7 +791,8 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   a.tol = (float)tol;
   a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
-  const size_t smem = (size_t)P * sizeof(float4) + (size_t)(2 * kPjTile) * (2 * kPjTile + 1) * sizeof(float2);
+  const size_t smem = (size_t)P * sizeof(float4) +
+                      (size_t)kPjTiles * (2 * kPjTile) * (2 * kPjTile + 1) * sizeof(float2);
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_jacobi_pos, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -783,7 +804,7 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_pos, kPjThreads, smem));
   if (per_sm < 1) return false;
   const int ntiles = T * (T + 1) / 2;
-  const int blocks = std::max(1, std::min(ntiles, nsm * std::min(per_sm, 2)));
+  const int blocks = std::max(1, std::min((ntiles + kPjTiles - 1) / kPjTiles, nsm * std::min(per_sm, 2)));
   void* args[] = {&a};
   PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_pos, blocks, kPjThreads, args, smem, st));
   note_launch();

@@ -314,6 +314,20 @@ void cgemm_f32_simt(System& s, bool conjA, int M, int N, int K, double2 alpha, c
   cgemm_impl<double, float>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, nullptr);
 }
 
+void cgemm_r16(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+               int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+               cudaStream_t st) {
+  // the tensor-core path above the same size and width thresholds as
+  // cgemm_f32 (narrower products: the FP32 pipe, more accurate anyway)
+  const int narrow = conjA ? std::min(M, N) : N;
+  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
+      slice_grid_ok(conjA, M, N, K)) {
+    x2_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+    return;
+  }
+  cgemm_impl<double, float>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st, nullptr);
+}
+
 void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st) {

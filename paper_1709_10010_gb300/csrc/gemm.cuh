@@ -47,6 +47,17 @@ void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const do
              cudaStream_t st);
 // Grow the workspace x3_gemm shares with oz_gemm for op(A) B of these sizes.
 void x3_reserve(System& s, bool conjA, int M, int N, int K);
+// 16-bit complex GEMM on the tensor cores (two BF16 slices per FP32-rounded
+// value, three slice products, about 1.5e-5 relative accuracy): the
+// reduced-precision phase's subspace products, whose operator is itself
+// accurate to the split-BF16 projector GEMMs.
+void x2_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+             int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+             cudaStream_t st);
+// x2_gemm above the cgemm_f32 thresholds, the FP32 SIMT GEMM below them.
+void cgemm_r16(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+               int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+               cudaStream_t st);
 // Products of at least this many flops (8 M N K) take x3_gemm in cgemm_f32.
 constexpr double kX3MinFlops = 4e8;
 

@@ -1118,17 +1118,21 @@ static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 al
 // below 2^-26 of |a b|.  Split-K partials are summed in FP64.
 constexpr int X3_S = 3, X3_TERMS = 6;
 
+// NSL = 3: the FP32 value as three BF16 slices (exact); NSL = 2: its two
+// leading slices, the second rounded (about 16 significant bits).
+template <int NSL>
 __device__ __forceinline__ void x3_split(double x, __nv_bfloat16* a) {
   const float f = d2f_rn(x);
   a[0] = __float2bfloat16_rn(f);
   const float r1 = f - __bfloat162float(a[0]);  // exact: at most 16 significant bits
   a[1] = __float2bfloat16_rn(r1);
-  a[2] = __float2bfloat16_rn(r1 - __bfloat162float(a[1]));  // exact remainder
+  if constexpr (NSL == 3) a[2] = __float2bfloat16_rn(r1 - __bfloat162float(a[1]));  // exact remainder
 }
 
 // Rows 2j (real parts) and 2j+1 (imaginary parts) of the interleaved operand
 // whose row pair j is column j of X (K x J, ld): segment s holds slice s at
 // column s seg + k (zero for K <= k < seg); two K positions per thread.
+template <int NSL>
 __global__ void k_x3_slice_cols(const double2* __restrict__ X, int64_t ld, int K, int seg,
                                 __nv_bfloat16* __restrict__ out, int64_t pitch) {
   const int j = blockIdx.y;
@@ -1137,15 +1141,15 @@ __global__ void k_x3_slice_cols(const double2* __restrict__ X, int64_t ld, int K
   const double2* x = X + (size_t)j * ld;
   const double2 v0 = k < K ? x[k] : make_double2(0.0, 0.0);
   const double2 v1 = k + 1 < K ? x[k + 1] : make_double2(0.0, 0.0);
-  __nv_bfloat16 r0[X3_S], i0[X3_S], r1[X3_S], i1[X3_S];
-  x3_split(v0.x, r0);
-  x3_split(v0.y, i0);
-  x3_split(v1.x, r1);
-  x3_split(v1.y, i1);
+  __nv_bfloat16 r0[NSL], i0[NSL], r1[NSL], i1[NSL];
+  x3_split<NSL>(v0.x, r0);
+  x3_split<NSL>(v0.y, i0);
+  x3_split<NSL>(v1.x, r1);
+  x3_split<NSL>(v1.y, i1);
   __nv_bfloat16* o0 = out + (size_t)(2 * j) * pitch + k;
   __nv_bfloat16* o1 = o0 + pitch;
 #pragma unroll
-  for (int t = 0; t < X3_S; ++t) {
+  for (int t = 0; t < NSL; ++t) {
     __nv_bfloat162 p, q;
     p.x = r0[t];
     p.y = r1[t];
@@ -1158,6 +1162,7 @@ __global__ void k_x3_slice_cols(const double2* __restrict__ X, int64_t ld, int K
 
 // A2[m][s seg + 2k + c] = slice s of (Re, Im) A[m][k] (A: M x K column-major,
 // zero for 2K <= 2k + c < seg); 32 x 32 tiles transposed through shared memory.
+template <int NSL>
 __global__ void k_x3_slice_rows(const double2* __restrict__ A, int64_t ld, int M, int K, int seg,
                                 __nv_bfloat16* __restrict__ out, int64_t pitch) {
   __shared__ double2 tile[32][33];
@@ -1173,12 +1178,12 @@ __global__ void k_x3_slice_rows(const double2* __restrict__ A, int64_t ld, int M
     const int m = m0 + mm, k = k0 + kk;
     if (m >= M || 2 * k >= seg) continue;
     const double2 v = tile[kk][mm];
-    __nv_bfloat16 ar[X3_S], ai[X3_S];
-    x3_split(v.x, ar);
-    x3_split(v.y, ai);
+    __nv_bfloat16 ar[NSL], ai[NSL];
+    x3_split<NSL>(v.x, ar);
+    x3_split<NSL>(v.y, ai);
     __nv_bfloat16* r = out + (size_t)m * pitch + 2 * k;
 #pragma unroll
-    for (int s = 0; s < X3_S; ++s) {
+    for (int s = 0; s < NSL; ++s) {
       __nv_bfloat162 p;
       p.x = ar[s];
       p.y = ai[s];
@@ -1190,19 +1195,20 @@ __global__ void k_x3_slice_rows(const double2* __restrict__ A, int64_t ld, int M
 // B operand of the non-conjugated product, rows 2n and 2n+1:
 //     B2[2n][2k] = Re, B2[2n][2k+1] = -Im, B2[2n+1][2k] = Im, B2[2n+1][2k+1] = Re
 // of B[k][n] (B: K x N column-major), each value as its three slices.
+template <int NSL>
 __global__ void k_x3_slice_b2(const double2* __restrict__ B, int64_t ld, int K, int seg,
                               __nv_bfloat16* __restrict__ out, int64_t pitch) {
   const int n = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (2 * k >= seg) return;
   const double2 v = k < K ? B[(size_t)n * ld + k] : make_double2(0.0, 0.0);
-  __nv_bfloat16 ar[X3_S], ai[X3_S];
-  x3_split(v.x, ar);
-  x3_split(v.y, ai);
+  __nv_bfloat16 ar[NSL], ai[NSL];
+  x3_split<NSL>(v.x, ar);
+  x3_split<NSL>(v.y, ai);
   __nv_bfloat16* r0 = out + (size_t)(2 * n) * pitch + 2 * k;
   __nv_bfloat16* r1 = r0 + pitch;
 #pragma unroll
-  for (int s = 0; s < X3_S; ++s) {
+  for (int s = 0; s < NSL; ++s) {
     __nv_bfloat162 p0, p1;
     p0.x = ar[s];
     p0.y = __hneg(ai[s]);
@@ -1398,19 +1404,19 @@ static void x3_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alph
   {
     __nv_bfloat16* wA = (__nv_bfloat16*)s.ws_oz.p;
     if (conjA)
-      k_x3_slice_cols<<<dim3((unsigned)((seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg,
+      k_x3_slice_cols<X3_S><<<dim3((unsigned)((seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg,
                                                                                 wA, pitch);
     else
-      k_x3_slice_rows<<<dim3((M + 31) / 32, (unsigned)((seg / 2 + 31) / 32)), 256, 0, st>>>(
+      k_x3_slice_rows<X3_S><<<dim3((M + 31) / 32, (unsigned)((seg / 2 + 31) / 32)), 256, 0, st>>>(
           A, lda, M, K, (int)seg, wA, pitch);
     PWH_LAUNCH_CHECK();
   }
   if (conjA) {
-    k_x3_slice_cols<<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+    k_x3_slice_cols<X3_S><<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
                                                                               pB, pitch);
     PWH_LAUNCH_CHECK();
   } else {
-    k_x3_slice_b2<<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+    k_x3_slice_b2<X3_S><<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
                                                                             pB, pitch);
     PWH_LAUNCH_CHECK();
   }
@@ -1474,6 +1480,132 @@ void x3_reserve(System& s, bool conjA, int M, int N, int K) {
   // the first segment is the largest
   const X3Geom g = x3_geom(conjA, M, N, x3_kseg(conjA, M, N, K));
   ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
+}
+
+// ---- 16-bit sliced complex GEMM (the reduced-precision phase's subspace
+// products): each operand value rounded to FP32 and cut to its two leading
+// BF16 slices [hi | lo] (about 16 significant bits, the accuracy of the
+// split-BF16 projector GEMMs of the reduced-precision H), the three products
+// hi.hi + hi.lo + lo.hi in one BF16 GEMM (the projector GEMM's operand
+// layout), FP32 accumulation in tensor memory over K ranges of at most
+// kX2Kmax real K (the tensor core's truncating accumulation stays below the
+// slices' own rounding there), FP32 reduction of the partials.
+constexpr int X2_S = 2, X2_TERMS = 3;
+constexpr int kX2Kmax = 8192;
+struct X2Geom {
+  int64_t Mr, Nr, seg, pitch, tiles;
+  int kb_seg, kps, nz;
+  size_t bytes_a, bytes_b, bytes_p;
+};
+static X2Geom x2_geom(bool conjA, int M, int N, int K) {
+  X2Geom g;
+  g.Mr = conjA ? 2 * (int64_t)M : M;
+  g.Nr = 2 * (int64_t)N;
+  const int64_t Kr = conjA ? K : 2 * (int64_t)K;
+  g.seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
+  g.kb_seg = (int)(g.seg / TC_BK);
+  g.pitch = X2_S * g.seg;
+  const int kb_total = X2_TERMS * g.kb_seg;
+  g.tiles = ((g.Mr + TC_BM - 1) / TC_BM) * ((g.Nr + TC_BN - 1) / TC_BN);
+  // about two waves of blocks, each K range at most kX2Kmax real K
+  const int nz_fill = (int)std::max<int64_t>(1, (2 * 152 + g.tiles - 1) / g.tiles);
+  const int nz_acc = (kb_total + kX2Kmax / TC_BK - 1) / (kX2Kmax / TC_BK);
+  int nz = std::max(1, std::min(kb_total, std::max(nz_fill, nz_acc)));
+  g.kps = (kb_total + nz - 1) / nz;
+  g.nz = (kb_total + g.kps - 1) / g.kps;
+  g.bytes_a = align256((size_t)g.Mr * g.pitch * 2);
+  g.bytes_b = align256((size_t)g.Nr * g.pitch * 2);
+  g.bytes_p = (size_t)g.nz * g.Mr * g.Nr * sizeof(float);
+  return g;
+}
+
+static void x2_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alpha,
+                        const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
+                        double2* C, int64_t ldc, cudaStream_t st) {
+  const X2Geom g = x2_geom(conjA, M, N, K);
+  const int64_t Mr = g.Mr, Nr = g.Nr, seg = g.seg, pitch = g.pitch;
+  ensure(s.ws_oz, g.bytes_a + g.bytes_b + g.bytes_p);
+  char* base = s.ws_oz.p;
+  __nv_bfloat16* pA = (__nv_bfloat16*)base;
+  __nv_bfloat16* pB = (__nv_bfloat16*)(base + g.bytes_a);
+  float* part = (float*)(base + g.bytes_a + g.bytes_b);
+  TimedScope ts(s, KF_GEMM_X3, st, 2.0 * X2_TERMS * (double)Mr * Nr * (double)seg,
+                16.0 * (double)M * K + 16.0 * (double)K * N + 4.0 * X2_S * ((double)Mr + Nr) * seg +
+                    8.0 * g.nz * (double)Mr * Nr + 16.0 * (double)M * N);
+  if (conjA) {
+    k_x3_slice_cols<X2_S><<<dim3((unsigned)((seg / 2 + 255) / 256), M), 256, 0, st>>>(A, lda, K, (int)seg,
+                                                                                    pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_x3_slice_cols<X2_S><<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+                                                                                    pB, pitch);
+  } else {
+    k_x3_slice_rows<X2_S><<<dim3((M + 31) / 32, (unsigned)((seg / 2 + 31) / 32)), 256, 0, st>>>(
+        A, lda, M, K, (int)seg, pA, pitch);
+    PWH_LAUNCH_CHECK();
+    k_x3_slice_b2<X2_S><<<dim3((unsigned)((seg / 2 + 255) / 256), N), 256, 0, st>>>(B, ldb, K, (int)seg,
+                                                                                  pB, pitch);
+  }
+  PWH_LAUNCH_CHECK();
+  CUtensorMap ma = make_map(pA, Mr, pitch, pitch, TC_BM);
+  CUtensorMap mb = make_map(pB, Nr, pitch, pitch, TC_BN);
+  TcArgs a{};
+  a.M = (int)Mr;
+  a.N = (int)Nr;
+  a.kb_seg = g.kb_seg;
+  a.terms = X2_TERMS;   // hi.hi + hi.lo + lo.hi over the [hi | lo] segments
+  a.kb_per_split = g.kps;
+  a.part = part;
+  a.err = device_error_word(s);
+  a.oz = 0;
+  dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), g.nz);
+  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  PWH_LAUNCH_CHECK();
+  X3Out o;
+  o.alpha = alpha;
+  o.beta = beta;
+  o.af = (float)alpha.x;
+  const bool ar = alpha.y == 0.0 && (double)o.af == alpha.x;
+  o.mode = ar && beta.x == 0.0 && beta.y == 0.0 ? 0 : ar && beta.x == 1.0 && beta.y == 0.0 ? 1 : 2;
+  const int64_t tot = (int64_t)M * N;
+  if (g.nz > 8 && N <= 65535) {
+    const dim3 rg((unsigned)((M + 31) / 32), (unsigned)N);
+    if (conjA)
+      k_x3_reduce_wide<true><<<rg, 256, 0, st>>>(part, g.nz, M, N, o, C, ldc);
+    else
+      k_x3_reduce_wide<false><<<rg, 256, 0, st>>>(part, g.nz, M, N, o, C, ldc);
+  } else if (conjA) {
+    k_x3_reduce<true><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, g.nz, M, N, o, C, ldc);
+  } else {
+    k_x3_reduce<false><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, g.nz, M, N, o, C, ldc);
+  }
+  PWH_LAUNCH_CHECK();
+}
+
+// K per segment so that the partials of one segment stay under kX3PartCap.
+static int x2_kseg(bool conjA, int M, int N, int K) {
+  const X2Geom g = x2_geom(conjA, M, N, K);
+  if (g.bytes_p <= kX3PartCap) return K;
+  const size_t plane = (size_t)g.Mr * g.Nr * sizeof(float);
+  const int64_t nzmax = std::max<int64_t>(1, (int64_t)(kX3PartCap / plane));
+  // real K a segment may take: nzmax ranges of kX2Kmax / 3 (three products)
+  const int64_t kr = std::max<int64_t>(TC_BK, nzmax * (kX2Kmax / X2_TERMS) / TC_BK * TC_BK);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(K, conjA ? kr : kr / 2));
+}
+
+void x2_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,
+             int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
+             cudaStream_t st) {
+  if (M <= 0 || N <= 0) return;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  const int kseg = x2_kseg(conjA, M, N, K);
+  for (int k0 = 0; k0 == 0 || k0 < K; k0 += kseg) {
+    const int kk = std::min(kseg, K - k0);
+    x2_gemm_seg(s, conjA, M, N, kk, alpha, A + (conjA ? (int64_t)k0 : (int64_t)k0 * lda), lda,
+                B + k0, ldb, k0 == 0 ? beta : make_double2(1, 0), C, ldc, st);
+  }
 }
 
 void x3_gemm(System& s, bool conjA, int M, int N, int K, double2 alpha, const double2* A,

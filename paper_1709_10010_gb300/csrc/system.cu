@@ -23,7 +23,16 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // this thread's launches
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void note_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
+long long launch_counter() { return t_launches; }
 
 const char* const kKernelFamilyName[KF_COUNT] = {
     "fft_z_inverse_fp64", "fft_plane_fp64", "fft_z_forward_fp64", "fft_z_inverse_fp32",

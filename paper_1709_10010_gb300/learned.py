@@ -164,8 +164,16 @@ def main():
     ap.add_argument("--rows", type=int, default=1_000_000)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--out", default=None, help="save the trained blob (.npy)")
+    ap.add_argument("--eval-only", default=None, metavar="BLOB",
+                    help="skip harvesting and training: evaluate this saved blob (.npy)")
     a = ap.parse_args()
     torch.cuda.set_device(0)
+    if a.eval_only:
+        blob = np.load(a.eval_only).astype(np.float32)
+        res = evaluate(blob, range(2000, 2000 + a.test), nb=a.nb)
+        print(json.dumps({"test_cells": a.test, "nb": a.nb, "blob": a.eval_only,
+                          "summary": summarize(res), "held_out": res}))
+        return
     t0 = time.time()
     parts, nrows = [], 0
     s = None

@@ -96,5 +96,5 @@ def test_density_edge_cases(torch):
     empty = torch.zeros((0, b.npw), dtype=torch.complex128, device="cuda")
     rho = s.density(empty, np.zeros(0))
     assert float(rho.abs().max()) == 0.0
-    with pytest.raises(pwh.PwhError):
-        pwh.lib().pwh_density(s._h, 2, None, b.npw, None, None)
+    # null band block or output: an argument error, nothing launched
+    assert pwh.lib().pwh_density(s._h, 2, None, b.npw, None, None) == 1
