@@ -232,6 +232,7 @@ struct System {
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)
   DevBuf<char> ws_grid;             // SCF steps: a real and a complex full-box grid
+  DevBuf<char> ws_tune;             // scratch of the tile autotuner
   DevBuf<char> ws_tc;               // packed BF16 operands of the tensor-core path
   DevBuf<char> ws_oz;               // sliced operands and partials of the FP64-equivalent GEMM
   int tc_nb_cap = 0, tc_P = -1;     // geometry the ws_tc zero padding was laid out for

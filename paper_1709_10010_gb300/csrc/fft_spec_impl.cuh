@@ -5,7 +5,9 @@
 // indices (no digit-reversed scatter, two shared-memory passes per
 // transform instead of one per radix stage).
 #pragma once
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "fft_device.cuh"
@@ -460,6 +462,80 @@ __global__ void __launch_bounds__(256) ks_zfwd(const cx<T>* __restrict__ W, int6
   }
 }
 
+// Rows per chunk of the plane pass, autotuned: the candidates are equal
+// chunkings of the N rows whose shared memory fits (one to six chunks); on the
+// first use per (N, precision, column count) with a batch of at least 8 bands,
+// each is timed with CUDA events (two launches, the second timed) on a scratch
+// copy of the batch's stick buffer, and the fastest is kept for the rest of
+// the process.  Before that, and while the stream is being captured, the size
+// heuristic decides: the fewest chunks that keep two blocks per SM, else one.
+template <typename T, int N> int plane_rows_heuristic(int ncols) {
+  int rows = N;
+  for (size_t cap : {(size_t)110 * 1024, (size_t)220 * 1024}) {
+    int r = N;
+    while (r > 1 && ks_plane_smem<T, N>(ncols, r) > cap) --r;
+    const int chunks = (N + r - 1) / r;
+    rows = (N + chunks - 1) / chunks;
+    if (ks_plane_smem<T, N>(ncols, rows) <= cap && (rows >= 32 || rows == N)) break;
+  }
+  if (ks_plane_smem<T, N>(ncols, rows) > 227 * 1024)
+    throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
+  return rows;
+}
+
+template <typename T, int N> int plane_rows(System& s, const PassArgs& a) {
+  static std::mutex mu;
+  static std::map<int, int> chosen;  // ncols -> rows
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = chosen.find(s.ncols);
+  if (it != chosen.end()) return it->second;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PWH_CUDA(cudaStreamIsCapturing(a.st, &cap));
+  const int heur = plane_rows_heuristic<T, N>(s.ncols);
+  // a capture cannot time; a batch of a few bands would time launch overhead
+  if (cap != cudaStreamCaptureStatusNone || a.bb < 8) return heur;
+  std::vector<int> cands;
+  for (int c = 1; c <= 6; ++c) {
+    const int r = (N + c - 1) / c;
+    if (ks_plane_smem<T, N>(s.ncols, r) <= 227 * 1024 &&
+        (cands.empty() || cands.back() != r))
+      cands.push_back(r);
+  }
+  int best = heur;
+  if (cands.size() > 1) {
+    const size_t bytes = (size_t)a.bb * a.wband * sizeof(cx<T>);
+    ensure(s.ws_tune, bytes);
+    cx<T>* Wt = (cx<T>*)s.ws_tune.p;
+    PWH_CUDA(cudaMemcpyAsync(Wt, a.W, bytes, cudaMemcpyDeviceToDevice, a.st));
+    cudaEvent_t e0, e1;
+    PWH_CUDA(cudaEventCreate(&e0));
+    PWH_CUDA(cudaEventCreate(&e1));
+    float best_ms = 0.f;
+    for (int r : cands) {
+      const size_t smem = ks_plane_smem<T, N>(s.ncols, r);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1) PWH_CUDA(cudaEventRecord(e0, a.st));
+        ks_plane<T, N, 512><<<dim3(N, a.bb), 512, smem, a.st>>>(
+            Wt, a.wband, s.nsticks, s.ncols, s.d_stick_at, s.d_xcol, (const T*)a.V,
+            s.plan[0].tw_off, (const cx<T>*)a.tw, r);
+        PWH_LAUNCH_CHECK();
+      }
+      PWH_CUDA(cudaEventRecord(e1, a.st));
+      PWH_CUDA(cudaEventSynchronize(e1));
+      PWH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = r;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  chosen[s.ncols] = best;
+  return best;
+}
+
 template <typename T, int N> void spec_launch(SpecPass pass, System& s, const PassArgs& a) {
   static std::once_flag once;
   std::call_once(once, [] {
@@ -477,19 +553,8 @@ template <typename T, int N> void spec_launch(SpecPass pass, System& s, const Pa
                                                  s.d_perm, W, a.wband, a.spb);
       break;
     case SPEC_PLANE: {
-      // rows per chunk: equal chunks, as many rows as keep two blocks per SM
-      // (110 KB each) if that leaves at least 32 rows, else one block per SM
-      int rows = N;
-      for (size_t cap : {(size_t)110 * 1024, (size_t)220 * 1024}) {
-        int r = N;
-        while (r > 1 && ks_plane_smem<T, N>(s.ncols, r) > cap) --r;
-        const int chunks = (N + r - 1) / r;
-        rows = (N + chunks - 1) / chunks;
-        if (ks_plane_smem<T, N>(s.ncols, rows) <= cap && (rows >= 32 || rows == N)) break;
-      }
-      const size_t smem = ks_plane_smem<T, N>(s.ncols, rows);
-      if (smem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
-      ks_plane<T, N, 512><<<dim3(N, a.bb), 512, smem, a.st>>>(
+      const int rows = plane_rows<T, N>(s, a);
+      ks_plane<T, N, 512><<<dim3(N, a.bb), 512, ks_plane_smem<T, N>(s.ncols, rows), a.st>>>(
           W, a.wband, s.nsticks, s.ncols, s.d_stick_at, s.d_xcol, (const T*)a.V, s.plan[0].tw_off,
           tw, rows);
       break;
