@@ -31,6 +31,12 @@
 
 namespace pwh {
 
+// Precision code of the 16-bit subspace products (see sgemm), and the largest
+// requested residual above which the reduced phase uses them: the 16-bit
+// products bound that phase's residuals at a few 1e-4.
+constexpr int kR16 = 16;
+constexpr double kR16Resid = 5e-3;
+
 struct DavWs {
   DevBuf<char> vec;    // V, HV (npw x mmax each), X, HX, R, Tw (npw x nb each)
   DevBuf<char> cg;     // Jacobi-Davidson PCG: r, z, p, q (npw x nb each), scalars
@@ -329,8 +335,8 @@ static void project_out(System& s, const double2* X, int nb, double2* v, int k, 
                         cudaStream_t st) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
   const int64_t npw = s.npw;
-  sgemm(s, PWH_MIXED, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
-  sgemm(s, PWH_MIXED, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
+  sgemm(s, kR16, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
+  sgemm(s, kR16, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
 }
 
 // Approximate solution t (npw x k) of (I-XX^H)(H-theta_j)(I-XX^H) t_j = -r_j
@@ -514,17 +520,21 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
   return w.h_idx[4096];
 }
 
-// Subspace GEMMs: FP64 in the FP64 phase; in the reduced-precision phase the
-// 16-bit sliced tensor-core product for large products (the accuracy of that
-// phase's operator, whose projector GEMMs are split BF16) and FP32 arithmetic
-// on FP64 storage for narrow ones.
+// Subspace GEMMs by precision code: PWH_FP64 (the FP64 phase), kR16 (the
+// 16-bit sliced tensor-core product: the reduced phase while its residuals are
+// far above that product's accuracy, and the projections of the
+// Jacobi-Davidson inner solves) or any other value (FP32-equivalent: the
+// reduced phase close to its hand-over target).  Narrow products take the
+// FP32 pipe in both reduced codes.
 static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
                   const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
                   double2* C, int64_t ldc, cudaStream_t st) {
   if (prec == PWH_FP64)
     cgemm<double>(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
-  else
+  else if (prec == kR16)
     cgemm_r16(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  else
+    cgemm_f32(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
 }
 
 static double now_s() {
@@ -630,9 +640,14 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     m = nb;
     hs_valid = 0;
   };
+  std::vector<double> red_hist;  // requested-band residuals of the reduced phase
   for (int it = 1;; ++it) {
+    // subspace-product precision of this iteration
+    const int gp = phase_prec == PWH_FP64
+                       ? PWH_FP64
+                       : ((it == 1 || maxr_target > kR16Resid) ? kR16 : phase_prec);
     // Rayleigh-Ritz on span(V): new columns of Hs, then its lowest nb eigenpairs
-    sgemm(s, phase_prec, true, m, m - hs_valid, (int)npw, one, L.V, npw,
+    sgemm(s, gp, true, m, m - hs_valid, (int)npw, one, L.V, npw,
           L.HV + (size_t)hs_valid * npw, npw, zero, L.Hs + (size_t)hs_valid * mmax, mmax, st);
     hermitize(L.Hs, mmax, hs_valid, m, st);
     // the leading hs_valid x hs_valid block was diagonalised last time: start there
@@ -646,8 +661,8 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // (relative to the largest diagonal entry), between 4e-7 and 1e-4
     const double tol32 = polish || it == 1 ? 4e-7 : std::min(1e-4, std::max(4e-7, 1e-3 * maxr_target));
     jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32);
-    sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
-    sgemm(s, phase_prec, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
+    sgemm(s, gp, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
+    sgemm(s, gp, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
     PWH_LAUNCH_CHECK();
     PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -708,7 +723,20 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     }
     bool buffers_done = true;
     for (int b = nbt; b < nb; ++b) buffers_done = buffers_done && !above(b);
-    if (phase_prec != PWH_FP64 && maxr_t <= o.switch_tol && buffers_done) {
+    // a reduced phase that stopped improving (its arithmetic's floor above
+    // switch_tol) hands over as well: the best of its last four requested-band
+    // residuals not 0.8 of the best of the four before
+    bool stalled = false;
+    if (phase_prec != PWH_FP64) {
+      red_hist.push_back(maxr_t);
+      const size_t h = red_hist.size();
+      if (h >= 8) {
+        const double a = *std::min_element(red_hist.end() - 4, red_hist.end());
+        const double b = *std::min_element(red_hist.end() - 8, red_hist.end() - 4);
+        stalled = a > 0.8 * b;
+      }
+    }
+    if (phase_prec != PWH_FP64 && ((maxr_t <= o.switch_tol && buffers_done) || stalled)) {
       // hand over to FP64: restart from the Ritz vectors with the FP64 operator
       const double t = now_s();
       S.t_mixed_s = t - t_phase;
@@ -767,13 +795,13 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // second, in the phase's precision, removes what it left.  Both
     // Cholesky-QR passes stay in the phase's precision: a reduced-precision
     // T Tr would bring back components along V that nothing removes.
-    const int first = jd ? PWH_MIXED : phase_prec;
+    const int first = jd ? kR16 : gp;
     for (int pass = 0; pass < 2; ++pass) {
-      const int pp = pass == 0 ? first : phase_prec;
+      const int pp = pass == 0 ? first : gp;
       sgemm(s, pp, true, m, k, (int)npw, one, L.V, npw, T, npw, zero, L.Wc, m, st);
       sgemm(s, pp, false, (int)npw, k, m, mone, L.V, npw, L.Wc, m, one, T, npw, st);
     }
-    const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st, phase_prec);
+    const int kn = cholqr2(s, w, L, T, k, L.t0, 1e-10, st, gp);
     if (kn == 0) {
       restart_from_ritz(false);
       continue;
