@@ -15,6 +15,7 @@
 // returns.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -766,7 +767,7 @@ static size_t pj_buf_bytes(int n) {
 static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
                          int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
                          cudaStream_t st) {
-  if (n <= 512 || n > 4096 || max_sweeps > 64) return false;
+  if (n < 64 || n > 4096 || max_sweeps > 64) return false;
   const int np = n + (n & 1), P = np / 2, T = (P + kPjTile - 1) / kPjTile;
   ensure(w.pj, pj_buf_bytes(n));
   ensure(w.jlog, pj_log_bytes(n, max_sweeps));
@@ -814,6 +815,52 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   k_jacobi_qlog_rows<<<(n + qrows - 1) / qrows, 1024, qsm, st>>>(a.log, info, n, P, qrows, Q, ldq);
   PWH_LAUNCH_CHECK();
   return true;
+}
+
+// FP32 stage, autotuned between the two kernels that fit: above n = 512 only
+// the position-order kernel; for 64 <= n <= 512 the cluster kernel or the
+// position-order one, whichever was faster on the first matrix of the size
+// class (n rounded up to 32): both are run on it (same read-only input, same
+// outputs; the second run's result is kept), timed with CUDA events.  While
+// the stream is being captured the cluster kernel runs without timing.
+static bool jacobi32_tuned(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
+                           int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
+                           cudaStream_t st) {
+  if (n > 512) return jacobi32_pos(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  if (n < 64) return false;
+  static std::mutex mu;
+  static std::map<int, int> choice;  // size class -> 0 cluster, 1 position order
+  const int cls = (n + 31) / 32;
+  int c = -1;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = choice.find(cls);
+    if (it != choice.end()) c = it->second;
+  }
+  if (c == 0) return jacobi32_cluster(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  if (c == 1) return jacobi32_pos(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PWH_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone)
+    return jacobi32_cluster(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  cudaEvent_t e[3];
+  for (auto& x : e) PWH_CUDA(cudaEventCreate(&x));
+  PWH_CUDA(cudaEventRecord(e[0], st));
+  const bool ok0 = jacobi32_cluster(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  PWH_CUDA(cudaEventRecord(e[1], st));
+  const bool ok1 = jacobi32_pos(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  PWH_CUDA(cudaEventRecord(e[2], st));
+  PWH_CUDA(cudaEventSynchronize(e[2]));
+  float t0 = 0.f, t1 = 0.f;
+  PWH_CUDA(cudaEventElapsedTime(&t0, e[0], e[1]));
+  PWH_CUDA(cudaEventElapsedTime(&t1, e[1], e[2]));
+  for (auto& x : e) cudaEventDestroy(x);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    choice[cls] = (ok1 && (!ok0 || t1 < t0)) ? 1 : 0;
+  }
+  if (ok1) return true;  // its result is the one in Q / diag / info
+  return ok0 && jacobi32_cluster(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
 }
 
 template <typename T>
@@ -944,8 +991,7 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
     // FP32 sweeps down to ~5 times FP32 rounding, so that one FP64 sweep (quadratic
     // convergence) usually finishes.  The whole matrix in one cluster's shared
     // memory when it fits, else through global memory.
-    if (!jacobi32_cluster(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st) &&
-        !jacobi32_pos(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
+    if (!jacobi32_tuned(s, w, start, ld_start, n, tol32, 30, Q0, n, dg, ob32, st)) {
       k_c64_to_c32<<<gq, 256, 0, st>>>(start, ld_start, n, a0);
       PWH_LAUNCH_CHECK();
       k_warm_basis<<<gq, 256, 0, st>>>(nullptr, 0, 0, n, Q0);  // identity
@@ -1036,7 +1082,7 @@ void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
   ensure(w.ns, (size_t)4 * kmax * kmax * sizeof(double2) + 64);
   if (nmax >= 64 && nmax <= 512) ensure(w.jlog, jacobi32_log_bytes(nmax, 30));
-  if (nmax > 512 && nmax <= 4096) {
+  if (nmax >= 64 && nmax <= 4096) {
     ensure(w.jlog, pj_log_bytes(nmax, 30));
     ensure(w.pj, pj_buf_bytes(nmax));
   }
