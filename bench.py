@@ -189,6 +189,20 @@ def hpsi_only(torch, s, psi0, reps=HPSI_REPS):
         med = statistics.median(ts)
         res[prec] = {"band_applies_s": psi0.shape[0] / med, "median_ms": 1e3 * med,
                      "repeats": reps}
+    # the same number of real bands at k = 0 on the half sphere (two real bands
+    # per complex FFT; the imaginary part stored at G = 0 is ignored)
+    nh = len(s.gamma_half())
+    psig = psi0[:, :nh].contiguous()
+    outg = torch.empty_like(psig)
+    for prec in ("fp64", "mixed"):
+        s.set_precision(prec)
+        for _ in range(3):
+            s.apply_h_gamma(psig, outg)
+        ts = [timed(torch, stream, lambda: s.apply_h_gamma(psig, outg))[0] for _ in range(reps)]
+        med = statistics.median(ts)
+        res["gamma_real_" + prec] = {"band_applies_s": psig.shape[0] / med, "median_ms": 1e3 * med,
+                                     "repeats": reps, "npw_half": nh}
+    del psig, outg
     s.set_precision("mixed")
     return res
 

@@ -156,6 +156,35 @@ pwh_status pwh_apply_local_noalloc(pwh_system* sys, int32_t nb, const void* psi,
  * int_to_pub[npw]: internal plane wave i is public plane wave int_to_pub[i]. */
 pwh_status pwh_get_internal_order(const pwh_system* sys, int32_t* int_to_pub);
 
+/* ----------------------------------------------------- real bands at k = 0 --
+ * At the Gamma point a real band psi(r) has c(-G) = conj c(G), so half of the
+ * sphere holds it (the Gamma-only real-wavefunction codes named in Sec.
+ * "Advanced implementation of exact (Fock) exchange" and Sec. "Many-body
+ * perturbation theory").  The half sphere: G = 0 and every plane wave whose
+ * first nonzero Miller index (m1, then m2, then m3) is positive, in public
+ * order; npw_half = (npw + 1) / 2.  The coefficient at G = 0 of a real band is
+ * real; the imaginary part a caller stores there is ignored.
+ *
+ * *npw_half receives the size of the half sphere and, when pub_index is not
+ * NULL, the host array pub_index[npw_half] the public index of each of its
+ * plane waves.  The first call builds the map (host work and a small device
+ * upload).  Errors: PWH_ERR_ARG when k != 0. */
+pwh_status pwh_get_gamma_half(pwh_system* sys, int64_t* npw_half, int32_t* pub_index);
+
+/* hpsi = H psi for nb real bands on the half sphere, in the system's
+ * precision (pwh_set_precision).  Two real bands share one complex band
+ * Psi = psi_a + i psi_b of the full sphere, so the FFTs and projector GEMMs run
+ * on ceil(nb/2) bands; H psi_a and H psi_b are the conjugate-symmetric and
+ * antisymmetric parts of H Psi.  psi, hpsi: DEVICE complex128, column-major,
+ * ld_psi, ld_hpsi >= npw_half, not overlapping.  Asynchronous on the system's
+ * stream, except that the first call after pwh_set_projectors checks (on the
+ * device, then synchronizes) that the projectors keep real functions real:
+ * beta_p(-G) = conj beta_p(G) to 1e-10 of max|beta| and a real D.  Errors:
+ * PWH_ERR_ARG (k != 0, projectors that fail that check, ld too small),
+ * PWH_ERR_STATE (no potential), PWH_ERR_OOM, PWH_ERR_CUDA.  nb = 0 is a no-op. */
+pwh_status pwh_apply_h_gamma(pwh_system* sys, int32_t nb, const void* psi, int64_t ld_psi,
+                             void* hpsi, int64_t ld_hpsi);
+
 /* ------------------------------------------------------------ eigensolver --
  * Block Davidson for the lowest nb eigenpairs of H: the iterative
  * diagonalisation with subspace diagonalisation of O_ij = <psi_i|O|psi_j>

@@ -82,6 +82,8 @@ SIGNATURES = {
     "pwh_apply_h": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_apply_h_host": (_c_i32, [_c_p, _c_i32, _c_p, _c_p]),
     "pwh_apply_h_internal": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_get_gamma_half": (_c_i32, [_c_p, ctypes.POINTER(_c_i64), _c_p]),
+    "pwh_apply_h_gamma": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_sync": (_c_i32, [_c_p]),
     "pwh_batch_davidson_solve": (_c_i32, [_c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_i32]),
     "pwh_subspace_eigh": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_i32, _c_p, _c_p, _c_p, _c_i64,
@@ -331,6 +333,27 @@ class System:
         p, ldp = _band_ptr(psi, self.npw)
         h, ldh = _band_ptr(hpsi, self.npw)
         _check(lib().pwh_apply_h_internal(self._h, int(psi.shape[0]), p, ldp, h, ldh))
+        return hpsi
+
+    def gamma_half(self) -> np.ndarray:
+        """Public indices of the half sphere that stores real bands at k = 0."""
+        n = _c_i64()
+        _check(lib().pwh_get_gamma_half(self._h, ctypes.byref(n), None))
+        idx = np.empty(n.value, dtype=np.int32)
+        _check(lib().pwh_get_gamma_half(self._h, ctypes.byref(n), idx.ctypes.data_as(_c_p)))
+        return idx
+
+    def apply_h_gamma(self, psi, hpsi=None):
+        """hpsi = H psi for real bands on the half sphere; psi (nb, npw_half)
+        complex128 CUDA tensor."""
+        torch = _torch()
+        n = _c_i64()
+        _check(lib().pwh_get_gamma_half(self._h, ctypes.byref(n), None))
+        if hpsi is None:
+            hpsi = torch.empty_like(psi, memory_format=torch.contiguous_format)
+        p, ldp = _band_ptr(psi, n.value)
+        h, ldh = _band_ptr(hpsi, n.value)
+        _check(lib().pwh_apply_h_gamma(self._h, int(psi.shape[0]), p, ldp, h, ldh))
         return hpsi
 
     def apply_local_noalloc(self, psi, hpsi):

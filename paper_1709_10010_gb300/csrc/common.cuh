@@ -228,6 +228,14 @@ struct System {
   void* d_beta_bf16 = nullptr;      // BF16 planar copies for the tensor-core GEMMs
   void* d_beta_bf16_t = nullptr;
 
+  // real bands at k = 0 (gamma.cu): the half sphere in public order, the
+  // internal positions of G and -G for each of its plane waves, and whether
+  // the projectors keep real functions real (-1: not checked since they were set)
+  std::vector<int32_t> gam_pub;
+  int32_t* d_gam_pos = nullptr;
+  int32_t* d_gam_neg = nullptr;
+  int gam_proj_ok = -1;
+
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)

@@ -80,6 +80,39 @@ def test_apply_h_large_sampled(large, mode):
         assert np.abs(out[bands, g] - ref).max() <= tol * scale
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_apply_h_gamma_large_sampled(large, mode):
+    """Real bands on the half sphere, all 512 at once (256 complex FFTs), on
+    sampled rows from the plain definition applied to the expanded bands."""
+    from oracle import gamma as og
+    torch, cell, b, v, beta, D = large
+    s = make_system(cell, v, beta, D, mode)
+    nb = syn.CONFIGS["large"]["nb"]
+    half, _ = og.half_sphere(b.miller)
+    nh = len(half)
+    psi = syn.initial_bands(4, nh, nb)
+    g0 = int(np.nonzero(np.all(b.miller[half] == 0, axis=1))[0][0])
+    psi[:, g0] = psi[:, g0].real
+    out = s.apply_h_gamma(torch.from_numpy(psi).cuda()).cpu().numpy()
+    s.sync()
+    s.close()
+    tol = FP64_TOL if mode == "fp64" else MIXED_TOL
+    rng = np.random.default_rng(6)
+    rows = np.concatenate([[0, g0, nh - 1], rng.choice(nh, 20, replace=False)])
+    bands = np.concatenate([[0, 1, nb - 1], rng.choice(nb, 3, replace=False)])
+    full = og.expand(b.miller, psi[bands])
+    vt = oh.v_tilde(v)
+    p = oh.becp(beta, full)
+    N = b.fft[0]
+    scale = np.abs(out[bands]).max()
+    for h in rows:
+        g = half[h]
+        d = b.miller[g][None, :] - b.miller
+        vrow = vt[d[:, 0] % N, d[:, 1] % N, d[:, 2] % N]
+        ref = b.kinetic[g] * full[:, g] + full @ vrow + (beta[:, g] * D) @ p
+        assert np.abs(out[bands, h] - ref).max() <= tol * scale
+
+
 @pytest.fixture(scope="module")
 def fp64_solve(large):
     torch, cell, b, v, beta, D = large
