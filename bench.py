@@ -68,6 +68,8 @@ def parse():
     p.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison solve")
     p.add_argument("--skip-batched", action="store_true", help="omit the batched cells x k-points solve")
     p.add_argument("--skip-medium", action="store_true", help="omit the medium-cell secondary line")
+    p.add_argument("--skip-gamma", action="store_true",
+                   help="omit the real-band (k = 0 half-sphere) solve of the same workload")
     p.add_argument("--workload", default=WORKLOAD, choices=["large", "medium", "small"],
                    help="system of the timed solves (default: the large cell)")
     p.add_argument("--mult", type=int, default=MULT, help="m_max = mult x nb")
@@ -207,6 +209,30 @@ def hpsi_only(torch, s, psi0, reps=HPSI_REPS):
     return res
 
 
+def gamma_solve(torch, s, nb, steps, seed=0):
+    """The same eigenproblem as real bands at k = 0: nb half-sphere bands from
+    the seeded generator, mixed + Jacobi-Davidson to 1e-8 (pwh_davidson_solve_gamma),
+    one warm-up solve, then the median of `steps` CUDA-event-timed solves."""
+    from paper_1709_10010_gb300 import synthetic as syn
+    nh = len(s.gamma_half())
+    psi0 = torch.from_numpy(syn.initial_bands(seed, nh, nb)).cuda()
+    psi = torch.empty_like(psi0)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        psi.copy_(psi0)
+        return s.davidson_gamma(psi, tol=TOL, mult=MULT, mixed=True, switch_tol=SWITCH_TOL,
+                                jd_inner=JD_INNER)
+    solve()
+    runs = [timed(torch, stream, solve) for _ in range(max(1, steps))]
+    t = statistics.median(r[0] for r in runs)
+    eig, st, status = runs[-1][1]
+    assert status == 0, status
+    return {"time_to_1e-8_s": t, "band_applies_s": st["n_apply"] / t, "iters": st["iters"],
+            "n_apply": st["n_apply"], "n_apply_fp64": st["n_apply_fp64"], "npw_half": nh,
+            "steps": len(runs), "eig": eig}
+
+
 def run_ours(a):
     import torch
     import paper_1709_10010_gb300 as pwh
@@ -314,6 +340,12 @@ def run_ours(a):
     # ---- H|psi> alone on the 512 resident bands, FP64 and mixed
     hp = hpsi_only(torch, s, psi0)
 
+    # ---- the same eigenproblem as real bands at k = 0 (half sphere)
+    gam = None
+    if not a.skip_gamma:
+        gam = gamma_solve(torch, s, nb, a.steps)
+        gam["max_abs_dlambda_vs_complex_ha"] = float(np.abs(gam.pop("eig") - eig).max())
+
     # ---- end to end through the C ABI with host buffers: pwh_davidson_solve_host
     # copies the pinned starting bands in and the eigenvectors out inside the call
     pin = torch.from_numpy(psi0_h).pin_memory()
@@ -366,6 +398,7 @@ def run_ours(a):
                                                    "max_resid")},
                      "fp64": fp64},
         "hpsi_only": hp,
+        "gamma_real_bands": gam,
         "medium": medium,
         "batched": batched,
         "kernels": {k: {"launches": d["launches"], "ms": round(d["ms"], 3),

@@ -269,6 +269,22 @@ pwh_status pwh_get_davidson_trace(const pwh_system* sys, int32_t cap,
 pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_host,
                                    double* eig, pwh_davidson_stats* stats);
 
+/* pwh_davidson_solve for real bands at k = 0 (the real-wavefunction form of
+ * the Gamma-only codes, Sec. "Advanced implementation of exact (Fock)
+ * exchange"): psi_io holds nb real bands on the half sphere
+ * (pwh_get_gamma_half: npw_half rows, public order, ld_psi >= npw_half,
+ * DEVICE complex128), starting bands in, eigenvectors out (c(0) real).  Every
+ * step of the complex solver runs on the half sphere: inner products are the
+ * real ones, 2 Re of the complex products over the half sphere with c(0)
+ * counted once (the solver stores c(0) / sqrt 2 internally); H is applied two
+ * bands per complex band (pwh_apply_h_gamma).  The eigenvalues are those of
+ * the complex solver at k = 0.  Same options, statistics, synchronous
+ * behaviour and status codes as pwh_davidson_solve, plus the errors of
+ * pwh_apply_h_gamma (k != 0, projectors that do not keep real functions
+ * real). */
+pwh_status pwh_davidson_solve_gamma(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
+                                    int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
+
 /* ------------------------------------------------------------- SCF steps --
  * The steps either side of H|psi> in a self-consistent Kohn-Sham calculation
  * (Sec. "Introduction"): the density of the occupied bands, then the new local

@@ -102,6 +102,8 @@ SIGNATURES = {
                                     ctypes.POINTER(DavidsonStats)]),
     "pwh_davidson_solve_host": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_p,
                                          ctypes.POINTER(DavidsonStats)]),
+    "pwh_davidson_solve_gamma": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
+                                          ctypes.POINTER(DavidsonStats)]),
     "pwh_get_davidson_trace": (_c_i32, [_c_p, _c_i32, _c_p, ctypes.POINTER(_c_i32)]),
     "pwh_density": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_p]),
     "pwh_hartree_xc": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
@@ -477,6 +479,25 @@ class System:
         eig = np.zeros(nb, dtype=np.float64)
         status = lib().pwh_davidson_solve(self._h, ctypes.byref(o), p, ld,
                                           eig.ctypes.data_as(_c_p), ctypes.byref(st))
+        if check and status not in (0,):
+            _check(status)
+        return eig, st.as_dict(), status
+
+    def davidson_gamma(self, psi, tol=1e-8, max_iter=200, mult=3, precond="tpa", mixed=False,
+                       switch_tol=1e-5, jd_inner=0, check=True):
+        """davidson() for real bands at k = 0: psi (nb, npw_half) CUDA complex128
+        on the half sphere (gamma_half()), starting bands in, eigenvectors out."""
+        n = _c_i64()
+        _check(lib().pwh_get_gamma_half(self._h, ctypes.byref(n), None))
+        p, ld = _band_ptr(psi, n.value)
+        nb = int(psi.shape[0])
+        o = DavidsonOpts(nb=nb, max_iter=int(max_iter), max_subspace_mult=int(mult),
+                         precond=PRECOND[precond], mixed=int(bool(mixed)), jd_inner=int(jd_inner),
+                         tol=float(tol), switch_tol=float(max(switch_tol, tol)))
+        st = DavidsonStats()
+        eig = np.zeros(nb, dtype=np.float64)
+        status = lib().pwh_davidson_solve_gamma(self._h, ctypes.byref(o), p, ld,
+                                                eig.ctypes.data_as(_c_p), ctypes.byref(st))
         if check and status not in (0,):
             _check(status)
         return eig, st.as_dict(), status

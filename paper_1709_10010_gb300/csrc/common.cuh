@@ -234,6 +234,9 @@ struct System {
   std::vector<int32_t> gam_pub;
   int32_t* d_gam_pos = nullptr;
   int32_t* d_gam_neg = nullptr;
+  int32_t* d_gam_shell = nullptr;   // shell of each half-sphere plane wave
+  double* d_gam_kin = nullptr;      // its kinetic energy
+  int64_t gam_g0 = -1;              // position of G = 0 in the half sphere
   int gam_proj_ok = -1;
 
   // workspaces (grown on demand)
@@ -333,6 +336,15 @@ void density_accumulate(System& s, int nb, const double2* psi_int, const double*
 // In-place unscaled 3D FFT of the full box (complex FP64, C order i3 fastest):
 // forward exp(-i G.r), inverse exp(+i G.r).
 void box_fft(System& s, double2* box, bool inverse);
+// Real bands at k = 0 (gamma.cu): build the half-sphere tables and check the
+// projectors (throws PWH_ERR_ARG where real bands do not apply); H on nb
+// half-sphere bands, two per complex band of the full sphere.  scaled0: the
+// bands store c(0) / sqrt 2 (the solver's storage, in which the real inner
+// product is 2 Re of the complex one over the half sphere).
+void gamma_prepare(System& s);
+void gamma_apply(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
+                 int precision, bool scaled0);
+
 void mlp_factors(System& s, const int* idx, int k, const double* theta, const double* rn,
                  const double* eref, float* out, cudaStream_t st);
 

@@ -43,6 +43,15 @@ struct DavWs {
   DevBuf<char> mlp;    // learned-preconditioner factors (k x nshell)
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
   DenseWs dense;
+  // plane-wave space of the current solve: the full sphere in the internal
+  // order, or (real bands at k = 0) the half sphere in public order with c(0)
+  // stored as c(0) / sqrt 2, so that the real inner product of two bands is
+  // 2 Re of their complex one over the half sphere (m2 = 2)
+  int64_t n = 0;
+  const double* kin = nullptr;
+  const int32_t* shell = nullptr;
+  bool gamma = false;
+  double m2 = 1.0;
   std::vector<pwh_davidson_trace_entry> trace;  // per Rayleigh-Ritz step of the last solve
   double* h_rn = nullptr;  // pinned host mirrors
   int* h_idx = nullptr;
@@ -62,14 +71,15 @@ void free_davidson_ws(DavWs* w) { delete w; }
 // Starting vectors of the buffer bands: pseudo-random coefficients (two
 // splitmix64 draws per entry, Steele, Lea and Flood 2014, uniform in [-1, 1)
 // for the real and imaginary part) damped by 1/(1 + T_G), so that they start
-// mostly on low kinetic energy.  V: npw x nbuf, column-major, internal order.
+// mostly on low kinetic energy.  V: npw x nbuf, column-major, internal order;
+// the entry g0 (G = 0 of real bands; -1 for none) is real.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
   return z ^ (z >> 31);
 }
 __global__ void k_buffer_start(double2* __restrict__ V, int64_t npw, int nbuf,
-                               const double* __restrict__ kin, uint64_t seed) {
+                               const double* __restrict__ kin, uint64_t seed, int64_t g0) {
   const int64_t tot = npw * nbuf;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -78,16 +88,17 @@ __global__ void k_buffer_start(double2* __restrict__ V, int64_t npw, int nbuf,
     const uint64_t b = splitmix64(seed + 0x9e3779b97f4a7c15ull * (uint64_t)(2 * t + 2));
     const double d = 1.0 / (1.0 + kin[g]);
     V[t] = make_double2(((double)(a >> 11) * 0x1.0p-53 * 2.0 - 1.0) * d,
-                        ((double)(b >> 11) * 0x1.0p-53 * 2.0 - 1.0) * d);
+                        g == g0 ? 0.0 : ((double)(b >> 11) * 0x1.0p-53 * 2.0 - 1.0) * d);
   }
 }
 
-// R = HX - X theta per band; rn[b] = ||r_b||, eref[b] = <x|T|x>/<x|x> (the
-// band's kinetic energy, the reference energy of the TPA preconditioner).
+// R = HX - X theta per band; rn[b] = ||r_b|| (squared norm times m2, the
+// metric of the band storage), eref[b] = <x|T|x>/<x|x> (the band's kinetic
+// energy, the reference energy of the TPA preconditioner).
 __global__ void k_residual(const double2* __restrict__ X, const double2* __restrict__ HX,
                            int64_t ld, int64_t npw, const double* __restrict__ theta,
                            const double* __restrict__ kin, double2* __restrict__ R,
-                           double* __restrict__ rn, double* __restrict__ eref) {
+                           double* __restrict__ rn, double* __restrict__ eref, double m2) {
   const int b = blockIdx.x;
   const double th = theta[b];
   const double2* x = X + (size_t)b * ld;
@@ -122,18 +133,18 @@ __global__ void k_residual(const double2* __restrict__ X, const double2* __restr
       c += red[1][w];
       d += red[2][w];
     }
-    rn[b] = sqrt(a);
+    rn[b] = sqrt(m2 * a);
     eref[b] = (d > 0 && c > 0) ? c / d : 1.0;
   }
 }
 
 // T[:, j] = K(T_G / eref) (.) R[:, idx[j]] (K = 1 when tpa == 0); with the
-// learned correction, K *= exp(s[j, shell(G)]).  t0[j] = ||t_j||.
+// learned correction, K *= exp(s[j, shell(G)]).  t0[j] = ||t_j|| (metric m2).
 __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw,
                           const int* __restrict__ idx, const double* __restrict__ eref,
                           const double* __restrict__ kin, int tpa, double2* __restrict__ T,
                           int64_t ldt, double* __restrict__ t0, const float* __restrict__ sfac,
-                          const int32_t* __restrict__ shell, int nshell) {
+                          const int32_t* __restrict__ shell, int nshell, double m2) {
   const int j = blockIdx.x;
   const int src = idx[j];
   const double2* r = R + (size_t)src * ld;
@@ -159,7 +170,7 @@ __global__ void k_precond(const double2* __restrict__ R, int64_t ld, int64_t npw
   if (threadIdx.x == 0) {
     double a = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
-    t0[j] = sqrt(a);
+    t0[j] = sqrt(m2 * a);
   }
 }
 
@@ -176,6 +187,25 @@ __global__ void k_ritz_block(double2* __restrict__ Hs, int64_t ldh, double2* __r
 
 __global__ void k_sqrt(double* __restrict__ a, int n) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = sqrt(fmax(a[i], 0.0));
+}
+
+// C = 2 Re C (M x N, ld): an inner-product matrix of half-sphere bands.
+__global__ void k_real2(double2* __restrict__ C, int64_t ldc, int M, int N) {
+  const int64_t tot = (int64_t)M * N;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % M, j = t / M;
+    double2* c = C + j * ldc + i;
+    *c = make_double2(2.0 * c->x, 0.0);
+  }
+}
+
+// V[row] = f Re V[row] in each of nb columns (the G = 0 entry of real bands).
+__global__ void k_scale_row(double2* __restrict__ V, int64_t ld, int nb, int64_t row, double f) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    double2* v = V + (size_t)b * ld + row;
+    *v = make_double2(f * v->x, 0.0);
+  }
 }
 
 __global__ void k_copy_cols(const double2* __restrict__ src, int64_t lds, double2* __restrict__ dst,
@@ -240,11 +270,11 @@ __global__ void k_cg_precond(const double2* __restrict__ r, int64_t npw, const i
     z[(size_t)j * npw + i] = make_double2(k * v.x, k * v.y);
   }
 }
-// out[j] = Re <a_j, b_j>, one 1024-thread block per column, four element
+// out[j] = m2 Re <a_j, b_j>, one 1024-thread block per column, four element
 // pairs in flight a thread (fixed-order reduction)
 __global__ void __launch_bounds__(1024) k_col_dot(const double2* __restrict__ a,
                                                   const double2* __restrict__ b, int64_t npw,
-                                                  double* __restrict__ out) {
+                                                  double* __restrict__ out, double m2) {
   const int j = blockIdx.x;
   const double2* aj = a + (size_t)j * npw;
   const double2* bj = b + (size_t)j * npw;
@@ -272,7 +302,7 @@ __global__ void __launch_bounds__(1024) k_col_dot(const double2* __restrict__ a,
   if (threadIdx.x == 0) {
     double a2 = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a2 += red[w];
-    out[j] = a2;
+    out[j] = m2 * a2;
   }
 }
 // q -= theta[idx[j]] p
@@ -327,6 +357,14 @@ struct Layout {
   int *idx, *kk;
 };
 
+// H on k bands of the solve's space (see DavWs).
+static void space_apply(System& s, DavWs& w, int k, const double2* in, double2* out, int prec) {
+  if (w.gamma)
+    gamma_apply(s, k, in, w.n, out, w.n, prec, true);
+  else
+    apply_internal(s, k, in, w.n, out, w.n, prec);
+}
+
 // P v = v - X (X^H v) on k columns (FP32 arithmetic, FP64 storage); W: nb x k.
 static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 alpha,
                   const double2* A, int64_t lda, const double2* B, int64_t ldb, double2 beta,
@@ -334,7 +372,7 @@ static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 
 static void project_out(System& s, const double2* X, int nb, double2* v, int k, double2* W,
                         cudaStream_t st) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
-  const int64_t npw = s.npw;
+  const int64_t npw = s.dav->n;
   sgemm(s, kR16, true, nb, k, (int)npw, one, X, npw, v, npw, zero, W, nb, st);
   sgemm(s, kR16, false, (int)npw, k, nb, mone, X, npw, W, nb, one, v, npw, st);
 }
@@ -347,7 +385,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
                           const int* idx, int k, const double* theta, const double* eref,
                           int iters, int prec, double2* t, double2* Wc, int* n_apply,
                           cudaStream_t st, const float* sfac = nullptr) {
-  const int64_t npw = s.npw;
+  const int64_t npw = w.n;
   ensure(w.cg, (size_t)4 * npw * k * sizeof(double2) + 8 * (size_t)k * sizeof(double) + 256);
   double2* r = (double2*)w.cg.p;
   double2* z = r + (size_t)npw * k;
@@ -358,28 +396,28 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
   const dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (npw + 255) / 256)), k);
   k_cg_init<<<g2, 256, 0, st>>>(R, npw, npw, idx, r, t);
   PWH_LAUNCH_CHECK();
-  k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z, sfac, s.d_shell, s.nshell);
+  k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, w.kin, z, sfac, w.shell, s.nshell);
   PWH_LAUNCH_CHECK();
   project_out(s, X, nb, z, k, Wc, st);
   PWH_CUDA(cudaMemcpyAsync(p, z, (size_t)npw * k * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[0]);
+  k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[0], w.m2);
   PWH_LAUNCH_CHECK();
   // one PCG step; rho[c] holds r.z of the step, rho[c ^ 1] receives the next
   auto step = [&](int c, bool last) {
-    apply_internal(s, k, p, npw, q, npw, prec);
+    space_apply(s, w, k, p, q, prec);
     *n_apply += k;
     k_cg_shift<<<g2, 256, 0, st>>>(q, p, npw, idx, theta);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, q, k, Wc, st);
-    k_col_dot<<<k, 1024, 0, st>>>(p, q, npw, pq);
+    k_col_dot<<<k, 1024, 0, st>>>(p, q, npw, pq, w.m2);
     PWH_LAUNCH_CHECK();
     k_cg_step<<<g2, 256, 0, st>>>(t, r, p, q, npw, rho[c], pq);
     PWH_LAUNCH_CHECK();
     if (last) return;
-    k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, s.d_kin, z, sfac, s.d_shell, s.nshell);
+    k_cg_precond<<<g2, 256, 0, st>>>(r, npw, idx, eref, w.kin, z, sfac, w.shell, s.nshell);
     PWH_LAUNCH_CHECK();
     project_out(s, X, nb, z, k, Wc, st);
-    k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[c ^ 1]);
+    k_col_dot<<<k, 1024, 0, st>>>(r, z, npw, rho[c ^ 1], w.m2);
     PWH_LAUNCH_CHECK();
     k_cg_dir<<<g2, 256, 0, st>>>(p, z, npw, rho[c ^ 1], rho[c]);
     PWH_LAUNCH_CHECK();
@@ -439,7 +477,7 @@ static void jd_correction(System& s, DavWs& w, const double2* X, int nb, const d
 }
 
 static Layout carve(System& s, DavWs& w, int nb, int mmax) {
-  const int64_t npw = s.npw;
+  const int64_t npw = w.n;
   const size_t nvec = (size_t)npw * (2 * (size_t)mmax + 4 * (size_t)nb);
   ensure(w.vec, nvec * sizeof(double2));
   const size_t nc = 2 * (size_t)mmax * mmax + (size_t)mmax * nb + (size_t)mmax * nb + 2 * (size_t)nb * nb;
@@ -488,7 +526,7 @@ static int cholqr2(System& s, DavWs& w, Layout& L, double2* T, int k, const doub
                    double drop_rel, cudaStream_t st, int prec = PWH_FP64,
                    int prec_first = -1) {
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
-  const int64_t npw = s.npw;
+  const int64_t npw = w.n;
   const int p1 = prec_first < 0 ? prec : prec_first;  // first pass may be cheaper
   sgemm(s, p1, true, k, k, (int)npw, one, T, npw, T, npw, zero, L.S, k, st);
   // the first factor only has to make T Tr well conditioned (the second pass,
@@ -535,6 +573,14 @@ static void sgemm(System& s, int prec, bool conjA, int M, int N, int K, double2 
     cgemm_r16(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
   else
     cgemm_f32(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
+  // half-sphere bands: the inner products are 2 Re of the complex ones (every
+  // inner-product GEMM of the solver starts from C = 0)
+  if (conjA && s.dav && s.dav->gamma && M > 0 && N > 0) {
+    if (beta.x != 0.0 || beta.y != 0.0)
+      throw Error{PWH_ERR_STATE, "inner-product GEMM with beta != 0 on half-sphere bands"};
+    k_real2<<<grid1d((int64_t)M * N), 256, 0, st>>>(C, ldc, M, N);
+    PWH_LAUNCH_CHECK();
+  }
 }
 
 static double now_s() {
@@ -552,8 +598,15 @@ static void check_err(System& s) {
 }
 
 pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, int64_t ldpsi,
-                          double* eig, pwh_davidson_stats* stats) {
-  const int64_t npw = s.npw;
+                          double* eig, pwh_davidson_stats* stats, bool gamma) {
+  if (!s.dav) s.dav = new DavWs();
+  DavWs& w = *s.dav;
+  w.gamma = gamma;
+  w.n = gamma ? (int64_t)s.gam_pub.size() : s.npw;
+  w.kin = gamma ? s.d_gam_kin : s.d_kin;
+  w.shell = gamma ? s.d_gam_shell : s.d_shell;
+  w.m2 = gamma ? 2.0 : 1.0;
+  const int64_t npw = w.n;
   // Buffer bands: the solver iterates nbt + nbuf Ritz pairs and requires the
   // tolerance only of the lowest nbt (the bands asked for); the others are
   // converged to a looser threshold.  Without them, a requested band whose
@@ -566,8 +619,6 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   const int nbuf = (int)std::max<int64_t>(0, *std::min_element(nbuf_cap, nbuf_cap + 5));
   const int nb = nbt + nbuf;
   const int mmax = o.max_subspace_mult * nb;
-  if (!s.dav) s.dav = new DavWs();
-  DavWs& w = *s.dav;
   Layout L = carve(s, w, nb, mmax);
   cudaStream_t st = s.stream;
   // grow every workspace the loop can need now, so that no allocation (and no
@@ -579,12 +630,12 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   oz_reserve(s, true, mmax, mmax, (int)npw);
   oz_reserve(s, false, (int)npw, nb, mmax);
   if (s.nproj > 0) {
-    oz_reserve(s, true, s.nproj, nb, (int)npw);
-    oz_reserve(s, false, (int)npw, nb, s.nproj);
+    oz_reserve(s, true, s.nproj, nb, (int)s.npw);
+    oz_reserve(s, false, (int)s.npw, nb, s.nproj);
   }
   // and of the reduced phase (FP32-equivalent products of the same shapes,
   // the FP32 nonlocal term of the reduced-precision H)
-  if (o.mixed && s.nproj > 0) ensure(s.ws_vnl, (size_t)npw * nb * sizeof(float2));
+  if (o.mixed && s.nproj > 0) ensure(s.ws_vnl, (size_t)s.npw * nb * sizeof(float2));
   if (o.precond == PWH_PRECOND_MLP) ensure(w.mlp, (size_t)nb * s.nshell * sizeof(float));
   if (o.mixed) {
     x3_reserve(s, true, mmax, mmax, (int)npw);
@@ -592,6 +643,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   }
   if (o.mixed && o.jd_inner > 0) {
     ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
+  }
+  if (gamma) {
+    // the complex full-sphere bands that carry pairs of real ones
+    ensure(s.ws_psi, (size_t)s.npw * ((nb + 1) / 2) * sizeof(double2));
+    ensure(s.ws_hpsi, (size_t)s.npw * ((nb + 1) / 2) * sizeof(double2));
   }
   const double2 one = make_double2(1, 0), zero = make_double2(0, 0), mone = make_double2(-1, 0);
   const int tpa = o.precond == PWH_PRECOND_TPA ? 1 : 0;
@@ -603,18 +659,27 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   int phase_prec = o.mixed ? (s.precision == PWH_FP64 ? PWH_MIXED : s.precision) : PWH_FP64;
 
   auto applyH = [&](const double2* in, double2* out, int k) {
-    apply_internal(s, k, in, npw, out, npw, phase_prec);
+    space_apply(s, w, k, in, out, phase_prec);
     S.n_apply += k;
     if (phase_prec == PWH_FP64) S.n_apply_fp64 += k;
   };
 
   // starting block: public -> internal order (and the buffer bands),
   // orthonormalise, apply H
-  k_perm_in<<<grid1d(npw * nbt), 256, 0, st>>>(psi, ldpsi, npw, nbt, s.d_int_to_pub, L.V, npw);
-  PWH_LAUNCH_CHECK();
+  if (gamma) {
+    // half-sphere bands keep the public order; c(0) -> c(0) / sqrt 2, real
+    k_copy_cols<<<grid1d(npw * nbt), 256, 0, st>>>(psi, ldpsi, L.V, npw, npw, nbt);
+    PWH_LAUNCH_CHECK();
+    k_scale_row<<<(nbt + 255) / 256, 256, 0, st>>>(L.V, npw, nbt, s.gam_g0, 0.7071067811865476);
+    PWH_LAUNCH_CHECK();
+  } else {
+    k_perm_in<<<grid1d(npw * nbt), 256, 0, st>>>(psi, ldpsi, npw, nbt, s.d_int_to_pub, L.V, npw);
+    PWH_LAUNCH_CHECK();
+  }
   if (nbuf > 0) {
-    k_buffer_start<<<grid1d(npw * nbuf), 256, 0, st>>>(L.V + (size_t)nbt * npw, npw, nbuf, s.d_kin,
-                                                       0x9e3779b97f4a7c15ull ^ (uint64_t)nbt);
+    k_buffer_start<<<grid1d(npw * nbuf), 256, 0, st>>>(L.V + (size_t)nbt * npw, npw, nbuf, w.kin,
+                                                       0x9e3779b97f4a7c15ull ^ (uint64_t)nbt,
+                                                       gamma ? s.gam_g0 : -1);
     PWH_LAUNCH_CHECK();
   }
   int k0 = cholqr2(s, w, L, L.V, nb, nullptr, 0.0, st);
@@ -663,7 +728,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32);
     sgemm(s, gp, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
     sgemm(s, gp, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
-    k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, s.d_kin, L.R, L.rn, L.eref);
+    k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, w.kin, L.R, L.rn, L.eref, w.m2);
     PWH_LAUNCH_CHECK();
     PWH_CUDA(cudaMemcpyAsync(w.h_rn, L.rn, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (s.timer.on) {
@@ -775,7 +840,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       const int red = s.precision == PWH_FP64 ? PWH_MIXED : s.precision;
       jd_correction(s, w, L.X, nb, L.R, L.idx, k, L.theta, L.eref, o.jd_inner, red, T, L.Wc,
                     &S.n_apply, st);
-      k_col_dot<<<k, 1024, 0, st>>>(T, T, npw, L.t0);
+      k_col_dot<<<k, 1024, 0, st>>>(T, T, npw, L.t0, w.m2);
       PWH_LAUNCH_CHECK();
       k_sqrt<<<1, 256, 0, st>>>(L.t0, k);
       PWH_LAUNCH_CHECK();
@@ -786,8 +851,8 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
         sfac = (float*)w.mlp.p;
         mlp_factors(s, L.idx, k, L.theta, L.rn, L.eref, sfac, st);
       }
-      k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, s.d_kin, tpa || sfac, T, npw, L.t0,
-                                   sfac, s.d_shell, s.nshell);
+      k_precond<<<k, 256, 0, st>>>(L.R, npw, npw, L.idx, L.eref, w.kin, tpa || sfac, T, npw, L.t0,
+                                   sfac, w.shell, s.nshell, w.m2);
       PWH_LAUNCH_CHECK();
     }
     // project twice; with Jacobi-Davidson corrections (already orthogonal to X
@@ -812,8 +877,15 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   // outputs: the requested bands' eigenvalues (host) and eigenvectors
   // (public order, caller's buffer)
   PWH_CUDA(cudaMemcpyAsync(eig, L.theta, nbt * sizeof(double), cudaMemcpyDeviceToHost, st));
-  k_perm_out<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, npw, nbt, s.d_int_to_pub, psi, ldpsi);
-  PWH_LAUNCH_CHECK();
+  if (gamma) {
+    k_copy_cols<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, psi, ldpsi, npw, nbt);
+    PWH_LAUNCH_CHECK();
+    k_scale_row<<<(nbt + 255) / 256, 256, 0, st>>>(psi, ldpsi, nbt, s.gam_g0, 1.4142135623730951);
+    PWH_LAUNCH_CHECK();
+  } else {
+    k_perm_out<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, npw, nbt, s.d_int_to_pub, psi, ldpsi);
+    PWH_LAUNCH_CHECK();
+  }
   PWH_CUDA(cudaStreamSynchronize(st));
   check_err(s);
   const double t_end = now_s();
@@ -857,6 +929,38 @@ extern "C" pwh_status pwh_davidson_solve(pwh_system* sys, const pwh_davidson_opt
     if (o.precond == PWH_PRECOND_MLP && !s.have_mlp)
       throw Error{PWH_ERR_STATE, "PWH_PRECOND_MLP needs pwh_set_mlp first"};
     st = davidson_solve(s, o, (double2*)psi_io, ld_psi, eig, stats);
+    if (st == PWH_ERR_NOT_CONVERGED) set_error("Davidson stopped at max_iter before tol");
+    if (st == PWH_ERR_NONFINITE) set_error("non-finite residual norm");
+  });
+  return g != PWH_OK ? g : st;
+}
+
+extern "C" pwh_status pwh_davidson_solve_gamma(pwh_system* sys, const pwh_davidson_opts* opts,
+                                               void* psi_io, int64_t ld_psi, double* eig,
+                                               pwh_davidson_stats* stats) {
+  pwh_status st = PWH_OK;
+  pwh_status g = guarded([&] {
+    PWH_CHECK_ARG(sys && opts && psi_io && eig, "null argument");
+    System& s = sys->s;
+    const pwh_davidson_opts& o = *opts;
+    gamma_prepare(s);
+    const int64_t nh = (int64_t)s.gam_pub.size();
+    PWH_CHECK_ARG(o.nb >= 1 && o.nb <= 1024, "nb out of range [1, 1024]");
+    PWH_CHECK_ARG(o.nb <= nh, "nb larger than the half sphere");
+    PWH_CHECK_ARG(o.max_subspace_mult >= 2 && (int64_t)o.max_subspace_mult * o.nb <= 4096,
+                  "max_subspace_mult must be >= 2 and m_max <= 4096");
+    PWH_CHECK_ARG(o.max_iter >= 1, "max_iter < 1");
+    PWH_CHECK_ARG(std::isfinite(o.tol) && o.tol > 0, "tol must be > 0");
+    PWH_CHECK_ARG(!o.mixed || (std::isfinite(o.switch_tol) && o.switch_tol >= o.tol),
+                  "switch_tol must be >= tol");
+    PWH_CHECK_ARG(o.precond == PWH_PRECOND_TPA || o.precond == PWH_PRECOND_NONE ||
+                      o.precond == PWH_PRECOND_MLP,
+                  "unknown preconditioner");
+    PWH_CHECK_ARG(ld_psi >= nh, "ld_psi < npw_half");
+    if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
+    if (o.precond == PWH_PRECOND_MLP && !s.have_mlp)
+      throw Error{PWH_ERR_STATE, "PWH_PRECOND_MLP needs pwh_set_mlp first"};
+    st = davidson_solve(s, o, (double2*)psi_io, ld_psi, eig, stats, true);
     if (st == PWH_ERR_NOT_CONVERGED) set_error("Davidson stopped at max_iter before tol");
     if (st == PWH_ERR_NONFINITE) set_error("non-finite residual norm");
   });

@@ -33,44 +33,59 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
   return t;
 }
 
-// Sense-counting grid barrier for a cooperative launch (all blocks resident).
-// Returns false (after recording the error) if the wait ran out or another
-// block already gave up.
+// Grid barrier for a cooperative launch (all blocks resident).  One arrival
+// counter, zeroed before the launch and never reset inside it: the e-th
+// barrier of a block (its own epoch count; every block passes the same
+// barriers) is complete once the counter reaches e * gridDim.x.  Thread 0
+// arrives with a release-acquire add (publishing the block's writes, ordered
+// before it by the first __syncthreads) and polls with acquire loads, so the
+// whole block sees every other block's writes after the second
+// __syncthreads.  Returns false (after recording the error) if the wait ran
+// out or another block already gave up.
 struct GridBar {
   unsigned* count;
-  unsigned* gen;
+  unsigned* unused;
   int* abort;
   int* err;
 };
 
-__device__ bool grid_sync(const GridBar& gb) {
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_sync(const GridBar& gb, unsigned& epoch) {
   __shared__ int s_ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned* vgen = gb.gen;
-    volatile int* vab = gb.abort;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(gb.count, 1u) == gridDim.x - 1) {
-      *gb.count = 0;
-      __threadfence();
-      atomicAdd(gb.gen, 1u);
-    } else {
+    const unsigned target = epoch * gridDim.x;
+    unsigned v = atom_add_acq_rel_gpu(gb.count, 1u) + 1u;
+    if ((int)(v - target) < 0) {
       const uint64_t t0 = gtimer_ns();
       unsigned it = 0;
-      while (*vgen == g) {
-        if (*vab) { ok = 0; break; }
-        if ((++it & 255) == 0 && gtimer_ns() - t0 > kWaitNs) {
-          ok = 0;
-          atomicExch(gb.abort, 1);
-          atomicExch(gb.err, (int)PWH_ERR_TIMEOUT);
-          break;
+      while ((int)(ld_acquire_gpu(gb.count) - target) < 0) {
+        if ((++it & 63) == 0) {
+          if (*(volatile int*)gb.abort) {
+            ok = 0;
+            break;
+          }
+          if (gtimer_ns() - t0 > kWaitNs) {
+            ok = 0;
+            atomicExch(gb.abort, 1);
+            atomicExch(gb.err, (int)PWH_ERR_TIMEOUT);
+            break;
+          }
         }
       }
     }
-    __threadfence();
-    if (*vab) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
@@ -130,6 +145,7 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
   __shared__ double s_red[2][32];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
+  unsigned epoch = 0;  // grid barriers passed
   int cur = 0, sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
@@ -211,7 +227,7 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
       cur ^= 1;
       if (CLUSTER) {
         cluster_sync_all();
-      } else if (!grid_sync(a.gb)) {
+      } else if (!grid_sync(a.gb, epoch)) {
         return;
       }
     }
@@ -244,7 +260,7 @@ __global__ void k_jacobi(JacobiArgsT<T> a) {
     }
     if (CLUSTER) {
       cluster_sync_all();
-    } else if (!grid_sync(a.gb)) {
+    } else if (!grid_sync(a.gb, epoch)) {
       return;
     }
     if (*(volatile int*)a.conv) {
@@ -566,11 +582,38 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
   const int ntiles = T * (T + 1) / 2;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   int cur = 0, sweep = 0, rounds = 0;
+  unsigned epoch = 0;  // grid barriers passed
   bool done = false;
   while (sweep < a.max_sweeps && !done) {
     for (int r = 0; r < np - 1; ++r) {
       const float2* A = cur ? a.A[1] : a.A[0];
       float2* An = cur ? a.A[0] : a.A[1];
+      const int kl = gt % kPjTile, ll = gt / kPjTile;
+      // upper-triangle tile (I, J), I <= J, numbered row by row; its two
+      // 16-byte loads for this thread's pair of pairs (k, l) when it has one
+      auto tile_load = [&](int tile, int& I, int& J, bool& act, float4& c0, float4& c1) {
+        int i = 0, rem = tile < ntiles ? tile : 0;
+        while (rem >= T - i) {
+          rem -= T - i;
+          ++i;
+        }
+        I = i;
+        J = i + rem;
+        const int k = I * kPjTile + kl, l = J * kPjTile + ll;
+        act = tile < ntiles && k < P && l < P && (I != J || kl <= ll);
+        if (act) {
+          c0 = *(const float4*)(A + (size_t)(2 * l) * np + 2 * k);      // a00, a10
+          c1 = *(const float4*)(A + (size_t)(2 * l + 1) * np + 2 * k);  // a01, a11
+        }
+      };
+      // the block's first tile is loaded before the rotations are formed, so
+      // both L2 round trips of the round overlap
+      const int stride = gridDim.x * kPjTiles;
+      int t0 = blockIdx.x * kPjTiles;
+      int I, J;
+      bool act;
+      float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+      tile_load(t0 + grp, I, J, act, c0, c1);
       for (int k = threadIdx.x; k < P; k += blockDim.x) {
         const size_t d = (size_t)(2 * k) * np + 2 * k;
         float c;
@@ -584,22 +627,17 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
       }
       __syncthreads();
       // kPjTiles tiles at once, one per group of threads; every group runs
-      // the same number of iterations (the barriers stay uniform)
-      for (int t0 = blockIdx.x * kPjTiles; t0 < ntiles; t0 += gridDim.x * kPjTiles) {
-        const int tile = t0 + grp;
-        const bool tact = tile < ntiles;
-        int I = 0, rem = tact ? tile : 0;  // upper-triangle tile (I, J), I <= J, row by row
-        while (rem >= T - I) {
-          rem -= T - I;
-          ++I;
-        }
-        const int J = I + rem;
-        const int kl = gt % kPjTile, ll = gt / kPjTile;
+      // the same number of iterations (the barriers stay uniform); the next
+      // tile's operands are fetched while the current one is rotated
+      for (; t0 < ntiles; t0 += stride) {
+        const bool tact = t0 + grp < ntiles;
+        int In = 0, Jn = 0;
+        bool actn = false;
+        float4 n0 = c0, n1 = c1;
+        if (t0 + stride < ntiles) tile_load(t0 + stride + grp, In, Jn, actn, n0, n1);
         const int k = I * kPjTile + kl, l = J * kPjTile + ll;
-        if (tact && k < P && l < P && (I != J || kl <= ll)) {
+        if (act) {
           const float4 rk = rot[k], rl = rot[l];
-          const float4 c0 = *(const float4*)(A + (size_t)(2 * l) * np + 2 * k);      // a00, a10
-          const float4 c1 = *(const float4*)(A + (size_t)(2 * l + 1) * np + 2 * k);  // a01, a11
           float2 y00, y01, y10, y11;
           jacobi_block<float>(make_float2(c0.x, c0.y), make_float2(c1.x, c1.y),
                               make_float2(c0.z, c0.w), make_float2(c1.z, c1.w), rk.z,
@@ -636,10 +674,15 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
           }
         }
         __syncthreads();
+        I = In;
+        J = Jn;
+        act = actn;
+        c0 = n0;
+        c1 = n1;
       }
       ++rounds;
       cur ^= 1;
-      if (!grid_sync(a.gb)) return;
+      if (!grid_sync(a.gb, epoch)) return;
     }
     // convergence of the current matrix (position = index again): grid-wide
     // maxima of |A_ij| (i < j) and |A_ii|, every block takes the same decision
@@ -670,7 +713,7 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
         atomicMax(a.red + 2 * sweep, __float_as_uint(s_red[0][0]));
         atomicMax(a.red + 2 * sweep + 1, __float_as_uint(s_red[1][0]));
       }
-      if (!grid_sync(a.gb)) return;
+      if (!grid_sync(a.gb, epoch)) return;
       const float offg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep));
       const float dmg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep + 1));
       done = offg <= a.tol * fmaxf(dmg, 1e-30f);
@@ -790,7 +833,7 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   a.red = red;
   a.n = n; a.np = np; a.P = P; a.T = T; a.max_sweeps = max_sweeps;
   a.tol = (float)tol;
-  a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
+  a.gb.count = ctl; a.gb.unused = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
   const size_t smem = (size_t)P * sizeof(float4) +
                       (size_t)kPjTiles * (2 * kPjTile) * (2 * kPjTile + 1) * sizeof(float2);
@@ -874,7 +917,7 @@ static void launch_jacobi(System& s, DenseWs& w, cx<T>* A0, cx<T>* A1, cx<T>* Q0
   a.n = n; a.np = np; a.max_sweeps = max_sweeps; a.tol = tol;
   a.out_buf = out_buf;
   a.conv = (int*)(ctl + 12);
-  a.gb.count = ctl; a.gb.gen = ctl + 1; a.gb.abort = (int*)(ctl + 2);
+  a.gb.count = ctl; a.gb.unused = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
   const int P = np / 2;
   const size_t smem = (size_t)P * (sizeof(cx<T>) + sizeof(T) + 2 * sizeof(int)) + 16;

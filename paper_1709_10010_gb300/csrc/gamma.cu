@@ -28,10 +28,11 @@ void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2*
                     int precision);
 
 // Psi_j at the internal positions of G and -G from half-sphere bands 2j, 2j+1
-// (band 2j+1 absent for the last pair of an odd nb); c(0) keeps its real part.
+// (band 2j+1 absent for the last pair of an odd nb); c(0) keeps its real part,
+// times f0 (sqrt 2 for bands stored with c(0) / sqrt 2, else 1).
 __global__ void k_gamma_pack(const double2* __restrict__ psi, int64_t ldp, int64_t nh, int nb,
                              const int32_t* __restrict__ pos, const int32_t* __restrict__ neg,
-                             double2* __restrict__ dst, int64_t npw) {
+                             double2* __restrict__ dst, int64_t npw, double f0) {
   const int np = (nb + 1) / 2;
   const int64_t tot = nh * np;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
@@ -43,7 +44,7 @@ __global__ void k_gamma_pack(const double2* __restrict__ psi, int64_t ldp, int64
     const int32_t ip = pos[h], in = neg[h];
     double2* d = dst + (size_t)j * npw;
     if (ip == in) {
-      d[ip] = make_double2(a.x, b.x);
+      d[ip] = make_double2(f0 * a.x, f0 * b.x);
     } else {
       d[ip] = make_double2(a.x - b.y, a.y + b.x);  // a + i b
       d[in] = make_double2(a.x + b.y, b.x - a.y);  // conj(a) + i conj(b)
@@ -51,10 +52,11 @@ __global__ void k_gamma_pack(const double2* __restrict__ psi, int64_t ldp, int64
   }
 }
 
-// H psi_{2j}, H psi_{2j+1} on the half sphere from Phi_j = H Psi_j (internal order).
+// H psi_{2j}, H psi_{2j+1} on the half sphere from Phi_j = H Psi_j (internal
+// order); the G = 0 results times g0 (1 / sqrt 2 for the scaled storage).
 __global__ void k_gamma_unpack(const double2* __restrict__ phi, int64_t npw, int64_t nh, int nb,
                                const int32_t* __restrict__ pos, const int32_t* __restrict__ neg,
-                               double2* __restrict__ out, int64_t ldo) {
+                               double2* __restrict__ out, int64_t ldo, double g0) {
   const int np = (nb + 1) / 2;
   const int64_t tot = nh * np;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
@@ -62,10 +64,16 @@ __global__ void k_gamma_unpack(const double2* __restrict__ phi, int64_t npw, int
     const int64_t h = t % nh;
     const int j = (int)(t / nh);
     const double2* f = phi + (size_t)j * npw;
-    const double2 p = f[pos[h]], n = f[neg[h]];
-    out[(size_t)(2 * j) * ldo + h] = make_double2(0.5 * (p.x + n.x), 0.5 * (p.y - n.y));
-    if (2 * j + 1 < nb)
-      out[(size_t)(2 * j + 1) * ldo + h] = make_double2(0.5 * (p.y + n.y), -0.5 * (p.x - n.x));
+    const int32_t ip = pos[h], in = neg[h];
+    const double2 p = f[ip], n = f[in];
+    if (ip == in) {
+      out[(size_t)(2 * j) * ldo + h] = make_double2(g0 * p.x, 0.0);
+      if (2 * j + 1 < nb) out[(size_t)(2 * j + 1) * ldo + h] = make_double2(g0 * p.y, 0.0);
+    } else {
+      out[(size_t)(2 * j) * ldo + h] = make_double2(0.5 * (p.x + n.x), 0.5 * (p.y - n.y));
+      if (2 * j + 1 < nb)
+        out[(size_t)(2 * j + 1) * ldo + h] = make_double2(0.5 * (p.y + n.y), -0.5 * (p.x - n.x));
+    }
   }
 }
 
@@ -131,27 +139,41 @@ static void gamma_maps(System& s) {
   where.reserve((size_t)npw * 2);
   for (int64_t g = 0; g < npw; ++g)
     where[key(s.miller[3 * g], s.miller[3 * g + 1], s.miller[3 * g + 2])] = (int32_t)g;
-  std::vector<int32_t> pub, pos, neg;
+  std::vector<int32_t> pub, pos, neg, shell;
+  std::vector<double> kin;
+  int64_t g0 = -1;
   for (int64_t g = 0; g < npw; ++g) {
     const int m1 = s.miller[3 * g], m2 = s.miller[3 * g + 1], m3 = s.miller[3 * g + 2];
     const bool half = m1 > 0 || (m1 == 0 && (m2 > 0 || (m2 == 0 && m3 >= 0)));
     if (!half) continue;
     auto it = where.find(key(-m1, -m2, -m3));
     if (it == where.end()) throw Error{PWH_ERR_ARG, "the sphere is not symmetric under G -> -G"};
+    if (m1 == 0 && m2 == 0 && m3 == 0) g0 = (int64_t)pub.size();
     pub.push_back((int32_t)g);
     pos.push_back(pub_to_int[g]);
     neg.push_back(pub_to_int[it->second]);
+    kin.push_back(s.kin_pub[g]);
+    shell.push_back(s.shell_pub[g]);
   }
   const size_t nh = pub.size();
+  // one allocation: pos, neg, shell (int32), then the kinetic energies (8-byte aligned)
+  const size_t ints = (3 * nh + 1) & ~(size_t)1;
   int32_t* d = nullptr;
-  PWH_CUDA(cudaMalloc((void**)&d, 2 * nh * sizeof(int32_t)));
+  PWH_CUDA(cudaMalloc((void**)&d, ints * sizeof(int32_t) + nh * sizeof(double)));
+  double* dk = (double*)(d + ints);
   PWH_CUDA(cudaMemcpyAsync(d, pos.data(), nh * sizeof(int32_t), cudaMemcpyHostToDevice, s.stream));
   PWH_CUDA(cudaMemcpyAsync(d + nh, neg.data(), nh * sizeof(int32_t), cudaMemcpyHostToDevice,
                            s.stream));
+  PWH_CUDA(cudaMemcpyAsync(d + 2 * nh, shell.data(), nh * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           s.stream));
+  PWH_CUDA(cudaMemcpyAsync(dk, kin.data(), nh * sizeof(double), cudaMemcpyHostToDevice, s.stream));
   PWH_CUDA(cudaStreamSynchronize(s.stream));
   s.gam_pub = std::move(pub);
   s.d_gam_pos = d;
   s.d_gam_neg = d + nh;
+  s.d_gam_shell = d + 2 * nh;
+  s.d_gam_kin = dk;
+  s.gam_g0 = g0;
 }
 
 // Whether the projectors keep real functions real (checked once per set).
@@ -187,6 +209,32 @@ static void gamma_check_projectors(System& s) {
   if (!ok) throw Error{PWH_ERR_ARG, "projectors break G -> -G conjugate symmetry or D is not real"};
 }
 
+void gamma_prepare(System& s) {
+  gamma_maps(s);
+  gamma_check_projectors(s);
+}
+
+void gamma_apply(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
+                 int precision, bool scaled0) {
+  if (nb <= 0) return;
+  const int64_t nh = (int64_t)s.gam_pub.size();
+  const int np = (nb + 1) / 2;
+  const size_t n = (size_t)s.npw * np;
+  ensure(s.ws_psi, n * sizeof(double2));
+  ensure(s.ws_hpsi, n * sizeof(double2));
+  double2* pi = (double2*)s.ws_psi.p;
+  double2* hi = (double2*)s.ws_hpsi.p;
+  const double r2 = 1.4142135623730951;  // sqrt 2
+  k_gamma_pack<<<gamma_grid(nh * np), 256, 0, s.stream>>>(psi, ldp, nh, nb, s.d_gam_pos, s.d_gam_neg,
+                                                         pi, s.npw, scaled0 ? r2 : 1.0);
+  PWH_LAUNCH_CHECK();
+  apply_internal(s, np, pi, s.npw, hi, s.npw, precision);
+  k_gamma_unpack<<<gamma_grid(nh * np), 256, 0, s.stream>>>(hi, s.npw, nh, nb, s.d_gam_pos,
+                                                           s.d_gam_neg, hpsi, ldh,
+                                                           scaled0 ? 1.0 / r2 : 1.0);
+  PWH_LAUNCH_CHECK();
+}
+
 }  // namespace pwh
 
 using namespace pwh;
@@ -216,19 +264,7 @@ pwh_status pwh_apply_h_gamma(pwh_system* sys, int32_t nb, const void* psi, int64
     PWH_CHECK_ARG(ld_psi >= nh && ld_hpsi >= nh, "leading dimension < npw_half");
     if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
     gamma_check_projectors(s);
-    const int np = (nb + 1) / 2;
-    const size_t n = (size_t)s.npw * np;
-    ensure(s.ws_psi, n * sizeof(double2));
-    ensure(s.ws_hpsi, n * sizeof(double2));
-    double2* pi = (double2*)s.ws_psi.p;
-    double2* hi = (double2*)s.ws_hpsi.p;
-    k_gamma_pack<<<gamma_grid(nh * np), 256, 0, s.stream>>>((const double2*)psi, ld_psi, nh, nb,
-                                                           s.d_gam_pos, s.d_gam_neg, pi, s.npw);
-    PWH_LAUNCH_CHECK();
-    apply_internal(s, np, pi, s.npw, hi, s.npw, s.precision);
-    k_gamma_unpack<<<gamma_grid(nh * np), 256, 0, s.stream>>>(hi, s.npw, nh, nb, s.d_gam_pos,
-                                                             s.d_gam_neg, (double2*)hpsi, ld_hpsi);
-    PWH_LAUNCH_CHECK();
+    gamma_apply(s, nb, (const double2*)psi, ld_psi, (double2*)hpsi, ld_hpsi, s.precision, false);
   });
 }
 

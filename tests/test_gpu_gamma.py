@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from oracle import gamma as og
+from oracle import hamiltonian as oh
 from paper_1709_10010_gb300 import synthetic as syn
 from tests.helpers import case, rel_err
 
@@ -159,3 +160,75 @@ def test_gamma_medium_cell(torch):
         s.sync()
         assert rel_err(out, ref) <= tol, (mode, rel_err(out, ref))
         s.close()
+
+
+# ------------------------------------------------------- real-band eigensolver
+def full_norms(b, R_half):
+    """Norms over the full sphere of real bands given on the half sphere."""
+    return np.linalg.norm(og.expand(b.miller, R_half), axis=1)
+
+
+@pytest.mark.parametrize("kw,nb", [
+    (dict(seed=0, a=8.0, natoms=4, ecut_ry=14.0, lmax=1), 8),
+    (dict(seed=1, a=10.0, natoms=8, ecut_ry=20.0, lmax=1), 16),   # the 1503-plane-wave cell
+    (dict(seed=4, a=9.0, natoms=3, ecut_ry=16.0, lmax=2), 11),
+])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_davidson_gamma_matches_dense_eigh(torch, kw, nb, mode):
+    """Lowest eigenpairs of real bands against LAPACK on the oracle's dense H
+    (the complex H at k = 0 has the same spectrum); eigenvectors as real
+    functions: orthonormal over the full sphere, residual by the oracle's H."""
+    cell, b, v, beta, D = case(**kw)
+    s = make_system(cell, v, beta, D, mode)
+    half, _ = og.half_sphere(b.miller)
+    psi = torch.from_numpy(real_bands(5, len(half), nb, b)).cuda()
+    mixed = mode == "mixed"
+    eig, st, status = s.davidson_gamma(psi, tol=1e-9, mixed=mixed, switch_tol=1e-3,
+                                       jd_inner=20 if mixed else 0)
+    assert status == 0 and st["max_resid"] <= 1e-9
+    ref = np.linalg.eigvalsh(oh.dense_h(b, v, beta, D))[:nb]
+    assert np.abs(eig - ref).max() <= (1e-10 if mode == "fp64" else 1e-8), np.abs(eig - ref).max()
+    X = psi.cpu().numpy()
+    g0 = int(np.nonzero(np.all(b.miller[half] == 0, axis=1))[0][0])
+    assert np.abs(X[:, g0].imag).max() == 0.0                  # c(0) real on output
+    F = og.expand(b.miller, X)
+    assert np.abs(F.conj() @ F.T - np.eye(nb)).max() < 1e-12
+    R = og.apply_h_gamma(b, v, beta, D, X) - eig[:, None] * X
+    assert full_norms(b, R).max() <= 2e-9
+
+
+def test_davidson_gamma_medium_vs_complex(torch):
+    """The 34,265-plane-wave cell, 128 real bands (mixed + Jacobi-Davidson)
+    against the complex solver on the same system: eigenvalues within 1e-8 Ha;
+    sampled eigenvectors' residuals by the oracle's H."""
+    cell = syn.config_cell("medium", 0)
+    from oracle import basis as ob
+    b = ob.sphere(cell.lattice, cell.kpoint, cell.ecut_ha)
+    v = syn.potential_grid(cell, b.fft)
+    beta = syn.projectors(cell, b.miller)
+    D = syn.d_diagonal(cell)
+    s = make_system(cell, v, beta, D, "mixed")
+    nb = 128
+    half, _ = og.half_sphere(b.miller)
+    psig = torch.from_numpy(real_bands(0, len(half), nb, b)).cuda()
+    eg, stg, status = s.davidson_gamma(psig, tol=1e-8, mixed=True, switch_tol=1e-3, jd_inner=20)
+    assert status == 0 and stg["max_resid"] <= 1e-8
+    psic = torch.from_numpy(syn.initial_bands(0, b.npw, nb)).cuda()
+    ec, stc, status = s.davidson(psic, tol=1e-8, mixed=True, switch_tol=1e-3, jd_inner=20)
+    assert status == 0
+    assert np.abs(eg - ec).max() <= 1e-8, np.abs(eg - ec).max()
+    X = psig.cpu().numpy()
+    pick = [0, 1, 63, 126, 127]
+    R = og.apply_h_gamma(b, v, beta, D, X[pick]) - eg[pick, None] * X[pick]
+    assert full_norms(b, R).max() <= 2e-8
+    s.close()
+
+
+def test_davidson_gamma_rejects_k_shift(torch):
+    import paper_1709_10010_gb300 as pwh
+    cell, b, v, beta, D = case(seed=2, a=9.0, natoms=3, ecut_ry=12.0, lmax=2, k=(0.25, 0, 0))
+    s = make_system(cell, v, beta, D)
+    psi = torch.zeros((4, (b.npw + 1) // 2), dtype=torch.complex128, device="cuda")
+    with pytest.raises(pwh.PwhError) as e:
+        s.davidson_gamma(psi)
+    assert e.value.status == 1
