@@ -76,6 +76,10 @@ def parse():
     p.add_argument("--hpsi-only", choices=["mixed", "fp64"], default=None,
                    help="for profilers: W + K applications of H (this precision) to the "
                         "workload's bands, a short JSON line, nothing else")
+    p.add_argument("--eigh", type=int, default=0, metavar="N",
+                   help="for profilers: W + K reduced-precision Rayleigh-Ritz eigensolves "
+                        "(pwh_subspace_eigh, the FP32 Jacobi stage) of a seeded random Hermitian "
+                        "N x N matrix, a short JSON line, nothing else")
     p.add_argument("--profile", action="store_true",
                    help="for a profiler's launch list: only the warm-up and timed solves, a short "
                         "JSON line (no FP64 solve, H-only, e2e, batched or CPU legs)")
@@ -233,6 +237,24 @@ def gamma_solve(torch, s, nb, steps, seed=0):
             "steps": len(runs), "eig": eig}
 
 
+def run_eigh(torch, pwh, syn, a):
+    """Profiling entry for the subspace eigensolver alone: the lowest N/3
+    eigenpairs of a seeded random Hermitian N x N matrix in reduced precision
+    (the FP32 Jacobi stage of the reduced phase), W untimed and K timed calls."""
+    n = a.eigh
+    s = pwh.System.from_cell(syn.config_cell("small", 0), precision="mixed")
+    H = torch.from_numpy(syn.random_hermitian(0, n).T.copy()).cuda()
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        s.subspace_eigh(H, n // 3, precision="mixed")
+    t, _ = timed(torch, stream, lambda: [s.subspace_eigh(H, n // 3, precision="mixed")
+                                         for _ in range(a.steps)])
+    s.sync()
+    print(json.dumps({"metric": "reduced-precision subspace eigensolves/s", "value": a.steps / t,
+                      "ms_per_call": 1e3 * t / a.steps, "n": n, "steps": a.steps,
+                      "warmup": a.warmup}))
+
+
 def run_ours(a):
     import torch
     import paper_1709_10010_gb300 as pwh
@@ -256,6 +278,9 @@ def run_ours(a):
 
     from paper_1709_10010_gb300 import build
     build.build()
+    if a.eigh:
+        run_eigh(torch, pwh, syn, a)
+        return
     cfg = syn.CONFIGS[a.workload]
     cell = syn.config_cell(a.workload, seed=rank)
     nb = cfg["nb"]
@@ -551,7 +576,7 @@ def roofline(kt, s=None):
     return r
 
 
-CPU_SAMPLE_BANDS = 16   # bands per oracle H application in the CPU baseline
+CPU_SAMPLE_BANDS = 64   # bands per oracle H application in the CPU baseline (about 10 s)
 REF_SAMPLE_BANDS = 4    # bands per step of the reference arm
 
 

@@ -786,9 +786,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       result = PWH_ERR_NONFINITE;
       break;
     }
-    bool buffers_done = true;
-    for (int b = nbt; b < nb; ++b) buffers_done = buffers_done && !above(b);
-    // a reduced phase that stopped improving (its arithmetic's floor above
+    // the hand-over waits for the requested bands only: buffer bands still
+    // above their reduced-phase target are carried into the FP64 phase, whose
+    // Jacobi-Davidson steps converge them anyway (waiting for them cost the
+    // 512-band solve three reduced iterations at the reduced phase's floor).
+    // A reduced phase that stopped improving (its arithmetic's floor above
     // switch_tol) hands over as well: the best of its last four requested-band
     // residuals not 0.8 of the best of the four before
     bool stalled = false;
@@ -801,7 +803,7 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
         stalled = a > 0.8 * b;
       }
     }
-    if (phase_prec != PWH_FP64 && ((maxr_t <= o.switch_tol && buffers_done) || stalled)) {
+    if (phase_prec != PWH_FP64 && (maxr_t <= o.switch_tol || stalled)) {
       // hand over to FP64: restart from the Ritz vectors with the FP64 operator
       const double t = now_s();
       S.t_mixed_s = t - t_phase;
