@@ -18,6 +18,11 @@ eye against the method's definitions:
 * ``scf``         the SCF steps around H: density of a set of bands, Hartree
                   potential by the Fourier-space Poisson solution, LDA
                   exchange-correlation (Slater + Perdew-Zunger)
+* ``gamma``       real bands at k = 0: the half sphere, expansion by conjugate
+                  symmetry, H of real bands, two real bands per complex FFT
+* ``exx``         exact (Fock) exchange by pair densities and the Fourier-space
+                  Poisson solution (FFT route and a reciprocal-space sum), and
+                  its adaptively compressed form (ACE)
 
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``) tie each function
 to closed forms, invariants, brute force or library routines, never to itself.
