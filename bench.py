@@ -51,6 +51,7 @@ SWITCH_TOL = 1e-3
 JD_INNER = 20
 MULT = 3
 HPSI_REPS = 20      # H|psi>-only repeats (median reported)
+ACE_NOCC = 32       # occupied bands of the exact-exchange (ACE) leg
 E2E_STEPS = 3       # end-to-end solves through host buffers
 # Fallback peaks (no measured-peaks file on this machine): HBM copy bandwidth
 # and the derived CUDA-core arithmetic peaks (lanes x FMA x clock).
@@ -68,6 +69,8 @@ def parse():
     p.add_argument("--skip-fp64", action="store_true", help="omit the FP64 comparison solve")
     p.add_argument("--skip-batched", action="store_true", help="omit the batched cells x k-points solve")
     p.add_argument("--skip-medium", action="store_true", help="omit the medium-cell secondary line")
+    p.add_argument("--skip-ace", action="store_true",
+                   help="omit the exact-exchange / ACE leg on the medium cell")
     p.add_argument("--skip-gamma", action="store_true",
                    help="omit the real-band (k = 0 half-sphere) solve of the same workload")
     p.add_argument("--workload", default=WORKLOAD, choices=["large", "medium", "small"],
@@ -80,6 +83,10 @@ def parse():
                    help="for profilers: W + K reduced-precision Rayleigh-Ritz eigensolves "
                         "(pwh_subspace_eigh, the FP32 Jacobi stage) of a seeded random Hermitian "
                         "N x N matrix, a short JSON line, nothing else")
+    p.add_argument("--gemm", default=None, metavar="M,N,K,PREC,CONJ",
+                   help="for profilers: W + K subspace GEMMs (pwh_subspace_gemm) of this shape, "
+                        "precision fp64|mixed and op(A) = A^H when CONJ is 1, on seeded random "
+                        "operands, a short JSON line, nothing else")
     p.add_argument("--profile", action="store_true",
                    help="for a profiler's launch list: only the warm-up and timed solves, a short "
                         "JSON line (no FP64 solve, H-only, e2e, batched or CPU legs)")
@@ -255,6 +262,28 @@ def run_eigh(torch, pwh, syn, a):
                       "warmup": a.warmup}))
 
 
+def run_gemm(torch, pwh, syn, a):
+    """Profiling entry for one subspace-GEMM shape: C = op(A) B with seeded
+    N(0,1) complex operands, W untimed and K timed calls."""
+    M, N, K, prec, conj = a.gemm.split(",")
+    M, N, K, conj = int(M), int(N), int(K), conj == "1"
+    s = pwh.System.from_cell(syn.config_cell("small", 0), precision="mixed")
+    g = torch.Generator(device="cuda").manual_seed(0)
+    ra, ka = (K, M) if conj else (M, K)             # stored A: ra rows x ka columns
+    A = torch.randn((ka, ra), dtype=torch.complex128, device="cuda", generator=g)
+    B = torch.randn((N, K), dtype=torch.complex128, device="cuda", generator=g)
+    C = torch.zeros((N, M), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(a.warmup):
+        s.gemm(A, B, C, conj_a=conj, precision=prec)
+    t, _ = timed(torch, stream, lambda: [s.gemm(A, B, C, conj_a=conj, precision=prec)
+                                         for _ in range(a.steps)])
+    print(json.dumps({"metric": "subspace GEMM TFLOP/s (8 M N K complex flops)",
+                      "value": 8.0 * M * N * K * a.steps / t / 1e12, "ms_per_call": 1e3 * t / a.steps,
+                      "shape": [M, N, K], "precision": prec, "conj_a": conj, "steps": a.steps,
+                      "warmup": a.warmup}))
+
+
 def run_ours(a):
     import torch
     import paper_1709_10010_gb300 as pwh
@@ -280,6 +309,9 @@ def run_ours(a):
     build.build()
     if a.eigh:
         run_eigh(torch, pwh, syn, a)
+        return
+    if a.gemm:
+        run_gemm(torch, pwh, syn, a)
         return
     cfg = syn.CONFIGS[a.workload]
     cell = syn.config_cell(a.workload, seed=rank)
@@ -390,6 +422,8 @@ def run_ours(a):
 
     # ---- the medium cell (34,265 plane waves, 128 bands) as a secondary line
     medium = None if (a.skip_medium or a.workload == "medium") else run_medium(pwh, syn, torch)
+    # ---- exact exchange: ACE built and applied on the medium cell
+    ace = None if a.skip_ace else run_ace(pwh, syn, torch)
     # ---- batched workload: 32 cells x 8 k-points solved concurrently
     batched = None if a.skip_batched else run_batched(pwh, syn, torch)
 
@@ -425,6 +459,7 @@ def run_ours(a):
         "hpsi_only": hp,
         "gamma_real_bands": gam,
         "medium": medium,
+        "ace": ace,
         "batched": batched,
         "kernels": {k: {"launches": d["launches"], "ms": round(d["ms"], 3),
                         "share": round(d["ms"] / max(1e-9, ktot), 4),
@@ -473,6 +508,52 @@ def run_medium(pwh, syn, torch):
                                                      "fp64": st64["iters"]},
             "max_abs_dlambda_mixed_vs_fp64_ha": float(np.abs(eig - eig64).max()),
             "hpsi_only": hp}
+
+
+def run_ace(pwh, syn, torch, nocc=ACE_NOCC):
+    """Exact exchange on the medium cell: the ACE operator built from the
+    lowest `nocc` bands (one FP64 solve supplies them; pair densities and
+    Poisson solves on the 90^3 box), H|psi> on the 128 resident bands with and
+    without the ACE term (median of 20), and one mixed + Jacobi-Davidson solve
+    of H + V_ACE to 1e-8 (alpha = 0.25, the PBE0 fraction), CUDA-event timed."""
+    cell = syn.config_cell("medium", 0)
+    nb = syn.CONFIGS["medium"]["nb"]
+    s, v, beta, D = make_system(pwh, syn, cell)
+    stream = torch.cuda.current_stream()
+    psi0 = torch.from_numpy(syn.initial_bands(0, s.npw, nb)).cuda()
+    psi = psi0.clone()
+    eig0, _, status = s.davidson(psi, tol=TOL, mult=MULT, mixed=True, switch_tol=SWITCH_TOL,
+                                 jd_inner=JD_INNER)
+    assert status == 0
+    occ_bands = psi[:nocc].contiguous()
+    occ = np.full(nocc, 2.0)
+    t_build, rank = timed(torch, stream, lambda: s.set_ace(occ_bands, occ, 0.25))
+    out = torch.empty_like(psi0)
+    res = {}
+    for label, on in (("without_ace", False), ("with_ace", True)):
+        if not on:
+            s.set_ace(None)
+        else:
+            s.set_ace(occ_bands, occ, 0.25)
+        for _ in range(3):
+            s.apply_h(psi0, out)
+        ts = [timed(torch, stream, lambda: s.apply_h(psi0, out))[0] for _ in range(HPSI_REPS)]
+        res[label] = {"band_applies_s": nb / statistics.median(ts),
+                      "median_ms": 1e3 * statistics.median(ts)}
+
+    def solve():
+        psi.copy_(psi0)
+        return s.davidson(psi, tol=TOL, mult=MULT, mixed=True, switch_tol=SWITCH_TOL,
+                          jd_inner=JD_INNER)
+    solve()
+    t_solve, (eig, st, status) = timed(torch, stream, solve)
+    assert status == 0
+    s.close()
+    return {"workload": f"medium cell, ACE from the lowest {nocc} bands (weights 2, alpha 0.25), "
+                        f"{nb} bands to 1e-8", "nocc": nocc, "rank": int(rank),
+            "ace_build_s": t_build, "pair_densities": nocc * nocc, "hpsi_only_mixed": res,
+            "solve_with_ace_s": t_solve, "iters": st["iters"],
+            "lowest_eig_shift_ha": float(eig[0] - eig0[0])}
 
 
 def run_batched(pwh, syn, torch, ncells=32, nthreads=16):

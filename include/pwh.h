@@ -111,7 +111,8 @@ pwh_status pwh_set_projectors(pwh_system* sys, int32_t nproj, const void* beta,
 /* Select the compute precision of pwh_apply_h (pwh_precision). */
 pwh_status pwh_set_precision(pwh_system* sys, int32_t precision);
 
-/* hpsi = H psi for nb bands.  psi, hpsi: DEVICE complex128, column-major with
+/* hpsi = H psi for nb bands (plus the ACE exchange term -zeta zeta^H psi when
+ * pwh_set_ace has set one).  psi, hpsi: DEVICE complex128, column-major with
  * leading dimensions ld_psi, ld_hpsi >= npw; they must not overlap.
  * Asynchronous on the system's stream.  Requires pwh_set_potential first
  * (PWH_ERR_STATE otherwise).  nb = 0 is a no-op. */
@@ -284,6 +285,43 @@ pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opt
  * real). */
 pwh_status pwh_davidson_solve_gamma(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                                     int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
+
+/* ------------------------------------------------ exact exchange and ACE --
+ * The Fock exchange operator of Eq. Vx (Sec. "Advanced implementation of exact
+ * (Fock) exchange and hybrid functionals"), Hartree units:
+ *   (V_x phi)(r) = - sum_j occ_j psi_j(r) v_j(r),  v_j(G) = 4 pi rho_j(G) / |G|^2,
+ *   rho_j(r) = conj(psi_j(r)) phi(r),
+ * with the pair-density potentials of Eq. Poisson solved on the full FFT box
+ * (the divergent G = 0 term is left out); psi_j and phi at the system's k.
+ * On the default box (N_d >= 4 mmax_d + 1) the FFT route is exact. */
+
+/* out = V_x phi for nb bands.  psi_occ: nocc occupied bands, occ: host weights
+ * (finite); phi, out: nb bands; all DEVICE complex128, public order,
+ * column-major, ld >= npw.  FP64.  Device scratch of (nocc + 64 MB / box + 2)
+ * full boxes is allocated for the call and freed before it returns;
+ * synchronous.  Cost: nb * nocc pair densities, two 3D FFTs each.  Errors:
+ * PWH_ERR_ARG, PWH_ERR_OOM, PWH_ERR_CUDA. */
+pwh_status pwh_exx_apply(pwh_system* sys, int32_t nocc, const void* psi_occ, int64_t ld_occ,
+                         const double* occ, int32_t nb, const void* phi, int64_t ld_phi,
+                         void* out, int64_t ld_out);
+
+/* Adaptively compressed exchange (ACE, Eq. Vxace): from nocc occupied bands
+ * psi_occ (DEVICE, public order, ld >= npw) with host weights occ (> 0),
+ * xi_i = V_x psi_i, M = <psi_j|xi_m>, and the operator
+ * alpha * sum_jm |xi_j> (M^-1)_jm <xi_m| = -zeta zeta^H (zeta = sqrt(alpha)
+ * xi L^-H, -M = L L^H).  The system keeps zeta; from then on pwh_apply_h, the
+ * eigensolvers and the real-band routes add -zeta zeta^H psi to H psi (two
+ * GEMMs in the system's precision: FP64-equivalent or FP32-equivalent on the
+ * tensor cores).  alpha: the exchange fraction (e.g. 0.25).  The operator
+ * equals alpha V_x on the span of psi_occ.  *rank (optional) receives the
+ * number of kept directions (columns of M that are numerically dependent are
+ * dropped).  nocc = 0 removes the term.  Synchronous.  Errors: PWH_ERR_ARG
+ * (sizes, weights, alpha, an exchange matrix without a positive direction),
+ * PWH_ERR_OOM, PWH_ERR_CUDA.  The real-band routes (pwh_apply_h_gamma,
+ * pwh_davidson_solve_gamma) accept the term only when zeta are real
+ * functions (psi_occ real at k = 0), else PWH_ERR_ARG. */
+pwh_status pwh_set_ace(pwh_system* sys, int32_t nocc, const void* psi_occ, int64_t ld_occ,
+                       const double* occ, double alpha, int32_t* rank);
 
 /* ------------------------------------------------------------- SCF steps --
  * The steps either side of H|psi> in a self-consistent Kohn-Sham calculation

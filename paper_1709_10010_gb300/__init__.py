@@ -105,6 +105,9 @@ SIGNATURES = {
     "pwh_davidson_solve_gamma": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
                                           ctypes.POINTER(DavidsonStats)]),
     "pwh_get_davidson_trace": (_c_i32, [_c_p, _c_i32, _c_p, ctypes.POINTER(_c_i32)]),
+    "pwh_exx_apply": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i32, _c_p, _c_i64, _c_p,
+                               _c_i64]),
+    "pwh_set_ace": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_d, ctypes.POINTER(_c_i32)]),
     "pwh_density": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_p]),
     "pwh_hartree_xc": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
@@ -375,6 +378,35 @@ class System:
         _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
                                       hpsi.ctypes.data_as(_c_p)))
         return hpsi
+
+    # ------------------------------------------------------- exact exchange
+    def exx_apply(self, psi_occ, occ, phi, out=None):
+        """V_x phi (Fock exchange of the occupied bands psi_occ with weights
+        occ) for bands phi; (n, npw) CUDA complex128 tensors, public order."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(phi, memory_format=torch.contiguous_format)
+        po, ldo = _band_ptr(psi_occ, self.npw)
+        pp, ldp = _band_ptr(phi, self.npw)
+        op, ldr = _band_ptr(out, self.npw)
+        w = np.ascontiguousarray(occ, dtype=np.float64)
+        _check(lib().pwh_exx_apply(self._h, int(psi_occ.shape[0]), po, ldo, w.ctypes.data_as(_c_p),
+                                   int(phi.shape[0]), pp, ldp, op, ldr))
+        return out
+
+    def set_ace(self, psi_occ=None, occ=None, alpha=1.0):
+        """Adaptively compressed exchange of the occupied bands psi_occ (CUDA
+        complex128 (nocc, npw)) added to H from now on; None removes it.
+        Returns the rank kept."""
+        r = _c_i32()
+        if psi_occ is None:
+            _check(lib().pwh_set_ace(self._h, 0, None, self.npw, None, 1.0, ctypes.byref(r)))
+            return 0
+        po, ldo = _band_ptr(psi_occ, self.npw)
+        w = np.ascontiguousarray(occ, dtype=np.float64)
+        _check(lib().pwh_set_ace(self._h, int(psi_occ.shape[0]), po, ldo, w.ctypes.data_as(_c_p),
+                                 float(alpha), ctypes.byref(r)))
+        return r.value
 
     # ------------------------------------------------------------ SCF steps
     def density(self, psi, occ):

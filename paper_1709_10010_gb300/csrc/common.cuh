@@ -239,6 +239,18 @@ struct System {
   int64_t gam_g0 = -1;              // position of G = 0 in the half sphere
   int gam_proj_ok = -1;
 
+  // exact exchange and ACE (exx.cu): the full-box index of each public plane
+  // wave, the Coulomb factor 4 pi / (|G|^2 Omega N^3) on the box (0 at G = 0),
+  // and the ACE projectors zeta (internal order, npw x ace_n; the operator is
+  // -zeta zeta^H, added to H when ace_n > 0) with whether they are real
+  // functions at k = 0 (-1: not checked)
+  int32_t* d_boxidx = nullptr;
+  double* d_kern = nullptr;
+  double2* d_ace = nullptr;
+  int ace_n = 0;
+  int ace_real = -1;
+  DevBuf<char> ws_ace;              // zeta^H psi of the ACE term (ace_n x nb)
+
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)
@@ -335,7 +347,9 @@ void density_accumulate(System& s, int nb, const double2* psi_int, const double*
                         double* rho_int);
 // In-place unscaled 3D FFT of the full box (complex FP64, C order i3 fastest):
 // forward exp(-i G.r), inverse exp(+i G.r).
-void box_fft(System& s, double2* box, bool inverse);
+// 3D FFT of nbox full boxes (complex FP64, C order, i3 fastest), bstride
+// elements apart; forward exp(-i) or inverse exp(+i), both unscaled.
+void box_fft(System& s, double2* box, bool inverse, int nbox = 1, int64_t bstride = 0);
 // Real bands at k = 0 (gamma.cu): build the half-sphere tables and check the
 // projectors (throws PWH_ERR_ARG where real bands do not apply); H on nb
 // half-sphere bands, two per complex band of the full sphere.  scaled0: the

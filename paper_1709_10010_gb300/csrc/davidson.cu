@@ -644,6 +644,16 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
   if (o.mixed && o.jd_inner > 0) {
     ensure(w.cg, (size_t)4 * npw * nb * sizeof(double2) + 8 * (size_t)nb * sizeof(double) + 256);
   }
+  if (s.ace_n > 0) {
+    // the ACE term's products (ace_n x nb over npw, npw x nb over ace_n)
+    ensure(s.ws_ace, (size_t)s.ace_n * nb * sizeof(double2));
+    oz_reserve(s, true, s.ace_n, nb, (int)s.npw);
+    oz_reserve(s, false, (int)s.npw, nb, s.ace_n);
+    if (o.mixed) {
+      x3_reserve(s, true, s.ace_n, nb, (int)s.npw);
+      x3_reserve(s, false, (int)s.npw, nb, s.ace_n);
+    }
+  }
   if (gamma) {
     // the complex full-sphere bands that carry pairs of real ones
     ensure(s.ws_psi, (size_t)s.npw * ((nb + 1) / 2) * sizeof(double2));

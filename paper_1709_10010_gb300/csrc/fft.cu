@@ -441,12 +441,15 @@ __global__ void __launch_bounds__(512) k_density_plane(const double2* __restrict
 // along one axis: lines of `axis` (0, 1, 2 for i1, i2, i3), `lines` of them a
 // block, chosen consecutive in the fastest other index so that loads and
 // stores are contiguous runs.  Forward: exp(-i), natural order in and out
-// (unscaled); inverse: exp(+i), unscaled.
+// (unscaled); inverse: exp(+i), unscaled.  blockIdx.y selects the box of a
+// batch, boxes bstride elements apart.
 __global__ void __launch_bounds__(256) k_box_fft_axis(double2* __restrict__ box, int n1, int n2,
                                                       int n3, int axis, int inverse, FftPlan pl,
                                                       const double2* __restrict__ tw_g,
-                                                      const int16_t* __restrict__ perm_g, int lines) {
+                                                      const int16_t* __restrict__ perm_g, int lines,
+                                                      int64_t bstride) {
   using T = double;
+  box += (int64_t)blockIdx.y * bstride;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n = pl.n, ld = n + 1;
   cx<T>* buf = (cx<T>*)smem_raw;
@@ -524,7 +527,7 @@ void density_accumulate(System& s, int nb, const double2* psi_int, const double*
   }
 }
 
-void box_fft(System& s, double2* box, bool inverse) {
+void box_fft(System& s, double2* box, bool inverse, int nbox, int64_t bstride) {
   const int n[3] = {s.n1, s.n2, s.n3};
   static std::once_flag once;
   std::call_once(once, [] {
@@ -537,8 +540,9 @@ void box_fft(System& s, double2* box, bool inverse) {
     int lines = 16;
     while (lines > 1 && ((size_t)lines * (pl.n + 1) + pl.n) * sizeof(double2) > 96 * 1024) lines /= 2;
     const size_t smem = ((size_t)lines * (pl.n + 1) + pl.n) * sizeof(double2) + pl.n * sizeof(int16_t);
-    k_box_fft_axis<<<(unsigned)((nlines + lines - 1) / lines), 256, smem, s.stream>>>(
-        box, s.n1, s.n2, s.n3, axis, inverse ? 1 : 0, pl, s.d_tw64, s.d_perm, lines);
+    k_box_fft_axis<<<dim3((unsigned)((nlines + lines - 1) / lines), (unsigned)nbox), 256, smem,
+                     s.stream>>>(box, s.n1, s.n2, s.n3, axis, inverse ? 1 : 0, pl, s.d_tw64, s.d_perm,
+                                 lines, bstride);
     PWH_LAUNCH_CHECK();
   }
 }

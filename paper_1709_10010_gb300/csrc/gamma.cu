@@ -209,9 +209,34 @@ static void gamma_check_projectors(System& s) {
   if (!ok) throw Error{PWH_ERR_ARG, "projectors break G -> -G conjugate symmetry or D is not real"};
 }
 
+// Whether the ACE projectors (when set) are real functions, so that the ACE
+// term keeps real bands real (checked once per pwh_set_ace).
+static void gamma_check_ace(System& s) {
+  if (s.ace_n == 0 || s.ace_real == 1) return;
+  if (s.ace_real == 0) throw Error{PWH_ERR_ARG, "the ACE projectors are not real functions"};
+  const int64_t nh = (int64_t)s.gam_pub.size();
+  unsigned* d = nullptr;
+  PWH_CUDA(cudaMalloc((void**)&d, 4 * sizeof(unsigned)));
+  PWH_CUDA(cudaMemsetAsync(d, 0, 4 * sizeof(unsigned), s.stream));
+  k_gamma_beta_check<<<gamma_grid(nh * s.ace_n), 256, 0, s.stream>>>(
+      s.d_ace, s.npw, nh, s.ace_n, s.d_gam_pos, s.d_gam_neg, d);
+  cudaError_t e = cudaGetLastError();
+  note_launch();
+  unsigned h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+  cudaFree(d);
+  PWH_CUDA(e);
+  float v[2];
+  for (int i = 0; i < 2; ++i) std::memcpy(&v[i], &h[i], sizeof(float));
+  s.ace_real = v[0] <= 1e-10f * v[1] ? 1 : 0;
+  if (!s.ace_real) throw Error{PWH_ERR_ARG, "the ACE projectors are not real functions"};
+}
+
 void gamma_prepare(System& s) {
   gamma_maps(s);
   gamma_check_projectors(s);
+  gamma_check_ace(s);
 }
 
 void gamma_apply(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
@@ -264,6 +289,7 @@ pwh_status pwh_apply_h_gamma(pwh_system* sys, int32_t nb, const void* psi, int64
     PWH_CHECK_ARG(ld_psi >= nh && ld_hpsi >= nh, "leading dimension < npw_half");
     if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
     gamma_check_projectors(s);
+    gamma_check_ace(s);
     gamma_apply(s, nb, (const double2*)psi, ld_psi, (double2*)hpsi, ld_hpsi, s.precision, false);
   });
 }

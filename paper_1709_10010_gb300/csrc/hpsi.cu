@@ -63,6 +63,9 @@ void nonlocal_fp64(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   cgemm<double>(s, false, (int)s.npw, nb, P, one, s.d_beta64, s.npw, becp, P, one, hpsi, ldh, st);
 }
 
+void ace_apply(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
+               int precision);  // exx.cu
+
 void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
                     int precision) {
   if (!s.have_v) throw Error{PWH_ERR_STATE, "pwh_set_potential has not been called"};
@@ -70,6 +73,7 @@ void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2*
   if (precision == PWH_FP64) {
     local_kinetic<double>(s, nb, psi, ldp, hpsi, ldh, s.stream);
     nonlocal_fp64(s, nb, psi, ldp, hpsi, ldh, s.stream);
+    ace_apply(s, nb, psi, ldp, hpsi, ldh, precision);
   } else {
     // the nonlocal term first, into an FP32 buffer that the last FFT pass adds
     float2* vnl = nullptr;
@@ -79,6 +83,7 @@ void apply_internal(System& s, int nb, const double2* psi, int64_t ldp, double2*
       nonlocal_mixed(s, nb, psi, ldp, vnl, s.npw, s.stream, precision == PWH_MIXED_FAST ? 1 : 3);
     }
     local_kinetic<float>(s, nb, psi, ldp, hpsi, ldh, s.stream, vnl, s.npw);
+    ace_apply(s, nb, psi, ldp, hpsi, ldh, precision);
   }
 }
 

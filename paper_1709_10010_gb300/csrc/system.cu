@@ -88,7 +88,8 @@ System::~System() {
                   d_stick_y, d_col_x, d_stick_at, d_xcol, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_vnl.p, ws_grid.p, ws_tune.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
-                  ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp, d_gam_pos};
+                  ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp, d_gam_pos,
+                  d_boxidx, d_kern, d_ace, ws_ace.p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
