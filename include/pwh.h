@@ -463,6 +463,21 @@ pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t 
                              double* theta, void* C, void* Q, int64_t ldq, int32_t warm,
                              int32_t precision);
 
+/* Cholesky-QR factor of the eigensolver's orthonormalisation (the iterative
+ * orthonormalisation of Sec. "New parallelization levels"): from the Gram
+ * matrix S = T^H T (k x k, DEVICE complex128, column-major, ld = k) of k
+ * columns, Tr (DEVICE k x k, ld = k) such that the first *kept columns of
+ * T Tr are orthonormal (the others zero).  Column j is dropped when S_jj <= 0,
+ * when t0 (optional DEVICE double[k], the column norms before a projection)
+ * is given and sqrt(S_jj) < drop_rel t0[j], or when the pivot of the
+ * unit-diagonal matrix falls to the rounding level of the arithmetic (1e-12
+ * in FP64, 1e-6 for PWH_MIXED: FP32).  Up to 156 (FP64) / 221 (FP32) columns on
+ * one block with the triangle in shared memory, above that a blocked
+ * factorisation and inverse over the whole GPU.  k <= 1024.  kept: HOST int;
+ * the call synchronises the stream to read it. */
+pwh_status pwh_subspace_cholqr(pwh_system* sys, int32_t precision, int32_t k, const void* S,
+                               const double* t0, double drop_rel, void* Tr, int32_t* kept);
+
 /* Complex GEMM of the subspace algebra (the O_ij = <psi_i|O|psi_j> products and
  * basis rotations of Sec. "New parallelization levels"), as the eigensolver
  * uses it: C = alpha op(A) B + beta C, op(A) = A^H when conj_a else A; op(A)

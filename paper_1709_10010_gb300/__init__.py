@@ -111,6 +111,8 @@ SIGNATURES = {
     "pwh_density": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_p]),
     "pwh_hartree_xc": (_c_i32, [_c_p, _c_p, _c_p, _c_p, _c_p]),
     "pwh_apply_local_noalloc": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
+    "pwh_subspace_cholqr": (_c_i32, [_c_p, _c_i32, _c_i32, _c_p, _c_p, _c_d, _c_p,
+                                     ctypes.POINTER(_c_i32)]),
     "pwh_subspace_gemm": (_c_i32, [_c_p, _c_i32, _c_i32, _c_i32, _c_i32, _c_i32, _c_p, _c_p, _c_i64,
                                    _c_p, _c_i64, _c_p, _c_p, _c_i64]),
     "pwh_last_error": (ctypes.c_char_p, []),
@@ -293,6 +295,22 @@ class System:
                                        ctypes.c_void_p(C.data_ptr()), qp, ldq, int(warm),
                                        PRECISIONS[precision]))
         return theta, C
+
+    def cholqr(self, S, t0=None, drop_rel=0.0, precision="fp64"):
+        """Cholesky-QR factor of a Gram matrix S = T^H T given as a (k, k) CUDA
+        complex128 tensor holding S^T (column-major S); returns (Tr as a (k, k)
+        tensor holding Tr^T, kept) with T Tr orthonormal in its first kept
+        columns."""
+        torch = _torch()
+        k = int(S.shape[0])
+        Sc = S.contiguous()
+        Tr = torch.empty((k, k), dtype=torch.complex128, device=S.device)
+        kept = _c_i32()
+        tp = ctypes.c_void_p(t0.data_ptr()) if t0 is not None else None
+        _check(lib().pwh_subspace_cholqr(self._h, PRECISIONS[precision], k,
+                                         ctypes.c_void_p(Sc.data_ptr()), tp, float(drop_rel),
+                                         ctypes.c_void_p(Tr.data_ptr()), ctypes.byref(kept)))
+        return Tr, kept.value
 
     def gemm(self, A, B, C=None, conj_a=False, alpha=1.0, beta=0.0, precision="fp64"):
         """C = alpha op(A) B + beta C on the device (the eigensolver's subspace

@@ -531,16 +531,26 @@ __global__ void k_ns_rhs(const double2* __restrict__ G, int n, double2* __restri
 // rotated element straight to its position of the next round, in the other
 // buffer, so the move costs no extra pass.  After np - 1 rounds every player
 // is back where it started: at a sweep boundary position = index.  Blocks
-// are taken in tiles of kPjTile x kPjTile pairs; only tiles on or above the
-// diagonal are computed and their mirror is written (conjugated) through a
-// shared-memory transpose, so A stays exactly Hermitian and every store is a
-// contiguous run.  The rotations go to a log in index form, (s, c, p | q <<
-// 16) per pair and round, from which k_jacobi_qlog_rows forms Q afterwards.
+// are taken in tiles of kPjTile x kPjTile pairs; only the upper triangle is
+// stored: tiles on or above the diagonal are computed and each element is
+// written once, at its canonical (upper) next-round position, conjugated where
+// the move swapped row and column order (a round reads half the matrix and
+// writes half).  The rotations go to a log in index form, (s, c, p | q << 16)
+// per pair and round, from which k_jacobi_qlog_rows forms Q afterwards.
 constexpr int kPjTile = 16;
 constexpr int kPjGroup = kPjTile * kPjTile;  // threads on one tile
 constexpr int kPjTiles = 4;                  // tiles a block works on at once
 constexpr int kPjThreads = kPjGroup * kPjTiles;
 constexpr int kQlogRowsL = 8;
+
+// A stores its upper triangle only (position order, column-major): element
+// (row, col) goes to (min, max), conjugated when the move swapped their order.
+__device__ __forceinline__ void pj_store_upper(float2* A, int np, int row, int col, float2 y) {
+  if (row <= col)
+    A[(size_t)col * np + row] = y;
+  else
+    A[(size_t)row * np + col] = make_float2(y.x, -y.y);
+}
 
 // next position of the player at x (np even)
 __device__ __forceinline__ int pj_next(int x, int np) {
@@ -573,10 +583,8 @@ struct PjArgs {
 
 __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
   extern __shared__ __align__(16) unsigned char pjs[];
-  constexpr int E = 2 * kPjTile;            // elements per tile side
   float4* rot = (float4*)pjs;               // P rotations (s.x, s.y, c, -)
   const int grp = threadIdx.x / kPjGroup, gt = threadIdx.x % kPjGroup;
-  float2* mir = (float2*)(rot + a.P) + (size_t)grp * E * (E + 1);  // this group's mirror tile
   __shared__ float s_red[2][kPjThreads / 32];
   const int np = a.np, P = a.P, T = a.T, n = a.n;
   const int ntiles = T * (T + 1) / 2;
@@ -630,7 +638,6 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
       // the same number of iterations (the barriers stay uniform); the next
       // tile's operands are fetched while the current one is rotated
       for (; t0 < ntiles; t0 += stride) {
-        const bool tact = t0 + grp < ntiles;
         int In = 0, Jn = 0;
         bool actn = false;
         float4 n0 = c0, n1 = c1;
@@ -638,9 +645,11 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
         const int k = I * kPjTile + kl, l = J * kPjTile + ll;
         if (act) {
           const float4 rk = rot[k], rl = rot[l];
+          // the diagonal 2 x 2 block keeps only its upper element: a10 = conj(a01)
+          const float2 a01 = make_float2(c1.x, c1.y);
+          const float2 a10 = k == l ? make_float2(c1.x, -c1.y) : make_float2(c0.z, c0.w);
           float2 y00, y01, y10, y11;
-          jacobi_block<float>(make_float2(c0.x, c0.y), make_float2(c1.x, c1.y),
-                              make_float2(c0.z, c0.w), make_float2(c1.z, c1.w), rk.z,
+          jacobi_block<float>(make_float2(c0.x, c0.y), a01, a10, make_float2(c1.z, c1.w), rk.z,
                               make_float2(rk.x, rk.y), rl.z, make_float2(rl.x, rl.y), y00, y01,
                               y10, y11);
           if (k == l) {
@@ -648,32 +657,14 @@ __global__ void __launch_bounds__(kPjThreads) k_jacobi_pos(PjArgs a) {
             y00.y = 0.f;
             y11.y = 0.f;
             y01 = make_float2(0.f, 0.f);
-            y10 = y01;
           }
           const int i0 = pj_next(2 * k, np), i1 = pj_next(2 * k + 1, np);
           const int j0 = pj_next(2 * l, np), j1 = pj_next(2 * l + 1, np);
-          An[(size_t)j0 * np + i0] = y00;
-          An[(size_t)j0 * np + i1] = y10;
-          An[(size_t)j1 * np + i0] = y01;
-          An[(size_t)j1 * np + i1] = y11;
-          if (k != l) {
-            // mirror (row of the l side, column of the k side), conjugated
-            mir[(2 * kl) * (E + 1) + 2 * ll] = make_float2(y00.x, -y00.y);
-            mir[(2 * kl) * (E + 1) + 2 * ll + 1] = make_float2(y01.x, -y01.y);
-            mir[(2 * kl + 1) * (E + 1) + 2 * ll] = make_float2(y10.x, -y10.y);
-            mir[(2 * kl + 1) * (E + 1) + 2 * ll + 1] = make_float2(y11.x, -y11.y);
-          }
+          pj_store_upper(An, np, i0, j0, y00);
+          pj_store_upper(An, np, i0, j1, y01);
+          pj_store_upper(An, np, i1, j1, y11);
+          if (k != l) pj_store_upper(An, np, i1, j0, y10);
         }
-        __syncthreads();
-        for (int e = gt; e < E * E && tact; e += kPjGroup) {
-          const int rl = e % E, cl = e / E;  // mirror row (l side) fastest
-          const int kk = I * kPjTile + cl / 2, lk = J * kPjTile + rl / 2;
-          if (kk < P && lk < P && (I != J || cl / 2 < rl / 2)) {
-            const int row = pj_next(2 * J * kPjTile + rl, np), col = pj_next(2 * I * kPjTile + cl, np);
-            An[(size_t)col * np + row] = mir[cl * (E + 1) + rl];
-          }
-        }
-        __syncthreads();
         I = In;
         J = Jn;
         act = actn;
@@ -835,8 +826,7 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   a.tol = (float)tol;
   a.gb.count = ctl; a.gb.unused = ctl + 1; a.gb.abort = (int*)(ctl + 2);
   a.gb.err = device_error_word(s);
-  const size_t smem = (size_t)P * sizeof(float4) +
-                      (size_t)kPjTiles * (2 * kPjTile) * (2 * kPjTile + 1) * sizeof(float2);
+  const size_t smem = (size_t)P * sizeof(float4);
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_jacobi_pos, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1122,7 +1112,9 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
 void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   const size_t nn = (size_t)nmax * nmax;
   ensure(w.jac, jacobi_ws_bytes(nn, nmax));
-  ensure(w.chol, (size_t)kmax * kmax * sizeof(double2));
+  // the blocked Cholesky's scratch: two k x k complex FP64 matrices and the
+  // per-column words (the FP32 factorisation needs less)
+  ensure(w.chol, 2 * (size_t)kmax * kmax * sizeof(double2) + (size_t)kmax * 16 + 256);
   ensure(w.ns, (size_t)4 * kmax * kmax * sizeof(double2) + 64);
   if (nmax >= 64 && nmax <= 512) ensure(w.jlog, jacobi32_log_bytes(nmax, 30));
   if (nmax >= 64 && nmax <= 4096) {
@@ -1140,12 +1132,259 @@ void hermitize(double2* H, int64_t ld, int m0, int m, cudaStream_t st) {
   PWH_LAUNCH_CHECK();
 }
 
+// ---- Cholesky-QR factor over the whole GPU, for blocks too wide for one
+// block's shared memory.  Same contract as k_cholqr.  The unit-diagonal
+// Gram matrix goes to a k x k scratch (lower triangle, column-major); a
+// right-looking Cholesky runs in panels of kCbw columns: each panel on one
+// block (the pivot test and the column drops in column order, then the
+// panel's own later columns), the trailing lower triangle updated by 32 x 32
+// tiles over the whole GPU.  Dropped rows and columns become identity rows and
+// columns, so that the inverse of the kept part is the inverse of the whole:
+// the diagonal blocks are inverted first (one warp each), then every block
+// column walks down its rows (one block each),
+//     X_IJ = -X_II sum_{J <= M < I} L_IM X_MJ.
+// The same operations as the one-block kernel in another summation order.
+constexpr int kCbw = 32;
+
+// keep[j] and dinv[j] = 1/sqrt(S_jj) from the diagonal (one block, k <= 1024)
+__global__ void k_chol_diag(const double2* __restrict__ S, int k, const double* __restrict__ t0,
+                            double drop_rel, int* __restrict__ keep, double* __restrict__ dinv) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double d = S[(size_t)j * k + j].x;
+    const bool kp = d > 0.0 && (!t0 || sqrt(d) >= drop_rel * t0[j]);
+    keep[j] = kp;
+    dinv[j] = kp ? 1.0 / sqrt(d) : 0.0;
+  }
+}
+
+// A = D^-1/2 S D^-1/2 on the lower triangle (upper triangle zero)
+template <typename T>
+__global__ void k_chol_scale(const double2* __restrict__ S, int k, const double* __restrict__ dinv,
+                             cx<T>* __restrict__ A) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double2 v = S[t];
+    const double sc = dinv[i] * dinv[j];
+    A[t] = i >= j ? mk<T>((T)(v.x * sc), (T)(v.y * sc)) : mk<T>((T)0, (T)0);
+  }
+}
+
+// Columns [j0, j0 + nbp) of the factor, in order, on one block.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chol_panel(cx<T>* __restrict__ A, int k, int j0, int nbp,
+                                                     int* __restrict__ keep, double piv_tol) {
+  __shared__ T piv_s;
+  __shared__ int keep_s;
+  const int j1 = min(k, j0 + nbp);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = j0; j < j1; ++j) {
+    if (threadIdx.x == 0) {
+      const T piv = A[(size_t)j * k + j].x;
+      int kp = keep[j];
+      if (kp && !(piv > (T)piv_tol)) {
+        kp = 0;
+        keep[j] = 0;
+      }
+      keep_s = kp;
+      piv_s = kp ? sqrt(piv) : (T)0;
+      if (kp) A[(size_t)j * k + j] = mk<T>(piv_s, (T)0);
+    }
+    __syncthreads();
+    if (keep_s) {
+      const T rl = (T)1 / piv_s;
+      for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
+        A[(size_t)j * k + i] = scl<T>(A[(size_t)j * k + i], rl);
+      __syncthreads();
+      // the panel's later columns l, rows i >= l: a warp per column
+      for (int l = j + 1 + warp; l < j1; l += nw) {
+        const cx<T> alj = A[(size_t)j * k + l];
+        for (int i = l + lane; i < k; i += 32)
+          A[(size_t)l * k + i] = sub<T>(A[(size_t)l * k + i], mulc<T>(A[(size_t)j * k + i], alj));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// A[i][l] -= sum_{j0 <= j < j1, keep[j]} A[i][j] conj(A[l][j]) for j1 <= l <= i < k:
+// 32 x 32 tiles of the trailing lower triangle, 256 threads with 2 x 2 outputs.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_update(cx<T>* __restrict__ A, int k, int j0, int j1,
+                                                     const int* __restrict__ keep) {
+  const int ti = blockIdx.x, tl = blockIdx.y;
+  if (ti < tl) return;
+  const int i0 = j1 + ti * 32, l0 = j1 + tl * 32, nbp = j1 - j0;
+  __shared__ cx<T> pi[32][kCbw + 1], pl[32][kCbw + 1];
+  __shared__ int kp[kCbw];
+  for (int t = threadIdx.x; t < 32 * nbp; t += blockDim.x) {
+    const int r = t % 32, c = t / 32;
+    const int i = i0 + r, l = l0 + r;
+    pi[r][c] = i < k ? A[(size_t)(j0 + c) * k + i] : mk<T>((T)0, (T)0);
+    pl[r][c] = l < k ? A[(size_t)(j0 + c) * k + l] : mk<T>((T)0, (T)0);
+  }
+  for (int c = threadIdx.x; c < nbp; c += blockDim.x) kp[c] = keep[j0 + c];
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  cx<T> acc[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = mk<T>((T)0, (T)0);
+  for (int c = 0; c < nbp; ++c) {
+    if (!kp[c]) continue;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+        acc[a][b] = add<T>(acc[a][b], mulc<T>(pi[tx + 16 * a][c], pl[ty + 16 * b][c]));
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + tx + 16 * a, l = l0 + ty + 16 * b;
+      if (i < k && l < k && i >= l) {
+        cx<T>* e = A + (size_t)l * k + i;
+        *e = sub<T>(*e, acc[a][b]);
+      }
+    }
+}
+
+// dropped indices become identity rows and columns of the lower triangle
+template <typename T>
+__global__ void k_chol_sanitize(cx<T>* __restrict__ A, int k, const int* __restrict__ keep) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    if (i < j || (keep[i] && keep[j])) continue;
+    A[t] = mk<T>(i == j ? (T)1 : (T)0, (T)0);
+  }
+}
+
+// X_II = L_II^-1 for the diagonal 32 x 32 blocks (one warp each; indices past
+// k act as identity): lane c solves column c by forward substitution.
+template <typename T>
+__global__ void k_chol_inv_diag(const cx<T>* __restrict__ A, int k, cx<T>* __restrict__ X) {
+  __shared__ cx<T> Ls[32][33], Xs[32][33];
+  const int b0 = blockIdx.x * 32, lane = threadIdx.x;
+  for (int c = 0; c < 32; ++c) {
+    const int i = b0 + lane, j = b0 + c;
+    Ls[lane][c] = (i < k && j < k) ? A[(size_t)j * k + i] : mk<T>(i == j ? (T)1 : (T)0, (T)0);
+  }
+  __syncwarp();
+  for (int i = 0; i < 32; ++i) {
+    cx<T> acc = mk<T>(i == lane ? (T)1 : (T)0, (T)0);
+    for (int m = lane; m < i; ++m) acc = sub<T>(acc, mul<T>(Ls[i][m], Xs[m][lane]));
+    Xs[i][lane] = i < lane ? mk<T>((T)0, (T)0) : scl<T>(acc, (T)1 / Ls[i][i].x);
+  }
+  __syncwarp();
+  for (int c = 0; c < 32; ++c) {
+    const int i = b0 + lane, j = b0 + c;
+    if (i < k && j < k) X[(size_t)j * k + i] = Xs[lane][c];
+  }
+}
+
+// The off-diagonal blocks of X = L^-1, one block column J per thread block
+// (32 x 32 threads, thread (r, c) owns row r, column c of each block), rows
+// of blocks in order: Y = sum_{J <= M < I} L_IM X_MJ, then X_IJ = -X_II Y.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_chol_inv_cols(const cx<T>* __restrict__ A, int k,
+                                                        cx<T>* __restrict__ X) {
+  __shared__ cx<T> Ys[32][33];
+  const int J = blockIdx.x, nbk = (k + 31) / 32;
+  const int r = threadIdx.x % 32, c = threadIdx.x / 32;
+  const int jcol = J * 32 + c;
+  for (int I = J + 1; I < nbk; ++I) {
+    const int irow = I * 32 + r;
+    cx<T> y = mk<T>((T)0, (T)0);
+    if (irow < k && jcol < k)
+      for (int m = J * 32; m < I * 32; ++m)
+        y = add<T>(y, mul<T>(A[(size_t)m * k + irow], X[(size_t)jcol * k + m]));
+    Ys[r][c] = y;
+    __syncthreads();
+    cx<T> x = mk<T>((T)0, (T)0);
+    if (irow < k && jcol < k)
+      for (int q = 0; q < 32 && I * 32 + q < k; ++q)
+        x = sub<T>(x, mul<T>(X[(size_t)(I * 32 + q) * k + irow], Ys[q][c]));
+    if (irow < k && jcol < k) X[(size_t)jcol * k + irow] = x;
+    // this block's new X_IJ is read by the next rows of blocks
+    __syncthreads();
+  }
+}
+
+__global__ void k_chol_rank(const int* __restrict__ keep, int k, int* __restrict__ rank,
+                            int* __restrict__ kk) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int c = 0;
+    for (int j = 0; j < k; ++j) rank[j] = keep[j] ? c++ : -1;
+    *kk = c;
+  }
+}
+
+// Tr = D^-1/2 L^-H on the kept set: column rank(j), row i <= j holds
+// conj((L^-1)_ji) / sqrt(S_ii) (Tr zeroed before)
+template <typename T>
+__global__ void k_chol_out(const cx<T>* __restrict__ X, int k, const int* __restrict__ keep,
+                           const int* __restrict__ rank, const double* __restrict__ dinv,
+                           double2* __restrict__ Tr) {
+  const int64_t tot = (int64_t)k * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    if (i > j || !keep[i] || !keep[j]) continue;
+    const cx<T> v = X[(size_t)i * k + j];
+    Tr[(size_t)rank[j] * k + i] = make_double2((double)v.x * dinv[i], -(double)v.y * dinv[i]);
+  }
+}
+
+template <typename T>
+static void cholqr_blocked(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
+                           double piv_tol, double2* Tr, int* kk, cudaStream_t st) {
+  const size_t kk2 = (size_t)k * k;
+  ensure(w.chol, 2 * kk2 * sizeof(cx<T>) + (size_t)k * (2 * sizeof(int) + sizeof(double)) + 256);
+  cx<T>* A = (cx<T>*)w.chol.p;
+  cx<T>* X = A + kk2;
+  double* dinv = (double*)(X + kk2);
+  int* keep = (int*)(dinv + k);
+  int* rank = keep + k;
+  const int g = (int)std::min<int64_t>(2048, ((int64_t)kk2 + 255) / 256);
+  k_chol_diag<<<1, 1024, 0, st>>>(S, k, t0, drop_rel, keep, dinv);
+  PWH_LAUNCH_CHECK();
+  k_chol_scale<T><<<g, 256, 0, st>>>(S, k, dinv, A);
+  PWH_LAUNCH_CHECK();
+  for (int j0 = 0; j0 < k; j0 += kCbw) {
+    const int j1 = std::min(k, j0 + kCbw);
+    k_chol_panel<T><<<1, 1024, 0, st>>>(A, k, j0, j1 - j0, keep, piv_tol);
+    PWH_LAUNCH_CHECK();
+    if (j1 < k) {
+      const int nt = (k - j1 + 31) / 32;
+      k_chol_update<T><<<dim3(nt, nt), 256, 0, st>>>(A, k, j0, j1, keep);
+      PWH_LAUNCH_CHECK();
+    }
+  }
+  k_chol_sanitize<T><<<g, 256, 0, st>>>(A, k, keep);
+  PWH_LAUNCH_CHECK();
+  const int nbk = (k + 31) / 32;
+  k_chol_inv_diag<T><<<nbk, 32, 0, st>>>(A, k, X);
+  PWH_LAUNCH_CHECK();
+  k_chol_inv_cols<T><<<nbk, 1024, 0, st>>>(A, k, X);
+  PWH_LAUNCH_CHECK();
+  k_chol_rank<<<1, 32, 0, st>>>(keep, k, rank, kk);
+  PWH_LAUNCH_CHECK();
+  PWH_CUDA(cudaMemsetAsync(Tr, 0, kk2 * sizeof(double2), st));
+  k_chol_out<T><<<g, 256, 0, st>>>(X, k, keep, rank, dinv, Tr);
+  PWH_LAUNCH_CHECK();
+}
+
 template <typename T>
 static void cholqr_launch(DenseWs& w, const double2* S, int k, const double* t0, double drop_rel,
                           double piv_tol, double2* Tr, int* kk, cudaStream_t st) {
   // the packed lower triangle in shared memory up to 192 KB (k = 156 in FP64,
-  // 221 in FP32; the kernel's static arrays take the rest), else in the
-  // global scratch
+  // 221 in FP32; the kernel's static arrays take the rest) on one block, else
+  // the blocked factorisation over the whole GPU
   const size_t tri = (size_t)k * (k + 1) / 2 * sizeof(cx<T>);
   static std::once_flag attr_once;
   std::call_once(attr_once, [] {
@@ -1153,11 +1392,10 @@ static void cholqr_launch(DenseWs& w, const double2* S, int k, const double* t0,
   });
   if (tri <= 192 * 1024) {
     k_cholqr<T, true><<<1, 1024, tri, st>>>(S, k, t0, drop_rel, piv_tol, nullptr, Tr, kk);
+    PWH_LAUNCH_CHECK();
   } else {
-    ensure(w.chol, (size_t)k * k * sizeof(double2));
-    k_cholqr<T, false><<<1, 1024, 0, st>>>(S, k, t0, drop_rel, piv_tol, (cx<T>*)w.chol.p, Tr, kk);
+    cholqr_blocked<T>(w, S, k, t0, drop_rel, piv_tol, Tr, kk, st);
   }
-  PWH_LAUNCH_CHECK();
 }
 
 // ||S - I||_F^2 of the leading k x k block of S (ld lds), one block.
@@ -1246,6 +1484,30 @@ void cholqr_factor(System& s, DenseWs& w, const double2* S, int k, const double*
 }
 
 }  // namespace pwh
+
+extern "C" pwh_status pwh_subspace_cholqr(pwh_system* sys, int32_t precision, int32_t k,
+                                          const void* S, const double* t0, double drop_rel,
+                                          void* Tr, int32_t* kept) {
+  using namespace pwh;
+  return guarded([&] {
+    PWH_CHECK_ARG(sys && S && Tr && kept, "null argument");
+    PWH_CHECK_ARG(k >= 1 && k <= 1024, "k out of range [1, 1024]");
+    PWH_CHECK_ARG(precision == PWH_FP64 || precision == PWH_MIXED, "unknown precision");
+    PWH_CHECK_ARG(std::isfinite(drop_rel) && drop_rel >= 0.0, "drop_rel must be >= 0");
+    System& s = sys->s;
+    DenseWs w;
+    int* dk = nullptr;
+    PWH_CUDA(cudaMalloc((void**)&dk, sizeof(int)));
+    cholqr_factor(s, w, (const double2*)S, k, t0, drop_rel, (double2*)Tr, dk, s.stream,
+                  precision != PWH_FP64);
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, dk, sizeof(int), cudaMemcpyDeviceToHost, s.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+    cudaFree(dk);
+    PWH_CUDA(e);
+    *kept = h;
+  });
+}
 
 extern "C" pwh_status pwh_subspace_eigh(pwh_system* sys, int32_t n, const void* H, int64_t ldh,
                                         int32_t nk, double* theta, void* C, void* Q, int64_t ldq,

@@ -64,7 +64,7 @@ struct TcArgs {
   // takes kb_per_split blocks of products 1.., the others kps0 blocks of
   // product 0
   int oz;
-  unsigned char oz_a[32], oz_b[32];
+  unsigned char oz_a[64], oz_b[64];
   int z_rest, kps0;
 };
 
@@ -584,18 +584,21 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, float2* 
 // al. (products of integer slices summed exactly).  Each real row r of an
 // operand (after the complex interleaving of the projector GEMM above) gets
 // the exponent e_r with max|x_r| < 2^e_r and is written as
-//     x = 2^e_r sum_{s < OZ_S} a_s 2^(-7 - 8 s),   a_s integers, |a_s| <= 128,
-// which BF16 holds exactly (balanced base-256 digits of the row-scaled value
-// as an integer).  A product a_s b_t is at most 2^14 and a sum of
-// 1024 of them at most 2^24, so every FP32 partial of a 1024-wide K chunk is an
-// exact integer.  The partials of the pairs with s + t <= OZ_G are summed in
-// int64 by weight 2^(-8(s+t)) and scaled once in FP64.  Dropped terms and
-// slice truncation are below 2^-54 of max|a| max|b| per elementary product.
-constexpr int OZ_S = 7;
+//     x = 2^e_r sum_{s < OZ_S} a_s 2^(-6 - 7 s),   a_s integers, |a_s| <= 64,
+// which BF16 holds exactly (balanced base-128 digits of the row-scaled value
+// as an integer).  A product a_s b_t is at most 2^12 and a sum of 4096 of
+// them at most 2^24, so every FP32 partial of a 4096-wide K chunk is an exact
+// integer (base-128 digits take one slice more than base-256 ones, 36 pairs
+// instead of 28, and write a third of the partials).  The partials of the
+// pairs with s + t <= OZ_G are summed in int64 by weight 2^(-7(s+t)) and
+// scaled once in FP64.  Dropped terms and slice truncation are below 2^-52 of
+// max|a| max|b| per elementary product.
+constexpr int OZ_S = 8;
 constexpr int OZ_G = OZ_S - 1;
 constexpr int OZ_PAIRS = (OZ_S * (OZ_S + 1)) / 2;  // pairs with s + t <= OZ_G
-static_assert(OZ_PAIRS <= 32, "pair table");
-__constant__ unsigned char c_oz_g[32];            // s + t of pair p
+constexpr int OZ_CHUNK_KB = 64;                    // 64-wide K blocks per exact partial
+static_assert(OZ_PAIRS <= 64, "pair table");
+__constant__ unsigned char c_oz_g[64];            // s + t of pair p
 
 // Slicing works on the IEEE bit patterns with integer arithmetic only (the
 // FP64 pipe of this GPU would make it the slowest step).  |x| as an unsigned
@@ -609,8 +612,8 @@ __device__ __forceinline__ int oz_exp_of_key(unsigned long long k) {
   const int eb = (int)(k >> 52);
   return eb ? eb - 1022 : -1021;  // frexp exponent; subnormals lie below 2^-1022
 }
-// The OZ_S balanced base-256 digits of X = round(x 2^(55 - e)), |X| < 2^55:
-// x = 2^e sum_s a_s 2^(-7 - 8 s) up to 2^(e - 56), |a_s| <= 128, as BF16.
+// The OZ_S balanced base-128 digits of X = round(x 2^(55 - e)), |X| < 2^55:
+// x = 2^e sum_s a_s 2^(-6 - 7 s) up to 2^(e - 56), |a_s| <= 64, as BF16.
 __device__ __forceinline__ void oz_split(double x, int e, __nv_bfloat16* a) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int eb = (int)((bits >> 52) & 0x7ff);
@@ -623,9 +626,9 @@ __device__ __forceinline__ void oz_split(double x, int e, __nv_bfloat16* a) {
   if (bits >> 63) X = -X;
 #pragma unroll
   for (int s = OZ_S - 1; s > 0; --s) {
-    const int d = (int)((X + 128) & 255) - 128;
+    const int d = (int)((X + 64) & 127) - 64;
     a[s] = __int2bfloat16_rn(d);
-    X = (X - d) >> 8;
+    X = (X - d) >> 7;
   }
   a[0] = __int2bfloat16_rn((int)X);
 }
@@ -774,17 +777,18 @@ __global__ void k_oz_slice_b2(const double2* __restrict__ B, int64_t ld, int K, 
 }
 
 // Exact accumulation of the integer partials of one real output: weights
-// 2^(-8g) folded into hi (g <= 2) and lo (g >= 3); value
-// 2^(e - 14) (hi 2^-16 + lo 2^-(8 OZ_G)).
+// 2^(-7g) folded into hi (g <= 3) and lo (g >= 4); value
+// 2^(e - 12) (hi 2^-21 + lo 2^-(7 OZ_G)).  At 161,235-wide K (40 chunks) both
+// stay below 2^53.
 struct OzAcc {
   long long hi = 0, lo = 0;
-  // i: a sum of exact integer partials (each |v| <= 2^24) of weight 2^(-8g)
+  // i: a sum of exact integer partials (each |v| <= 2^24) of weight 2^(-7g)
   __device__ __forceinline__ void add_int(long long i, int g) {
-    if (g <= 2) hi += i * (1ll << (8 * (2 - g)));
-    else lo += i * (1ll << (8 * (OZ_G - g)));
+    if (g <= 3) hi += i * (1ll << (7 * (3 - g)));
+    else lo += i * (1ll << (7 * (OZ_G - g)));
   }
   __device__ __forceinline__ double value(int e) const {
-    return ldexp((double)hi, e - 14 - 16) + ldexp((double)lo, e - 14 - 8 * OZ_G);
+    return ldexp((double)hi, e - 12 - 21) + ldexp((double)lo, e - 12 - 7 * OZ_G);
   }
 };
 
@@ -870,7 +874,7 @@ __global__ void k_oz_reduce_nn(const float* __restrict__ part, int nz, int nchun
   const int npair = nz / nchunk;
   if (nchunk == 1) {
     // one chunk: every pair's partial in flight together
-#pragma unroll 7
+#pragma unroll 9
     for (int pr = 0; pr < OZ_PAIRS; ++pr) {
       qr.add_int(__float2int_rn(p0[(size_t)pr * plane]), c_oz_g[pr]);
       qi.add_int(__float2int_rn(p1[(size_t)pr * plane]), c_oz_g[pr]);
@@ -919,20 +923,20 @@ static OzGeom oz_geom(bool conjA, int M, int N, int K) {
   const int64_t Kr = conjA ? K : 2 * (int64_t)K;
   g.seg = round_up(std::max<int64_t>(Kr, 1), TC_BK);
   g.kb_seg = (int)(g.seg / TC_BK);
-  // K blocks per exact partial: at most 16 (1024 wide) and dividing kb_seg;
-  // pad the segment to whole 16-block chunks when that costs little, else
-  // take a divisor of at least 8
+  // K blocks per exact partial: at most OZ_CHUNK_KB (4096 wide) and dividing
+  // kb_seg; pad the segment to whole chunks when that costs little, else take
+  // a divisor of at least half a chunk
   g.kbps = g.kb_seg;
-  if (g.kb_seg > 16) {
-    const int pad16 = (g.kb_seg + 15) / 16 * 16;
+  if (g.kb_seg > OZ_CHUNK_KB) {
+    const int padc = (g.kb_seg + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB * OZ_CHUNK_KB;
     g.kbps = 0;
-    if ((pad16 - g.kb_seg) * 16 > g.kb_seg)
-      for (int d = 16; d >= 8 && !g.kbps; --d)
+    if ((padc - g.kb_seg) * 16 > g.kb_seg)
+      for (int d = OZ_CHUNK_KB; d >= OZ_CHUNK_KB / 2 && !g.kbps; --d)
         if (g.kb_seg % d == 0) g.kbps = d;
     if (!g.kbps) {
-      g.kb_seg = pad16;
+      g.kb_seg = padc;
       g.seg = (int64_t)g.kb_seg * TC_BK;
-      g.kbps = 16;
+      g.kbps = OZ_CHUNK_KB;
     }
   }
   g.nchunk = g.kb_seg / g.kbps;
@@ -945,7 +949,7 @@ static OzGeom oz_geom(bool conjA, int M, int N, int K) {
   return g;
 }
 
-// The exact partials (28 per K chunk, FP32, of the whole real output) are
+// The exact partials (OZ_PAIRS per K chunk, FP32, of the whole real output) are
 // bounded.  A product over many chunks first runs as K segments of whole
 // chunks, each added into C in FP64 (one more rounding per segment, no
 // operand sliced twice); a segment that still does not fit runs as pieces of
@@ -960,18 +964,18 @@ struct OzSplit {
 };
 static OzSplit oz_split_of(bool conjA, int M, int N, int K) {
   OzSplit sp{K, M >= N, M >= N ? M : N};
-  // at most 2048 chunks a segment (28 x chunks partials along grid z): 2^20
-  // real K, in chunks of at least 512 (a divisor of at least 8 blocks)
+  // at most 2^20 real K a segment (at most 512 chunks, OZ_PAIRS x chunks
+  // partials along grid z)
   const int kmax = conjA ? (1 << 20) : (1 << 19);
   if (K > kmax) sp.kseg = kmax;
   const OzGeom g = oz_geom(conjA, M, N, sp.kseg);
   if (g.bytes_p <= kOzPartCap) return sp;
   const size_t per_chunk = g.bytes_p / (size_t)g.nchunk;
   if (g.nchunk > 1) {
-    // whole 1024-wide real chunks per segment (1024 complex K for A^H B,
-    // 512 for A B, whose real K is 2K)
+    // whole 4096-wide real chunks per segment (4096 complex K for A^H B,
+    // 2048 for A B, whose real K is 2K)
     const int64_t c = std::max<int64_t>(1, (int64_t)(kOzPartCap / per_chunk));
-    const int64_t kc = conjA ? 1024 : 512;
+    const int64_t kc = conjA ? 64 * OZ_CHUNK_KB : 32 * OZ_CHUNK_KB;
     if (c < g.nchunk) sp.kseg = (int)std::min<int64_t>(sp.kseg, c * kc);
   }
   const OzGeom gs = oz_geom(conjA, M, N, sp.kseg);
@@ -1025,9 +1029,9 @@ static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 al
                           double2 beta, double2* C, int64_t ldc, cudaStream_t st,
                           const double* rowscale) {
   static std::once_flag once;
-  static unsigned char pa[32], pb[32];
+  static unsigned char pa[64], pb[64];
   std::call_once(once, [] {
-    unsigned char g[32] = {};
+    unsigned char g[64] = {};
     int p = 0;
     for (int gg = 0; gg <= OZ_G; ++gg)
       for (int sa = 0; sa <= gg; ++sa) {

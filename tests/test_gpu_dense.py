@@ -170,3 +170,47 @@ def test_subspace_eigh_degenerate_davidson_sequence(env):
             assert np.abs(V.conj().T @ V - np.eye(nk)).max() <= 1e-12
         s.subspace_eigh(Ht, nk, Q=Q, warm=warm)
     s.sync()
+
+
+# ------------------------------------------------------------ Cholesky-QR
+@pytest.mark.parametrize("k", [100, 200, 300, 545, 1024])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_subspace_cholqr_paths(env, k, precision):
+    """The orthonormalisation factor on one block (k <= 156 FP64 / 221 FP32)
+    and blocked over the whole GPU (above), with one column below the drop
+    threshold (and, in FP64, two dependent columns): the kept count is the rank,
+    T Tr is orthonormal, and without drops Tr equals D^-1/2 L^-H from LAPACK's
+    Cholesky of the unit-diagonal Gram matrix."""
+    torch, s = env
+    rng = np.random.default_rng(k)
+    n = 2 * k + 400
+    T = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    # exactly dependent columns: dropped by the FP64 pivot test (in FP32 the
+    # rounding of a late pivot can exceed its threshold, so only the norm-based
+    # drop is required there)
+    dep = [(17, 3), (k - 5, 40)] if precision == "fp64" else []
+    for c, src in dep:
+        T[:, c] = (0.3 - 0.7j) * T[:, src] + 1e-15 * rng.standard_normal(n)
+    T[:, 11] *= 1e-12
+    t0 = np.linalg.norm(T, axis=0)
+    t0[11] = 1.0
+    S = T.conj().T @ T
+    Tr, kept = s.cholqr(torch.from_numpy(S.T.copy()).cuda(), torch.from_numpy(t0).cuda(),
+                        1e-10, precision)
+    assert kept == k - 1 - len(dep)
+    Q = T @ Tr.cpu().numpy().T[:, :kept]
+    # FP32: forward error about kappa sqrt(k) eps32 (kappa of the Gram matrix
+    # up to 22 here): 1e-3
+    tol = 1e-10 if precision == "fp64" else 1e-3
+    assert np.abs(Q.conj().T @ Q - np.eye(kept)).max() <= tol
+    assert np.abs(Tr.cpu().numpy().T[:, kept:]).max() == 0.0
+    # no drops: the factor itself against LAPACK
+    T2 = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    S2 = T2.conj().T @ T2
+    Tr2, kept2 = s.cholqr(torch.from_numpy(S2.T.copy()).cuda(), None, 0.0, precision)
+    assert kept2 == k
+    dinv = 1.0 / np.sqrt(S2.diagonal().real)
+    L = np.linalg.cholesky(S2 * dinv[:, None] * dinv[None, :])
+    ref = dinv[:, None] * np.linalg.inv(L).conj().T
+    err = np.abs(Tr2.cpu().numpy().T - ref).max() / np.abs(ref).max()
+    assert err <= (1e-11 if precision == "fp64" else 1e-3), err
