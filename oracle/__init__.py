@@ -23,6 +23,9 @@ eye against the method's definitions:
 * ``exx``         exact (Fock) exchange by pair densities and the Fourier-space
                   Poisson solution (FFT route and a reciprocal-space sum), and
                   its adaptively compressed form (ACE)
+* ``overlap``     the generalised eigenproblem H x = e S x of ultrasoft / PAW
+                  projectors, S = 1 + sum_ij |beta_i> q_ij <beta_j|, and the
+                  separable S^-1/2
 
 Pins (``tests/test_oracle_*.py``, run with ``-m "not gpu"``) tie each function
 to closed forms, invariants, brute force or library routines, never to itself.
