@@ -48,7 +48,10 @@ def test_single_projector_closed_forms():
 
 
 def test_separable_inverse_square_root_matches_dense():
-    cell, b, v, beta, D = case(seed=2, a=7.0, natoms=3, ecut_ry=10.0, lmax=1)
+    # a shifted k: the projector Gram matrix is complex (at k = 0 it is real)
+    cell, b, v, beta, D = case(seed=2, a=7.0, natoms=3, ecut_ry=10.0, lmax=1, k=(0.25, -0.1, 0.3))
+    G = np.conj(beta) @ beta.T
+    assert np.abs(G.imag).max() > 1e-3 * np.abs(G).max()
     for full in (False, True):
         q = q_matrix(beta.shape[0], 3, full)
         S = oo.dense_s(beta, q, b.npw)
@@ -62,7 +65,7 @@ def test_separable_inverse_square_root_matches_dense():
 
 
 def test_generalised_pairs():
-    cell, b, v, beta, D = case(seed=3, a=7.5, natoms=3, ecut_ry=10.0, lmax=1)
+    cell, b, v, beta, D = case(seed=3, a=7.5, natoms=3, ecut_ry=10.0, lmax=1, k=(0.1, 0.2, -0.3))
     H = oh.dense_h(b, v, beta, D)
     q = q_matrix(beta.shape[0], 5, True)
     S = oo.dense_s(beta, q, b.npw)
