@@ -501,13 +501,26 @@ def run_medium(pwh, syn, torch):
     eig = ts[-1][1][0]
     t64, (eig64, st64, _) = timed(torch, stream, lambda: solve(False))
     hp = hpsi_only(torch, s, psi0)
+    # the generalised problem H x = e S x of ultrasoft / PAW projectors:
+    # S = 1 + sum_i |beta_i> q_i <beta_i|, q_i ~ U(0.1, 0.8) (seeded)
+    q = np.random.default_rng(8).uniform(0.1, 0.8, beta.shape[0])
+    t_set, _ = timed(torch, stream, lambda: s.set_overlap(q))
+    solve(True)
+    t_gen, (eig_g, st_g, status_g) = timed(torch, stream, lambda: solve(True))
+    assert status_g == 0
+    s.set_overlap(None)
     s.close()
     return {"workload": f"medium: a=20 bohr, 64 atoms, 40 Ry, npw={s.npw}, 90^3, 576 projectors, "
                         f"{nb} bands", "time_to_1e-8_s": {"mixed": tmix, "fp64": t64},
             "fp64_over_mixed": t64 / tmix, "iters": {"mixed": ts[-1][1][1]["iters"],
                                                      "fp64": st64["iters"]},
             "max_abs_dlambda_mixed_vs_fp64_ha": float(np.abs(eig - eig64).max()),
-            "hpsi_only": hp}
+            "hpsi_only": hp,
+            "generalised": {"problem": "H x = e S x, S = 1 + sum_i |beta_i> q_i <beta_i|, "
+                                       "q_i ~ U(0.1, 0.8), mixed + Jacobi-Davidson",
+                            "set_overlap_s": t_set, "time_to_1e-8_s": t_gen,
+                            "iters": st_g["iters"],
+                            "lowest_eig_shift_ha": float(eig_g[0] - eig[0])}}
 
 
 def run_ace(pwh, syn, torch, nocc=ACE_NOCC):

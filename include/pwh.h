@@ -286,6 +286,34 @@ pwh_status pwh_davidson_solve_host(pwh_system* sys, const pwh_davidson_opts* opt
 pwh_status pwh_davidson_solve_gamma(pwh_system* sys, const pwh_davidson_opts* opts, void* psi_io,
                                     int64_t ld_psi, double* eig, pwh_davidson_stats* stats);
 
+/* ---------------------------------------------------- overlap operator S --
+ * Ultrasoft / PAW projectors make the Kohn-Sham problem generalised,
+ * H x = e S x (the S of Eq. pauli_ks, Sec. "Fully relativistic projector
+ * augmented-wave method").  The separable form over the projectors of
+ * pwh_set_projectors is used:
+ *   S = 1 + sum_ij |beta_i> q_ij <beta_j|,   q Hermitian, S positive definite. */
+
+/* Set q: nproj real diagonal values (q_is_diag = 1) or an nproj x nproj
+ * complex128 Hermitian matrix (column-major; its Hermitian part is used), on the
+ * host or the device (on_device).  Builds, once, the separable inverse square
+ * root S^-1/2 = 1 + beta K beta^H (FP64: beta^H beta and two device Jacobi
+ * eigendecompositions of nproj x nproj matrices, GEMMs).  From then on
+ * pwh_davidson_solve and pwh_batch_davidson_solve solve H x = e S x through the
+ * Loewdin form S^-1/2 H S^-1/2 (same eigenvalues; the eigenvectors returned are
+ * S-orthonormal; the reported residual max ||H' phi - e phi|| is that of the
+ * transformed problem, and ||H x - e S x|| <= ||S^1/2|| times it).  pwh_apply_h
+ * keeps applying H.  q = NULL removes the overlap; pwh_set_projectors removes
+ * it too.  Synchronous.  Errors: PWH_ERR_STATE (no projectors), PWH_ERR_ARG
+ * (S not positive definite), PWH_ERR_OOM, PWH_ERR_CUDA.  The real-band solver
+ * (pwh_davidson_solve_gamma) refuses a system with an overlap (PWH_ERR_ARG). */
+pwh_status pwh_set_overlap(pwh_system* sys, const void* q, int32_t q_is_diag, int32_t on_device);
+
+/* spsi = S psi for nb bands (the identity when no overlap is set), FP64.
+ * psi, spsi: DEVICE complex128, public order, column-major, ld >= npw, not
+ * overlapping.  Asynchronous on the system's stream. */
+pwh_status pwh_apply_s(pwh_system* sys, int32_t nb, const void* psi, int64_t ld_psi, void* spsi,
+                       int64_t ld_spsi);
+
 /* ------------------------------------------------ exact exchange and ACE --
  * The Fock exchange operator of Eq. Vx (Sec. "Advanced implementation of exact
  * (Fock) exchange and hybrid functionals"), Hartree units:

@@ -105,6 +105,8 @@ SIGNATURES = {
     "pwh_davidson_solve_gamma": (_c_i32, [_c_p, ctypes.POINTER(DavidsonOpts), _c_p, _c_i64, _c_p,
                                           ctypes.POINTER(DavidsonStats)]),
     "pwh_get_davidson_trace": (_c_i32, [_c_p, _c_i32, _c_p, ctypes.POINTER(_c_i32)]),
+    "pwh_set_overlap": (_c_i32, [_c_p, _c_p, _c_i32, _c_i32]),
+    "pwh_apply_s": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i64]),
     "pwh_exx_apply": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_i32, _c_p, _c_i64, _c_p,
                                _c_i64]),
     "pwh_set_ace": (_c_i32, [_c_p, _c_i32, _c_p, _c_i64, _c_p, _c_d, ctypes.POINTER(_c_i32)]),
@@ -396,6 +398,32 @@ class System:
         _check(lib().pwh_apply_h_host(self._h, int(psi.shape[0]), psi.ctypes.data_as(_c_p),
                                       hpsi.ctypes.data_as(_c_p)))
         return hpsi
+
+    # ------------------------------------------------------------- overlap
+    def set_overlap(self, q=None):
+        """S = 1 + sum_ij |beta_i> q_ij <beta_j| over the projectors: q a host
+        array of nproj reals (diagonal) or an (nproj, nproj) complex matrix;
+        None removes it.  The eigensolvers then solve H x = e S x."""
+        if q is None:
+            _check(lib().pwh_set_overlap(self._h, None, 0, 0))
+            return
+        q = np.asarray(q)
+        if q.ndim == 1:
+            d = np.ascontiguousarray(q, dtype=np.float64)
+            _check(lib().pwh_set_overlap(self._h, d.ctypes.data_as(_c_p), 1, 0))
+        else:
+            m = np.asfortranarray(q, dtype=np.complex128)
+            _check(lib().pwh_set_overlap(self._h, m.ctypes.data_as(_c_p), 0, 0))
+
+    def apply_s(self, psi, spsi=None):
+        """spsi = S psi on the device; psi (nb, npw) complex128 CUDA tensor."""
+        torch = _torch()
+        if spsi is None:
+            spsi = torch.empty_like(psi, memory_format=torch.contiguous_format)
+        p, ldp = _band_ptr(psi, self.npw)
+        h, ldh = _band_ptr(spsi, self.npw)
+        _check(lib().pwh_apply_s(self._h, int(psi.shape[0]), p, ldp, h, ldh))
+        return spsi
 
     # ------------------------------------------------------- exact exchange
     def exx_apply(self, psi_occ, occ, phi, out=None):

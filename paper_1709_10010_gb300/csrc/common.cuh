@@ -251,6 +251,15 @@ struct System {
   int ace_real = -1;
   DevBuf<char> ws_ace;              // zeta^H psi of the ACE term (ace_n x nb)
 
+  // overlap operator S = 1 + sum_ij |beta_i> q_ij <beta_j| of ultrasoft / PAW
+  // projectors (overlap.cu): q and the separable S^-1/2 = 1 + beta K beta^H
+  // (both nproj x nproj, complex FP64, column-major); with an overlap set the
+  // eigensolvers solve H x = e S x
+  bool have_overlap = false;
+  double2* d_q = nullptr;
+  double2* d_ksq = nullptr;
+  DevBuf<char> ws_ov;               // products of the S and S^-1/2 applications
+
   // workspaces (grown on demand)
   DevBuf<char> ws_fft, ws_psi, ws_hpsi, ws_becp, ws_split, ws_host;
   DevBuf<char> ws_vnl;              // FP32 nonlocal term of the mixed H (npw x nb)

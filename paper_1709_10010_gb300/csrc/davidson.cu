@@ -41,6 +41,7 @@ struct DavWs {
   DevBuf<char> vec;    // V, HV (npw x mmax each), X, HX, R, Tw (npw x nb each)
   DevBuf<char> cg;     // Jacobi-Davidson PCG: r, z, p, q (npw x nb each), scalars
   DevBuf<char> mlp;    // learned-preconditioner factors (k x nshell)
+  DevBuf<char> ovt;    // S^-1/2 psi of the generalised problem (npw x nb)
   DevBuf<char> small;  // Hs, C, theta, rn, eref, t0, Wc, S, Tr, idx, kk
   DenseWs dense;
   // plane-wave space of the current solve: the full sphere in the internal
@@ -59,6 +60,7 @@ struct DavWs {
     if (vec.p) cudaFree(vec.p);
     if (cg.p) cudaFree(cg.p);
     if (mlp.p) cudaFree(mlp.p);
+    if (ovt.p) cudaFree(ovt.p);
     if (small.p) cudaFree(small.p);
     if (h_rn) cudaFreeHost(h_rn);
     if (h_idx) cudaFreeHost(h_idx);
@@ -357,12 +359,22 @@ struct Layout {
   int *idx, *kk;
 };
 
-// H on k bands of the solve's space (see DavWs).
+void overlap_inv_sqrt(System& s, int nb, const double2* in, int64_t ldi, double2* out,
+                      int64_t ldo, int prec);  // overlap.cu
+
+// H on k bands of the solve's space (see DavWs); with an overlap operator the
+// Loewdin form S^-1/2 H S^-1/2 of the generalised problem.
 static void space_apply(System& s, DavWs& w, int k, const double2* in, double2* out, int prec) {
-  if (w.gamma)
+  if (w.gamma) {
     gamma_apply(s, k, in, w.n, out, w.n, prec, true);
-  else
+  } else if (s.have_overlap) {
+    double2* t = (double2*)w.ovt.p;
+    overlap_inv_sqrt(s, k, in, w.n, t, w.n, prec);
+    apply_internal(s, k, t, w.n, out, w.n, prec);
+    overlap_inv_sqrt(s, k, out, w.n, out, w.n, prec);
+  } else {
     apply_internal(s, k, in, w.n, out, w.n, prec);
+  }
 }
 
 // P v = v - X (X^H v) on k columns (FP32 arithmetic, FP64 storage); W: nb x k.
@@ -654,6 +666,16 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
       x3_reserve(s, false, (int)s.npw, nb, s.ace_n);
     }
   }
+  if (s.have_overlap) {
+    if (gamma) throw Error{PWH_ERR_ARG, "the real-band solver takes no overlap operator"};
+    // S^-1/2 psi, and the projector products of the S^-1/2 applications
+    ensure(w.ovt, (size_t)npw * nb * sizeof(double2));
+    ensure(s.ws_ov, (size_t)2 * s.nproj * nb * sizeof(double2));
+    if (o.mixed) {
+      x3_reserve(s, true, s.nproj, nb, (int)npw);
+      x3_reserve(s, false, (int)npw, nb, s.nproj);
+    }
+  }
   if (gamma) {
     // the complex full-sphere bands that carry pairs of real ones
     ensure(s.ws_psi, (size_t)s.npw * ((nb + 1) / 2) * sizeof(double2));
@@ -893,6 +915,11 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     k_copy_cols<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, psi, ldpsi, npw, nbt);
     PWH_LAUNCH_CHECK();
     k_scale_row<<<(nbt + 255) / 256, 256, 0, st>>>(psi, ldpsi, nbt, s.gam_g0, 1.4142135623730951);
+    PWH_LAUNCH_CHECK();
+  } else if (s.have_overlap) {
+    // eigenvectors of H x = e S x: x = S^-1/2 phi (S-orthonormal)
+    overlap_inv_sqrt(s, nbt, L.X, npw, L.R, npw, PWH_FP64);
+    k_perm_out<<<grid1d(npw * nbt), 256, 0, st>>>(L.R, npw, npw, nbt, s.d_int_to_pub, psi, ldpsi);
     PWH_LAUNCH_CHECK();
   } else {
     k_perm_out<<<grid1d(npw * nbt), 256, 0, st>>>(L.X, npw, npw, nbt, s.d_int_to_pub, psi, ldpsi);

@@ -1032,12 +1032,14 @@ static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 al
   static unsigned char pa[64], pb[64];
   std::call_once(once, [] {
     unsigned char g[64] = {};
+    // pairs by A slice, then B slice: consecutive grid slices share an A
+    // slice, so one K chunk needs one A slice and its B slices in L2 at a time
     int p = 0;
-    for (int gg = 0; gg <= OZ_G; ++gg)
-      for (int sa = 0; sa <= gg; ++sa) {
+    for (int sa = 0; sa <= OZ_G; ++sa)
+      for (int sb = 0; sa + sb <= OZ_G; ++sb) {
         pa[p] = (unsigned char)sa;
-        pb[p] = (unsigned char)(gg - sa);
-        g[p] = (unsigned char)gg;
+        pb[p] = (unsigned char)sb;
+        g[p] = (unsigned char)(sa + sb);
         ++p;
       }
     cudaMemcpyToSymbol(c_oz_g, g, sizeof(g));

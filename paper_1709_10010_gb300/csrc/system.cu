@@ -89,7 +89,7 @@ System::~System() {
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_vnl.p, ws_grid.p, ws_tune.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
                   ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp, d_gam_pos,
-                  d_boxidx, d_kern, d_ace, ws_ace.p};
+                  d_boxidx, d_kern, d_ace, ws_ace.p, d_q, d_ksq, ws_ov.p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -451,6 +451,12 @@ pwh_status pwh_set_projectors(pwh_system* sys, int32_t nproj, const void* beta,
     }
     s.nproj = 0;
     s.gam_proj_ok = -1;
+    // an overlap belongs to the projectors it was set with
+    for (double2** p : {&s.d_q, &s.d_ksq}) {
+      if (*p) cudaFree(*p);
+      *p = nullptr;
+    }
+    s.have_overlap = false;
     if (nproj == 0) return;
     PWH_CHECK_ARG(beta && D, "null beta or D");
     size_t nb = (size_t)s.npw * nproj;
