@@ -628,7 +628,19 @@ FAMILY_BOUND = {
 # (dram__bytes_read.sum + dram__bytes_write.sum per launch divided by the
 # units that launch processed; summaries and commands under profiles/).
 # Families missing here report traffic null.
-TRAFFIC_PER_UNIT = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) behind the
+# roofline, from ncu captures summarised under profiles/: per launch of a
+# family as it runs in the large solve (the capture made inside the same
+# command), or per counted flop of one representative product, scaled by the
+# launch's flops.  A family whose kernels changed after the capture is absent
+# (traffic null).
+TRAFFIC_PER_LAUNCH = {}   # family -> bytes per launch
+TRAFFIC_PER_FLOP = {      # family -> bytes per counted flop
+    # one 1088 x 544 x 16,384 FP64-equivalent product (bench.py --gemm
+    # 1088,544,16384,fp64,1): 6.16 GB of DRAM traffic over its six kernels
+    # for 2.79e12 counted tensor flops (profiles/oz_gemm_fp64_conj_1088x544x16384.md)
+    "zgemm_fp64_tc": 6.1555e9 / 2.7928e12,
+}
 
 
 def family_roofline(fam, d, s=None):
@@ -651,8 +663,10 @@ def family_roofline(fam, d, s=None):
         peak, unit, psrc = FP64_ALU_TFLOPS, "TFLOP/s", "nominal FP64 rate"
         achieved = work / sec / 1e12
     traffic = None
-    if fam in TRAFFIC_PER_UNIT and d.get("units"):
-        traffic = TRAFFIC_PER_UNIT[fam] * d["units"] / d["launches"]
+    if fam in TRAFFIC_PER_LAUNCH:
+        traffic = TRAFFIC_PER_LAUNCH[fam]
+    elif fam in TRAFFIC_PER_FLOP and work:
+        traffic = TRAFFIC_PER_FLOP[fam] * work
     return {"kernel": fam, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": (achieved / peak) if (peak and work) else None, "traffic": traffic,
             "avg_launch_ms": d["ms"] / d["launches"], "peak_source": psrc}

@@ -536,7 +536,7 @@ __global__ void k_ns_rhs(const double2* __restrict__ G, int n, double2* __restri
 // written once, at its canonical (upper) next-round position, conjugated where
 // the move swapped row and column order (a round reads half the matrix and
 // writes half).  The rotations go to a log in index form, (s, c, p | q << 16)
-// per pair and round, from which k_jacobi_qlog_warp forms Q afterwards.
+// per pair and round, from which k_jacobi_qlog_rows forms Q afterwards.
 constexpr int kPjTile = 16;
 constexpr int kPjGroup = kPjTile * kPjTile;  // threads on one tile
 constexpr int kPjTiles = 4;                  // tiles a block works on at once
@@ -731,63 +731,58 @@ __global__ void k_to_pos32(const double2* __restrict__ A, int64_t lda, int n, in
   }
 }
 
-// Q from the log of k_jacobi_pos, one warp per row of Q: the row lives in
-// shared memory and takes every round in order; the pairs of a round touch
-// disjoint elements, so the lanes apply them (P / 32 each, their log entries
-// loaded together) with no block-wide barrier, only __syncwarp between rounds.
-// W = blockDim / 32 rows a block; the rows are written back as W-wide runs.
-__global__ void __launch_bounds__(512) k_jacobi_qlog_warp(const float4* __restrict__ log,
-                                                          const int* __restrict__ info, int n,
-                                                          int P, double2* __restrict__ Q,
-                                                          int64_t ldq) {
-  extern __shared__ __align__(16) unsigned char qws[];
-  float2* qs = (float2*)qws;  // [W][n]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
-  const int row0 = blockIdx.x * W, row = row0 + warp;
-  float2* qr = qs + (size_t)warp * n;
-  for (int c = lane; c < n; c += 32) qr[c] = make_float2(row == c ? 1.f : 0.f, 0.f);
-  __syncwarp();
-  const int R = row < n ? info[2] : 0;
+// Q = J_0 J_1 ... J_{R-1} from the log of k_jacobi_pos (R = info[2]): the rows
+// of Q evolve independently, `rows` rows a block in shared memory (starting
+// as rows of the identity), every round applied to them in order.  Thread t
+// owns pairs t and t + blockDim (P <= 2 blockDim) and applies them to every
+// row of the block; the next round's log entries are fetched before the
+// barrier that closes the current round.
+__global__ void __launch_bounds__(1024) k_jacobi_qlog_rows(const float4* __restrict__ log,
+                                                           const int* __restrict__ info, int n,
+                                                           int P, int rows, double2* __restrict__ Q,
+                                                           int64_t ldq) {
+  extern __shared__ __align__(16) unsigned char qrs[];
+  float2* qs = (float2*)qrs;  // [rows][n]
+  const int i0 = blockIdx.x * rows;
+  const int nr = min(rows, n - i0);
+  for (int t = threadIdx.x; t < rows * n; t += blockDim.x) {
+    const int r = t / n, c = t - r * n;
+    qs[t] = make_float2((r < nr && i0 + r == c) ? 1.f : 0.f, 0.f);
+  }
+  const int R = info[2];
+  const int k0 = threadIdx.x, k1 = threadIdx.x + blockDim.x;
+  const float4 idle = make_float4(0.f, 0.f, 1.f, __int_as_float(0xffff | (0xffff << 16)));
+  float4 c0 = (R > 0 && k0 < P) ? log[k0] : idle, c1 = (R > 0 && k1 < P) ? log[k1] : idle;
+  __syncthreads();
   for (int rd = 0; rd < R; ++rd) {
-    const float4* lg = log + (size_t)rd * P;
-    int k = lane;
-    for (; k + 96 < P; k += 128) {
-      float4 e[4];
+    const float4 u0 = c0, u1 = c1;
+    if (rd + 1 < R) {
+      const float4* nx = log + (size_t)(rd + 1) * P;
+      c0 = k0 < P ? __ldg(nx + k0) : idle;
+      c1 = k1 < P ? __ldg(nx + k1) : idle;
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) e[u] = __ldg(lg + k + 32 * u);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int pq = __float_as_int(e[u].w);
-        const int p = pq & 0xffff, q = (pq >> 16) & 0xffff;
-        if (p < n && q < n) {
-          const float c = e[u].z;
-          const float2 sv = make_float2(e[u].x, e[u].y), sm = make_float2(-e[u].x, e[u].y);
-          const float2 q0 = qr[p], q1 = qr[q];
-          qr[p] = add<float>(scl<float>(q0, c), mul<float>(q1, sm));
-          qr[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
+    for (int h = 0; h < 2; ++h) {
+      const float4 cur = h ? u1 : u0;
+      const int pq = __float_as_int(cur.w);
+      const int p = pq & 0xffff, q = (pq >> 16) & 0xffff;
+      if (p < n && q < n) {
+        const float c = cur.z;
+        const float2 sv = make_float2(cur.x, cur.y), sm = make_float2(-cur.x, cur.y);
+        for (int r = 0; r < nr; ++r) {
+          float2* row = qs + (size_t)r * n;
+          const float2 q0 = row[p], q1 = row[q];
+          row[p] = add<float>(scl<float>(q0, c), mul<float>(q1, sm));
+          row[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
         }
       }
     }
-    for (; k < P; k += 32) {
-      const float4 e = __ldg(lg + k);
-      const int pq = __float_as_int(e.w);
-      const int p = pq & 0xffff, q = (pq >> 16) & 0xffff;
-      if (p < n && q < n) {
-        const float c = e.z;
-        const float2 sv = make_float2(e.x, e.y), sm = make_float2(-e.x, e.y);
-        const float2 q0 = qr[p], q1 = qr[q];
-        qr[p] = add<float>(scl<float>(q0, c), mul<float>(q1, sm));
-        qr[q] = add<float>(mul<float>(q0, sv), scl<float>(q1, c));
-      }
-    }
-    __syncwarp();
+    __syncthreads();
   }
-  __syncthreads();
-  const int nr = min(W, n - row0);
   for (int t = threadIdx.x; t < nr * n; t += blockDim.x) {
-    const int c = t / nr, r = t - c * nr;
-    const float2 v = qs[(size_t)r * n + c];
-    Q[(size_t)c * ldq + row0 + r] = make_double2((double)v.x, (double)v.y);
+    const int c = t / nr, rr = t - c * nr;
+    const float2 v = qs[(size_t)rr * n + c];
+    Q[(size_t)c * ldq + i0 + rr] = make_double2((double)v.x, (double)v.y);
   }
 }
 
@@ -834,7 +829,7 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_jacobi_pos, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-    cudaFuncSetAttribute(k_jacobi_qlog_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    cudaFuncSetAttribute(k_jacobi_qlog_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   int dev = 0, nsm = 0, per_sm = 0;
   PWH_CUDA(cudaGetDevice(&dev));
@@ -846,12 +841,13 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   void* args[] = {&a};
   PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_pos, blocks, kPjThreads, args, smem, st));
   note_launch();
-  // Q: one warp per row, W rows a block so that the blocks cover the SMs
-  // (at most 16 rows, and W rows of n FP32 complex values within 220 KB)
-  const int W = (int)std::max<int64_t>(
-      1, std::min<int64_t>({16, ((int64_t)n + nsm - 1) / nsm, (220 << 10) / ((int64_t)n * 8)}));
-  const size_t qsm = (size_t)W * n * sizeof(float2);
-  k_jacobi_qlog_warp<<<(n + W - 1) / W, 32 * W, qsm, st>>>(a.log, info, n, P, Q, ldq);
+  // Q rows per block: enough for the blocks to make one wave over the SMs
+  // (every round costs a block barrier whatever its row count), at most what
+  // fits in 220 KB of shared memory
+  const int qrows = (int)std::max<int64_t>(
+      1, std::min<int64_t>(((int64_t)n + nsm - 1) / nsm, (220 << 10) / ((int64_t)n * 8)));
+  const size_t qsm = (size_t)qrows * n * sizeof(float2);
+  k_jacobi_qlog_rows<<<(n + qrows - 1) / qrows, 1024, qsm, st>>>(a.log, info, n, P, qrows, Q, ldq);
   PWH_LAUNCH_CHECK();
   return true;
 }

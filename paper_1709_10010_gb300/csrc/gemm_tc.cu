@@ -536,11 +536,27 @@ void nonlocal_mixed(System& s, int nb, const double2* psi, int64_t ldp, float2* 
   k_pack_psi<<<gblk, 256, 0, st>>>(psi, ldp, s.npw, nb, B1, g.pitch1, g.seg1);
   PWH_LAUNCH_CHECK();
 
-  // ---- becp GEMM, split over K to fill the GPU
+  // ---- becp GEMM, split over K to fill the GPU: the split with the least
+  // modelled time, waves of CTAs (one per SM at a time) times a CTA's share
+  // of its tile's K on the tensor cores and about 2 us of set-up and
+  // epilogue, plus the split-K partials written and read once more (nominal
+  // rates: 2.25 PFLOP/s BF16, 7.9 TB/s)
   const int gm1 = (2 * P + TC_BM - 1) / TC_BM, gn1 = (2 * nb + TC_BN - 1) / TC_BN;
   const int kbs1 = (int)(g.seg1 / TC_BK);
   const int kbt1 = terms * kbs1;
-  int split = std::max(1, std::min(kbt1, (2 * 152 + gm1 * gn1 - 1) / (gm1 * gn1)));
+  const int tiles1 = gm1 * gn1;
+  const double tile_s = 2.0 * TC_BM * TC_BN * TC_BK * (double)kbt1 / (2.25e15 / 152);
+  const double part_s = 2.0 * (2.0 * P) * (2.0 * nb) * sizeof(float) / 7.9e12;
+  int split = 1;
+  double best = 1e300;
+  for (int sp = 1; sp <= std::min(64, kbt1); ++sp) {
+    const double waves = (double)(((int64_t)tiles1 * sp + 151) / 152);
+    const double t = waves * (tile_s / sp + 2e-6) + sp * part_s;
+    if (t < best) {
+      best = t;
+      split = sp;
+    }
+  }
   int kper = (kbt1 + split - 1) / split;
   split = (kbt1 + kper - 1) / kper;  // every split gets >= 1 block
   ensure(s.ws_split, (size_t)split * 2 * P * 2 * nb * sizeof(float));

@@ -34,11 +34,12 @@ def make_system(cell, v, beta, D, precision="fp64"):
 
 
 def q_of(P, seed, full):
+    """Diagonal q_i ~ U(0.1, 0.8), or a full positive definite q (so S > 0)."""
     rng = np.random.default_rng(seed)
     if not full:
         return rng.uniform(0.1, 0.8, P)
-    a = 0.2 * (rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P)))
-    return 0.5 * (a + a.conj().T) + np.eye(P)
+    a = rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P))
+    return 0.5 * (a @ a.conj().T) / P + 0.1 * np.eye(P)
 
 
 CASES = [
