@@ -634,7 +634,12 @@ FAMILY_BOUND = {
 # command), or per counted flop of one representative product, scaled by the
 # launch's flops.  A family whose kernels changed after the capture is absent
 # (traffic null).
-TRAFFIC_PER_LAUNCH = {}   # family -> bytes per launch
+TRAFFIC_PER_LAUNCH = {    # family -> bytes per launch
+    # every k_to_pos32, k_jacobi_pos and k_jacobi_qlog_rows launch of one large
+    # solve (bench.py --profile --steps 1 --warmup 0 under ncu): 2.749 GB over
+    # the 13 Rayleigh-Ritz eigensolves (profiles/jacobi_fp32_large_solve_dram.md)
+    "jacobi_fp32": 2.7494e9 / 13,
+}
 TRAFFIC_PER_FLOP = {      # family -> bytes per counted flop
     # one 1088 x 544 x 16,384 FP64-equivalent product (bench.py --gemm
     # 1088,544,16384,fp64,1): 6.16 GB of DRAM traffic over its six kernels

@@ -83,6 +83,24 @@ __global__ void k_exx_acc(const double2* __restrict__ U, const double2* __restri
   }
 }
 
+// W[j][r] -= f_i U_i[r] conj(v[j][r]) for the J boxes of a batch, skipping
+// box jskip: the term of source i in the exchange of band j, from the pair
+// potential of (i, j) (v_ji = conj(v_ij), the Coulomb kernel being real)
+__global__ void k_exx_acc_t(const double2* __restrict__ Ui, const double2* __restrict__ v,
+                            double fi, double2* __restrict__ W, int64_t nbox, int J, int jskip) {
+  const int64_t tot = nbox * J;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t / nbox);
+    if (j == jskip) continue;
+    const int64_t r = t - (int64_t)j * nbox;
+    const double2 u = Ui[r], a = v[t];
+    // u conj(a)
+    W[t].x -= fi * (u.x * a.x + u.y * a.y);
+    W[t].y -= fi * (u.y * a.x - u.x * a.y);
+  }
+}
+
 // out[g] = scale * box[idx[g]]
 __global__ void k_exx_gather(const double2* __restrict__ box, const int32_t* __restrict__ idx,
                              int64_t npw, double scale, double2* __restrict__ out) {
@@ -226,6 +244,55 @@ static void exx_apply(System& s, int nocc, const double2* psi_occ, int64_t ld_oc
   }
 }
 
+// out[:, i] = V_x psi_i for the occupied bands themselves: each unordered pair
+// (i, j) is transformed once and feeds both bands' exchange, so about half the
+// pair densities of exx_apply with the same bands as targets.
+static void exx_apply_self(System& s, int nocc, const double2* psi, int64_t ld, const double* occ,
+                           double2* out, int64_t ld_out) {
+  exx_tables(s);
+  cudaStream_t st = s.stream;
+  const int64_t npw = s.npw, nbox = (int64_t)s.n1 * s.n2 * s.n3;
+  const size_t bb = (size_t)nbox * sizeof(double2);
+  const int J = (int)std::max<int64_t>(1, std::min<int64_t>(nocc, ((int64_t)64 << 20) / (int64_t)bb));
+  ExxScratch sc{st, {}};
+  double2* U = (double2*)sc.get(bb * nocc);
+  double2* W = (double2*)sc.get(bb * nocc);
+  double2* pair = (double2*)sc.get(bb * J);
+  double* f = (double*)sc.get(nocc * sizeof(double));
+  PWH_CUDA(cudaMemcpyAsync(f, occ, nocc * sizeof(double), cudaMemcpyHostToDevice, st));
+  PWH_CUDA(cudaMemsetAsync(U, 0, bb * nocc, st));
+  PWH_CUDA(cudaMemsetAsync(W, 0, bb * nocc, st));
+  k_exx_scatter<<<exx_grid(npw * nocc), 256, 0, st>>>(psi, ld, npw, nocc, s.d_boxidx, U, nbox);
+  PWH_LAUNCH_CHECK();
+  box_fft(s, U, true, nocc, nbox);
+  for (int i = 0; i < nocc; ++i) {
+    const double2* Ui = U + (size_t)i * nbox;
+    double2* Wi = W + (size_t)i * nbox;
+    for (int j0 = 0; j0 <= i; j0 += J) {
+      const int jb = std::min(J, i + 1 - j0);
+      const double2* Uj = U + (size_t)j0 * nbox;
+      k_exx_pair<<<exx_grid(nbox * jb), 256, 0, st>>>(Uj, Ui, pair, nbox, jb);
+      PWH_LAUNCH_CHECK();
+      box_fft(s, pair, false, jb, nbox);
+      k_exx_coulomb<<<exx_grid(nbox * jb), 256, 0, st>>>(pair, s.d_kern, nbox, jb);
+      PWH_LAUNCH_CHECK();
+      box_fft(s, pair, true, jb, nbox);
+      // band i: sources j0.. (v_ij); bands j0.. (j < i): source i (conj v_ij)
+      k_exx_acc<<<exx_grid(nbox), 256, 0, st>>>(Uj, pair, f + j0, Wi, nbox, jb);
+      PWH_LAUNCH_CHECK();
+      k_exx_acc_t<<<exx_grid(nbox * jb), 256, 0, st>>>(Ui, pair, occ[i], W + (size_t)j0 * nbox,
+                                                      nbox, jb, i - j0 < jb ? i - j0 : -1);
+      PWH_LAUNCH_CHECK();
+    }
+  }
+  box_fft(s, W, false, nocc, nbox);
+  for (int i = 0; i < nocc; ++i) {
+    k_exx_gather<<<exx_grid(npw), 256, 0, st>>>(W + (size_t)i * nbox, s.d_boxidx, npw,
+                                               1.0 / (double)nbox, out + (size_t)i * ld_out);
+    PWH_LAUNCH_CHECK();
+  }
+}
+
 void ace_apply(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
                int precision) {
   if (s.ace_n == 0 || nb <= 0) return;
@@ -295,7 +362,7 @@ pwh_status pwh_set_ace(pwh_system* sys, int32_t nocc, const void* psi_occ, int64
     int* kk = (int*)sc.get(sizeof(int));
     const double2* psi = (const double2*)psi_occ;
     // xi = V_x psi, M = psi^H xi, -M = L L^H with Tr = L^-H (Tr^H (-M) Tr = I)
-    exx_apply(s, nocc, psi, ld_occ, occ, nocc, psi, ld_occ, xi, npw);
+    exx_apply_self(s, nocc, psi, ld_occ, occ, xi, npw);
     const double2 one = make_double2(1, 0), zero = make_double2(0, 0);
     cgemm<double>(s, true, nocc, nocc, (int)npw, one, psi, ld_occ, xi, npw, zero, M, nocc, st);
     k_exx_neg_herm<<<exx_grid((int64_t)nocc * nocc), 256, 0, st>>>(M, nocc, S);

@@ -1529,10 +1529,24 @@ static X2Geom x2_geom(bool conjA, int M, int N, int K) {
   g.pitch = X2_S * g.seg;
   const int kb_total = X2_TERMS * g.kb_seg;
   g.tiles = ((g.Mr + TC_BM - 1) / TC_BM) * ((g.Nr + TC_BN - 1) / TC_BN);
-  // about two waves of blocks, each K range at most kX2Kmax real K
-  const int nz_fill = (int)std::max<int64_t>(1, (2 * 152 + g.tiles - 1) / g.tiles);
-  const int nz_acc = (kb_total + kX2Kmax / TC_BK - 1) / (kX2Kmax / TC_BK);
-  int nz = std::max(1, std::min(kb_total, std::max(nz_fill, nz_acc)));
+  // K ranges: at least enough that none exceeds kX2Kmax real K (accuracy),
+  // then the count with the least modelled time (waves of CTAs, one per SM at
+  // a time, times a CTA's share of its tile's K and about 2 us of set-up and
+  // epilogue, plus the partials written and read once more; nominal rates
+  // 2.25 PFLOP/s BF16, 7.9 TB/s)
+  const int nz_acc = std::max(1, (kb_total + kX2Kmax / TC_BK - 1) / (kX2Kmax / TC_BK));
+  const double tile_s = 2.0 * TC_BM * TC_BN * TC_BK * (double)kb_total / (2.25e15 / 152);
+  const double part_s = 2.0 * (double)g.Mr * g.Nr * sizeof(float) / 7.9e12;
+  int nz = std::min(kb_total, nz_acc);
+  double best = 1e300;
+  for (int z = nz_acc; z <= std::min(kb_total, std::max(nz_acc, 1024)); ++z) {
+    const double waves = (double)((g.tiles * z + 151) / 152);
+    const double t = waves * (tile_s / z + 2e-6) + z * part_s;
+    if (t < best) {
+      best = t;
+      nz = z;
+    }
+  }
   g.kps = (kb_total + nz - 1) / nz;
   g.nz = (kb_total + g.kps - 1) / g.kps;
   g.bytes_a = align256((size_t)g.Mr * g.pitch * 2);
