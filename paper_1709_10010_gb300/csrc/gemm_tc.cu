@@ -100,6 +100,9 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)),
                "r"(bytes)
@@ -165,6 +168,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// K blocks [kb0, kb_end) of grid slice z: sliced operands (oz = 1: z = chunk x
+// products + product; oz = 2: the long ranges of products 1.. first, then the
+// short ranges of product 0) or plain split-K ranges.
+__device__ __forceinline__ void tc_krange(const TcArgs& args, int z, int& kb0, int& kb_end) {
+  const int kb_total = args.terms * args.kb_seg;
+  if (args.oz == 1) {
+    kb0 = (z % args.terms) * args.kb_seg + (z / args.terms) * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  } else if (args.oz == 2 && z < args.z_rest) {
+    kb0 = args.kb_seg + z * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  } else if (args.oz == 2) {
+    kb0 = (z - args.z_rest) * args.kps0;
+    kb_end = min(args.kb_seg, kb0 + args.kps0);
+  } else {
+    kb0 = z * args.kb_per_split;
+    kb_end = min(kb_total, kb0 + args.kb_per_split);
+  }
+}
+
 // Logical K block kb -> (A column, B column) in elements, for the [hi|lo]
 // operand layout: term 0 = (hi, hi), term 1 = (hi, lo), term 2 = (lo, hi).
 __device__ __forceinline__ void kb_coords(int kb, int kb_seg, int& xa, int& xb) {
@@ -174,48 +197,50 @@ __device__ __forceinline__ void kb_coords(int kb, int kb_seg, int& xa, int& xb) 
   xb = (sb * kb_seg + r) * TC_BK;
 }
 
+// Persistent, warp-specialised form: one CTA per SM walks the output tiles
+// (x = M tile fastest, then N tile, then grid slice z) with two accumulators
+// in tensor memory, so that a tile's epilogue overlaps the next tile's MMAs.
+//   warp 0: allocates the 512 TMEM columns; one thread issues the TMA loads
+//           of every tile's K blocks through the TC_STAGES ring;
+//   warp 1: one thread waits for a free accumulator, issues the tile's MMAs
+//           into it and commits them to tfull[buffer];
+//   warps 2-5: the epilogue; warp w drains TMEM lanes 32 (w mod 4) .. +32
+//           (its lane sub-partition), stores, and releases the accumulator
+//           (tempty[buffer], one arrival per warp).
+// Every wait is bounded; a wait that gives up raises the abort flag, which
+// every other wait sees, and the kernel records PWH_ERR_TIMEOUT.
+constexpr int TCP_THREADS = 192;
+constexpr int TCP_TMEM_COLS = 512;
+
+struct TcWork {
+  int gm, gn, gz;  // M tiles, N tiles, grid slices
+};
+
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TCP_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b,
-              TcArgs args) {
+              TcArgs args, TcWork wk) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + TC_STAGES * TC_STAGE_BYTES);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  uint64_t* tfull = empty + TC_STAGES;  // [2]
+  uint64_t* tempty = tfull + 2;         // [2]
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * TC_BN;
-  const int kb_total = args.terms * args.kb_seg;
-  // sliced operands: z = chunk * pairs + pair, so that the pairs of one K chunk
-  // (which share operand slices) run close together and hit in L2
-  const int z = (int)blockIdx.z;
-  int kb0, kb_end;
-  if (args.oz == 1) {
-    kb0 = (z % args.terms) * args.kb_seg + (z / args.terms) * args.kb_per_split;
-    kb_end = min(kb_total, kb0 + args.kb_per_split);
-  } else if (args.oz == 2 && z < args.z_rest) {
-    // products 1.. (the smaller slices): long ranges
-    kb0 = args.kb_seg + z * args.kb_per_split;
-    kb_end = min(kb_total, kb0 + args.kb_per_split);
-  } else if (args.oz == 2) {
-    // product 0 (leading slices): short ranges
-    kb0 = (z - args.z_rest) * args.kps0;
-    kb_end = min(args.kb_seg, kb0 + args.kps0);
-  } else {
-    kb0 = z * args.kb_per_split;
-    kb_end = min(kb_total, kb0 + args.kb_per_split);
-  }
-  const int nkb = max(0, kb_end - kb0);
+  const int tiles = wk.gm * wk.gn, items = tiles * wk.gz;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -223,7 +248,7 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tmem_slot)),
-                 "r"(TC_TMEM_COLS)
+                 "r"(TCP_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -232,95 +257,153 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;  // producer: number of K blocks whose loads were started
+  int issued = 0;  // producer: ring slots whose loads were started
   if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = ((kb / TC_STAGES) & 1) ^ 1;
-      if (!mbar_wait(&empty[s], ph, abort_flag)) {
-        *abort_flag = 1;
-        break;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+      const int z = it / tiles, rem = it - z * tiles;
+      const int m0 = (rem % wk.gm) * TC_BM, n0 = (rem / wk.gm) * TC_BN;
+      int kb0, kb_end;
+      tc_krange(args, z, kb0, kb_end);
+      bool ok = true;
+      for (int kb = kb0; kb < kb_end; ++kb) {
+        const int s = issued % TC_STAGES;
+        const uint32_t ph = ((issued / TC_STAGES) & 1) ^ 1;
+        if (!mbar_wait(&empty[s], ph, abort_flag)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        int xa, xb;
+        if (args.oz) {
+          const int t = kb / args.kb_seg, r = kb - t * args.kb_seg;
+          xa = (args.oz_a[t] * args.kb_seg + r) * TC_BK;
+          xb = (args.oz_b[t] * args.kb_seg + r) * TC_BK;
+        } else {
+          kb_coords(kb, args.kb_seg, xa, xb);
+        }
+        uint8_t* sa = smem + s * TC_STAGE_BYTES;
+        mbar_expect_tx(&full[s], TC_STAGE_BYTES);
+        tma_load_2d(sa, &tma_a, xa, m0, &full[s]);
+        tma_load_2d(sa + TC_A_BYTES, &tma_b, xb, n0, &full[s]);
+        ++issued;
       }
-      int xa, xb;
-      if (args.oz) {
-        const int t = (kb0 + kb) / args.kb_seg, r = (kb0 + kb) - t * args.kb_seg;
-        xa = (args.oz_a[t] * args.kb_seg + r) * TC_BK;
-        xb = (args.oz_b[t] * args.kb_seg + r) * TC_BK;
-      } else {
-        kb_coords(kb0 + kb, args.kb_seg, xa, xb);
-      }
-      uint8_t* sa = smem + s * TC_STAGE_BYTES;
-      mbar_expect_tx(&full[s], TC_STAGE_BYTES);
-      tma_load_2d(sa, &tma_a, xa, m0, &full[s]);
-      tma_load_2d(sa + TC_A_BYTES, &tma_b, xb, n0, &full[s]);
-      ++issued;
+      if (!ok) break;
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = idesc_bf16(TC_BM, TC_BN);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (kb / TC_STAGES) & 1;
-      if (!mbar_wait(&full[s], ph, abort_flag)) {
+    int used = 0, lj = 0;  // ring slots consumed, tiles of this CTA
+    for (int it = blockIdx.x; it < items; it += gridDim.x, ++lj) {
+      const int z = it / tiles;
+      int kb0, kb_end;
+      tc_krange(args, z, kb0, kb_end);
+      const int nkb = max(0, kb_end - kb0);
+      const int buf = lj & 1;
+      if (!mbar_wait(&tempty[buf], ((lj >> 1) & 1) ^ 1, abort_flag)) {
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = su32(smem + s * TC_STAGE_BYTES);
-      const uint32_t b0 = a0 + TC_A_BYTES;
+      const uint32_t dst = tmem + (uint32_t)(buf * TC_BN);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb, ++used) {
+        const int s = used % TC_STAGES;
+        if (!mbar_wait(&full[s], (used / TC_STAGES) & 1, abort_flag)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = su32(smem + s * TC_STAGE_BYTES);
+        const uint32_t b0 = a0 + TC_A_BYTES;
 #pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k)
-        mma_bf16(tmem, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc,
-                 (kb > 0 || k > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int k = 0; k < TC_BK / 16; ++k)
+          mma_bf16(dst, smem_desc(a0 + k * 32), smem_desc(b0 + k * 32), idesc,
+                   (kb > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      if (!ok) break;
+      mma_commit(&tfull[buf]);  // arrives once every MMA issued so far has completed
     }
-    mma_commit(done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // ---- epilogue: TMEM -> registers -> global
-  const bool ok = mbar_wait(done, 0, nullptr) && !*abort_flag && nkb > 0;
-  tc_fence_after();
-  if (ok) {
-    const int row = warp * 32 + lane;
-    const int m = m0 + row;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (m < args.M) {
-        if (MODE == 0) {
+  } else if (warp >= 2) {
+    const int sub = warp & 3;  // the TMEM lane sub-partition this warp may read
+    const int row = sub * 32 + lane;
+    int lj = 0;
+    for (int it = blockIdx.x; it < items; it += gridDim.x, ++lj) {
+      const int z = it / tiles, rem = it - z * tiles;
+      const int m0 = (rem % wk.gm) * TC_BM, n0 = (rem / wk.gm) * TC_BN;
+      int kb0, kb_end;
+      tc_krange(args, z, kb0, kb_end);
+      const int buf = lj & 1;
+      if (!mbar_wait(&tfull[buf], (lj >> 1) & 1, abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (kb_end > kb0) {
+        const int m = m0 + row;
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(buf * TC_BN + c0), v);
+          if (m < args.M) {
+            if (MODE == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            int n = n0 + c0 + j;
-            if (n < args.N) args.part[((size_t)blockIdx.z * args.N + n) * args.M + m] = v[j];
-          }
-        } else {
-          // the nonlocal term of band b at plane wave m, FP32 (the z-forward
-          // FFT pass adds it into H psi): plain stores, one 256-byte run per
-          // band and warp
+              for (int j = 0; j < 32; ++j) {
+                const int n = n0 + c0 + j;
+                if (n < args.N) args.part[((size_t)z * args.N + n) * args.M + m] = v[j];
+              }
+            } else {
+              // the nonlocal term of band b at plane wave m, FP32 (the
+              // z-forward FFT pass adds it into H psi)
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const int b = (n0 + c0 + j) >> 1;
-            if (b < args.nb) args.vnl[(size_t)b * args.ldv + m] = make_float2(v[j], v[j + 1]);
+              for (int j = 0; j < 32; j += 2) {
+                const int b = (n0 + c0 + j) >> 1;
+                if (b < args.nb) args.vnl[(size_t)b * args.ldv + m] = make_float2(v[j], v[j + 1]);
+              }
+            }
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(args.err, (int)PWH_ERR_TIMEOUT);
   }
+  __syncwarp();
   // producer: make sure every copy it started has landed before smem goes away
   if (warp == 0 && lane == 0) {
-    for (int kb = max(0, issued - TC_STAGES); kb < issued; ++kb)
-      mbar_wait(&full[kb % TC_STAGES], (kb / TC_STAGES) & 1, nullptr);
+    for (int j = max(0, issued - TC_STAGES); j < issued; ++j)
+      mbar_wait(&full[j % TC_STAGES], (j / TC_STAGES) & 1, nullptr);
   }
   tc_fence_before();
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(args.err, (int)PWH_ERR_TIMEOUT);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TC_TMEM_COLS)
+                 "r"(TCP_TMEM_COLS)
                  : "memory");
   }
+}
+
+// Launches the persistent kernel over the gm x gn x gz grid of tiles and
+// slices: one CTA per SM (fewer when there are fewer tiles).
+template <int MODE>
+static void tc_launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& a, dim3 grid,
+                      cudaStream_t st) {
+  static int nsm = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 152;
+    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  });
+  TcWork wk{(int)grid.x, (int)grid.y, (int)grid.z};
+  const int64_t items = (int64_t)grid.x * grid.y * grid.z;
+  const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(items, nsm));
+  k_tc_gemm<MODE><<<ctas, TCP_THREADS, TC_SMEM, st>>>(ma, mb, a, wk);
 }
 
 // ------------------------------------------------------- operand packing ----
@@ -494,16 +577,11 @@ static void launch_tc(System& s, int mode, const CUtensorMap& ma, const CUtensor
   TimedScope ts(s, mode == 0 ? KF_TC_BECP : KF_TC_BACK, st, 2.0 * a.M * (double)a.N * kk,
                 2.0 * ((double)a.M + a.N) * kk + (mode == 0 ? 4.0 * gz * (double)a.M * a.N
                                                             : 8.0 * a.M * (a.N / 2)));
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-  });
   dim3 grid(gm, gn, gz);
   if (mode == 0)
-    k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+    tc_launch<0>(ma, mb, a, grid, st);
   else
-    k_tc_gemm<1><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+    tc_launch<1>(ma, mb, a, grid, st);
   PWH_LAUNCH_CHECK();
 }
 
@@ -1119,7 +1197,7 @@ static void oz_gemm_piece(System& s, bool conjA, int M, int N, int K, double2 al
     a.oz_b[p] = pb[p];
   }
   dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), nz);
-  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  tc_launch<0>(ma, mb, a, grid, st);
   PWH_LAUNCH_CHECK();
   const int64_t tot = (int64_t)M * N;
   if (conjA)
@@ -1462,7 +1540,7 @@ static void x3_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alph
     a.oz_b[p] = tb[p];
   }
   dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), nz);
-  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  tc_launch<0>(ma, mb, a, grid, st);
   PWH_LAUNCH_CHECK();
   X3Out o;
   o.alpha = alpha;
@@ -1594,7 +1672,7 @@ static void x2_gemm_seg(System& s, bool conjA, int M, int N, int K, double2 alph
   a.err = device_error_word(s);
   a.oz = 0;
   dim3 grid((unsigned)((Mr + TC_BM - 1) / TC_BM), (unsigned)((Nr + TC_BN - 1) / TC_BN), g.nz);
-  k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(ma, mb, a);
+  tc_launch<0>(ma, mb, a, grid, st);
   PWH_LAUNCH_CHECK();
   X3Out o;
   o.alpha = alpha;
