@@ -641,6 +641,11 @@ TRAFFIC_PER_LAUNCH = {    # family -> bytes per launch
     "jacobi_fp32": 2.7494e9 / 13,
 }
 TRAFFIC_PER_FLOP = {      # family -> bytes per counted flop
+    # one 1088 x 544 x 16,384 FP64-equivalent product on the persistent
+    # tensor-core kernel (bench.py --gemm 1088,544,16384,fp64,1): 6.12 GB of
+    # DRAM traffic over its six kernels for 2.79e12 counted tensor flops
+    # (profiles/oz_gemm_fp64_conj_1088x544x16384.md)
+    "zgemm_fp64_tc": 6.118e9 / 2.7928e12,
 }
 
 

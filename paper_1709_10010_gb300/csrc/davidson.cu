@@ -780,11 +780,13 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
         s.timer.bytes[KF_JACOBI] += sw * (m - 1) * 3.0 * 16.0 * (double)m * m;
       }
       // FP32 stage: per round 20 m^2 operations on A (2 x 2 blocks, both
-      // triangles) and 10 m^2 on Q; plus the warm-start transform and the
+      // triangles) and 10 m^2 on Q (the block kernel above m = 512: its own
+      // count per sweep); plus the warm-start transform and the
       // Newton-Schulz step (complex GEMMs of 8 m^3 each)
       const double sw32 = w.h_idx[4101];
       const int ngemm32 = (warm ? 3 : 0) + (polish ? 0 : 3);
-      const double fj = sw32 * (m - 1) * 30.0 * (double)m * m;
+      const double fj = m > 512 ? sw32 * jacobi32_blk_sweep_flops(m)
+                                : sw32 * (m - 1) * 30.0 * (double)m * m;
       s.timer.flops[KF_JACOBI32] += fj + ngemm32 * 8.0 * (double)m * m * m;
     }
     s.timer.resolve();

@@ -852,8 +852,439 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
   return true;
 }
 
-// FP32 stage, autotuned between the two kernels that fit: above n = 512 only
-// the position-order kernel; for 64 <= n <= 512 the cluster kernel or the
+// ---- FP32 block Jacobi over the whole GPU -----------------------------------
+// The indices are cut into blocks of kBjB = 16 that play a round-robin
+// tournament (circle method): nblk - 1 rounds a sweep, every block paired
+// with one other in each round, so a round holds nblk / 2 pair groups
+// P = (I, J) of 32 indices.  A round has two phases, each closed by a grid
+// barrier:
+//   1. per pair group, one cyclic Jacobi sweep (31 rounds of 16 plane
+//      rotations) of the 32 x 32 diagonal block A_PP in shared memory, the
+//      rotations accumulated into the block rotation U_P (32 x 32), which one
+//      Newton-Schulz step brings back to unitary before it is used;
+//   2. every other block of the matrix and the eigenvector basis as small
+//      complex GEMMs on the CUDA cores, groups of 64 threads each taking one
+//      item: A_PQ <- U_P^H A_PQ U_Q for each pair of groups P < Q (A_QP
+//      written as its conjugate transpose), Q_RP <- Q_RP U_P for each group R
+//      of 32 rows.
+// One pass over the matrix thus carries a 32 x 32 block rotation per pair
+// group instead of one plane rotation per index pair, and a sweep makes
+// nblk - 1 passes instead of n - 1.  Storage: A and Q as nblk x nblk tiles of
+// 16 x 16 (A row-major within a tile, Q column-major), A in full (both
+// triangles); padding indices beyond n have zero rows and columns, so every
+// rotation that involves them is the identity.
+constexpr int kBjB = 16;
+constexpr int kBjG = 2 * kBjB;
+constexpr int kBjTile = kBjB * kBjB;
+constexpr int kBjThreads = 512;
+constexpr int kBjGroups = kBjThreads / 64;
+constexpr int kBjLd = kBjG + 1;  // padded row of the phase-1 block
+constexpr int kBjGroupElems = 3 * kBjG * kBjG;
+constexpr size_t kBjSmem = (size_t)kBjGroups * kBjGroupElems * sizeof(float2);
+
+struct BjArgs {
+  float2* A;          // nblk x nblk tiles, row-major tiles, full Hermitian
+  float2* Q;          // nblk x nblk tiles, column-major tiles
+  float2* U;          // nblk / 2 block rotations, 32 x 32 row-major
+  double* diag;       // out: eigenvalue estimates, by index
+  double2* Qout;      // out: n x n, column-major, ld ldq
+  int64_t ldq;
+  int* info;          // out: [0] 0, [1] sweeps, [2] 0
+  unsigned* red;      // 2 words per sweep (max off-diagonal, max diagonal; float bits), zeroed
+  int n, nblk, max_sweeps;
+  float tol;
+  GridBar gb;
+};
+
+// pair k of round r among m players (m even): player m - 1 fixed, the others
+// on a circle
+__device__ __forceinline__ void bj_pair(int r, int k, int m, int& I, int& J) {
+  const int L = m - 1;
+  if (k == 0) {
+    I = r;
+    J = L;
+  } else {
+    I = (r + k) % L;
+    J = (r - k + L) % L;
+  }
+}
+__device__ __forceinline__ float2* bj_tile(float2* X, int nblk, int I, int J) {
+  return X + ((size_t)I * nblk + J) * kBjTile;
+}
+__device__ __forceinline__ void bj_bar(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+__device__ __forceinline__ void bj_ld2(const float2* p, float2& a, float2& b) {
+  const float4 v = *(const float4*)p;
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void bj_st2(float2* p, float2 a, float2 b) {
+  *(float4*)p = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Phase 1 for pair group (I, J): one sweep on A_PP, U_P to Ub.
+__device__ void bj_phase1(const BjArgs& a, float2* sm, int I, int J, float2* Ub) {
+  float2* S = sm;                         // 32 x kBjLd
+  float2* Us = sm + kBjG * kBjLd;         // 32 x kBjLd
+  float4* rot = (float4*)(Us + kBjG * kBjLd);
+  const int tid = threadIdx.x;
+  for (int t = tid; t < kBjG * kBjG; t += kBjThreads) {
+    const int row = t >> 5, col = t & 31;
+    const int Br = row < kBjB ? I : J, Bc = col < kBjB ? I : J;
+    S[row * kBjLd + col] = bj_tile(a.A, a.nblk, Br, Bc)[(row & 15) * kBjB + (col & 15)];
+    Us[row * kBjLd + col] = make_float2(row == col ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  for (int ir = 0; ir < kBjG - 1; ++ir) {
+    if (tid < kBjB) {
+      int p, q;
+      bj_pair(ir, tid, kBjG, p, q);
+      float c;
+      float2 sv;
+      jacobi_rotation<float>(S[p * kBjLd + q], S[p * kBjLd + p].x, S[q * kBjLd + q].x, c, sv);
+      rot[tid] = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 8)));
+    }
+    __syncthreads();
+    if (tid < kBjB * kBjB) {
+      // 2 x 2 block (pair kk rows, pair ll columns) of J^H S J
+      const int kk = tid >> 4, ll = tid & 15;
+      const float4 rk = rot[kk], rl = rot[ll];
+      const int pq = __float_as_int(rk.w), pl_ql = __float_as_int(rl.w);
+      const int pk = pq & 255, qk = pq >> 8, pl = pl_ql & 255, ql = pl_ql >> 8;
+      float2 y00, y01, y10, y11;
+      jacobi_block<float>(S[pk * kBjLd + pl], S[pk * kBjLd + ql], S[qk * kBjLd + pl],
+                          S[qk * kBjLd + ql], rk.z, make_float2(rk.x, rk.y), rl.z,
+                          make_float2(rl.x, rl.y), y00, y01, y10, y11);
+      if (kk == ll) {
+        y00.y = 0.f;
+        y11.y = 0.f;
+        y01 = make_float2(0.f, 0.f);
+        y10 = y01;
+      }
+      S[pk * kBjLd + pl] = y00;
+      S[pk * kBjLd + ql] = y01;
+      S[qk * kBjLd + pl] = y10;
+      S[qk * kBjLd + ql] = y11;
+    } else {
+      // U <- U J on the column pairs: [u_p, u_q] <- [c u_p - conj(s) u_q, s u_p + c u_q]
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int idx = tid - kBjB * kBjB + h * (kBjThreads - kBjB * kBjB);
+        const int row = idx >> 4, l = idx & 15;
+        const float4 rl = rot[l];
+        const int pl_ql = __float_as_int(rl.w);
+        const int p = pl_ql & 255, q = pl_ql >> 8;
+        const float c = rl.z;
+        const float2 sv = make_float2(rl.x, rl.y), sm_ = make_float2(-rl.x, rl.y);
+        const float2 u0 = Us[row * kBjLd + p], u1 = Us[row * kBjLd + q];
+        Us[row * kBjLd + p] = add<float>(scl<float>(u0, c), mul<float>(u1, sm_));
+        Us[row * kBjLd + q] = add<float>(mul<float>(u0, sv), scl<float>(u1, c));
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < kBjG * kBjG; t += kBjThreads) {
+    const int row = t >> 5, col = t & 31;
+    const int Br = row < kBjB ? I : J, Bc = col < kBjB ? I : J;
+    bj_tile(a.A, a.nblk, Br, Bc)[(row & 15) * kBjB + (col & 15)] = S[row * kBjLd + col];
+  }
+  __syncthreads();
+  // one Newton-Schulz step towards the nearest unitary, U (3I - U^H U) / 2:
+  // U is a product of 496 FP32 rotations, and its deviation from unitary
+  // would otherwise accumulate in Q over every round of every sweep
+  for (int t = tid; t < kBjG * kBjG; t += kBjThreads) {
+    const int i = t >> 5, j = t & 31;
+    float2 g = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int k = 0; k < kBjG; ++k) {
+      const float2 x = Us[k * kBjLd + i], y = Us[k * kBjLd + j];
+      g.x = fmaf(x.x, y.x, fmaf(x.y, y.y, g.x));
+      g.y = fmaf(x.x, y.y, fmaf(-x.y, y.x, g.y));
+    }
+    S[i * kBjLd + j] = g;  // G = U^H U
+  }
+  __syncthreads();
+  for (int t = tid; t < kBjG * kBjG; t += kBjThreads) {
+    const int i = t >> 5, j = t & 31;
+    float2 v = make_float2(0.f, 0.f);
+#pragma unroll 8
+    for (int k = 0; k < kBjG; ++k) v = add<float>(v, mul<float>(Us[i * kBjLd + k], S[k * kBjLd + j]));
+    const float2 u = Us[i * kBjLd + j];
+    Ub[t] = make_float2(1.5f * u.x - 0.5f * v.x, 1.5f * u.y - 0.5f * v.y);
+  }
+  __syncthreads();
+}
+
+// acc[a][b] += (CONJ ? conj(x[a]) : x[a]) y[b] over k, x = X[k][4 ti ..], y = Y[k][4 tj ..]
+// (X, Y 32 x 32 row-major in shared memory)
+template <bool CONJ>
+__device__ __forceinline__ void bj_gemm(const float2* X, const float2* Y, int ti, int tj,
+                                        float2 (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int k = 0; k < kBjG; ++k) {
+    float2 x[4], y[4];
+    bj_ld2(X + k * kBjG + 4 * ti, x[0], x[1]);
+    bj_ld2(X + k * kBjG + 4 * ti + 2, x[2], x[3]);
+    bj_ld2(Y + k * kBjG + 4 * tj, y[0], y[1]);
+    bj_ld2(Y + k * kBjG + 4 * tj + 2, y[2], y[3]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (CONJ) {
+          acc[i][j].x = fmaf(x[i].x, y[j].x, fmaf(x[i].y, y[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(x[i].x, y[j].y, fmaf(-x[i].y, y[j].x, acc[i][j].y));
+        } else {
+          acc[i][j].x = fmaf(x[i].x, y[j].x, fmaf(-x[i].y, y[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(x[i].x, y[j].y, fmaf(x[i].y, y[j].x, acc[i][j].y));
+        }
+      }
+  }
+}
+
+__global__ void __launch_bounds__(kBjThreads, 1) k_jacobi_blk(BjArgs a) {
+  extern __shared__ __align__(16) unsigned char bjs[];
+  float2* sm = (float2*)bjs;
+  __shared__ float s_red[2][kBjThreads / 32];
+  const int tid = threadIdx.x, grp = tid >> 6, lt = tid & 63;
+  const int ti = lt & 7, tj = lt >> 3;
+  const int nblk = a.nblk, nb2 = nblk / 2, n = a.n;
+  const int nA = nb2 * (nb2 - 1) / 2, nQ = nb2 * nb2, nItems = nQ + nA;
+  const int gtid = blockIdx.x * blockDim.x + tid, nth = gridDim.x * blockDim.x;
+  float2* gs = sm + (size_t)grp * kBjGroupElems;
+  float2* X0 = gs;
+  float2* X1 = gs + kBjG * kBjG;
+  float2* X2 = gs + 2 * kBjG * kBjG;
+  unsigned epoch = 0;
+  int sweep = 0;
+  bool done = false;
+  while (sweep < a.max_sweeps && !done) {
+    for (int r = 0; r < nblk - 1; ++r) {
+      // ---- phase 1: the diagonal pair blocks
+      for (int k = blockIdx.x; k < nb2; k += gridDim.x) {
+        int I, J;
+        bj_pair(r, k, nblk, I, J);
+        bj_phase1(a, sm, I, J, a.U + (size_t)k * kBjG * kBjG);
+      }
+      if (!grid_sync(a.gb, epoch)) return;
+      // ---- phase 2: Q row groups, then the off-diagonal pair blocks
+      for (int it = blockIdx.x * kBjGroups + grp; it < nItems; it += gridDim.x * kBjGroups) {
+        float2 acc[4][4];
+        if (it < nQ) {
+          const int R = it / nb2, P = it - R * nb2;
+          int I, J;
+          bj_pair(r, P, nblk, I, J);
+          // X0[k][i] = Q[32 R + i][col k of P] (column-major tiles: contiguous in i)
+          for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
+            const int e = 2 * v, k = e >> 5, i = e & 31;
+            const float2* src = bj_tile(a.Q, nblk, 2 * R + (i >> 4), k < kBjB ? I : J);
+            *(float4*)(X0 + e) = *(const float4*)(src + (k & 15) * kBjB + (i & 15));
+            *(float4*)(X1 + e) = *(const float4*)(a.U + (size_t)P * kBjG * kBjG + e);
+          }
+          bj_bar(grp + 1);
+          bj_gemm<false>(X0, X1, ti, tj, acc);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int col = 4 * tj + j;
+            float2* dst = bj_tile(a.Q, nblk, 2 * R + (ti >> 2), col < kBjB ? I : J) +
+                          (col & 15) * kBjB + ((4 * ti) & 15);
+            bj_st2(dst, acc[0][j], acc[1][j]);
+            bj_st2(dst + 2, acc[2][j], acc[3][j]);
+          }
+        } else {
+          // pair of groups (P, Q), P < Q, numbered row by row
+          const int t = it - nQ;
+          const int m2 = 2 * nb2 - 1;
+          int P = (int)((m2 - sqrtf((float)m2 * m2 - 8.f * t)) * 0.5f);
+          P = max(0, min(P, nb2 - 2));
+          while (P > 0 && P * (m2 - P) / 2 > t) --P;
+          while ((P + 1) * (m2 - P - 1) / 2 <= t) ++P;
+          const int Qg = P + 1 + (t - P * (m2 - P) / 2);
+          int I1, J1, I2, J2;
+          bj_pair(r, P, nblk, I1, J1);
+          bj_pair(r, Qg, nblk, I2, J2);
+          for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
+            const int e = 2 * v, row = e >> 5, col = e & 31;
+            const float2* src = bj_tile(a.A, nblk, row < kBjB ? I1 : J1, col < kBjB ? I2 : J2);
+            *(float4*)(X0 + e) = *(const float4*)(src + (row & 15) * kBjB + (col & 15));
+            *(float4*)(X1 + e) = *(const float4*)(a.U + (size_t)P * kBjG * kBjG + e);
+            *(float4*)(X2 + e) = *(const float4*)(a.U + (size_t)Qg * kBjG * kBjG + e);
+          }
+          bj_bar(grp + 1);
+          bj_gemm<true>(X1, X0, ti, tj, acc);  // T = U_P^H A_PQ
+          bj_bar(grp + 1);
+          // X0 <- T^T (row k holds column k of T)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2* d = X0 + (4 * tj + j) * kBjG + 4 * ti;
+            bj_st2(d, acc[0][j], acc[1][j]);
+            bj_st2(d + 2, acc[2][j], acc[3][j]);
+          }
+          bj_bar(grp + 1);
+          bj_gemm<false>(X0, X2, ti, tj, acc);  // T U_Q
+          const int rb = (4 * ti) < kBjB ? I1 : J1, cb = (4 * tj) < kBjB ? I2 : J2;
+          float2* up = bj_tile(a.A, nblk, rb, cb);
+          float2* lo = bj_tile(a.A, nblk, cb, rb);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float2* d = up + (((4 * ti) & 15) + i) * kBjB + ((4 * tj) & 15);
+            bj_st2(d, acc[i][0], acc[i][1]);
+            bj_st2(d + 2, acc[i][2], acc[i][3]);
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            float2* d = lo + (((4 * tj) & 15) + j) * kBjB + ((4 * ti) & 15);
+            bj_st2(d, make_float2(acc[0][j].x, -acc[0][j].y), make_float2(acc[1][j].x, -acc[1][j].y));
+            bj_st2(d + 2, make_float2(acc[2][j].x, -acc[2][j].y), make_float2(acc[3][j].x, -acc[3][j].y));
+          }
+        }
+        bj_bar(grp + 1);
+      }
+      if (!grid_sync(a.gb, epoch)) return;
+    }
+    // convergence: grid-wide maxima of |A_ij| (i < j < n) and |A_ii|
+    {
+      float off = 0.f, dm = 0.f;
+      const int64_t tot = (int64_t)nblk * nblk * kBjTile;
+      for (int64_t t = gtid; t < tot; t += nth) {
+        const int64_t tile = t / kBjTile;
+        const int e = (int)(t - tile * kBjTile);
+        const int i = (int)(tile / nblk) * kBjB + (e >> 4), j = (int)(tile % nblk) * kBjB + (e & 15);
+        if (i >= n || j >= n || i > j) continue;
+        const float2 v = a.A[t];
+        if (i == j) dm = fmaxf(dm, fabsf(v.x));
+        else off = fmaxf(off, sqrtf(v.x * v.x + v.y * v.y));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off = fmaxf(off, __shfl_xor_sync(0xffffffffu, off, o));
+        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+      }
+      if ((tid & 31) == 0) {
+        s_red[0][tid >> 5] = off;
+        s_red[1][tid >> 5] = dm;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < kBjThreads / 32; ++w) {
+          s_red[0][0] = fmaxf(s_red[0][0], s_red[0][w]);
+          s_red[1][0] = fmaxf(s_red[1][0], s_red[1][w]);
+        }
+        atomicMax(a.red + 2 * sweep, __float_as_uint(s_red[0][0]));
+        atomicMax(a.red + 2 * sweep + 1, __float_as_uint(s_red[1][0]));
+      }
+      if (!grid_sync(a.gb, epoch)) return;
+      const float offg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep));
+      const float dmg = __uint_as_float(*(volatile unsigned*)(a.red + 2 * sweep + 1));
+      done = offg <= a.tol * fmaxf(dmg, 1e-30f);
+    }
+    ++sweep;
+  }
+  if (gtid == 0) {
+    a.info[0] = 0;
+    a.info[1] = sweep;
+    a.info[2] = 0;
+  }
+  for (int i = gtid; i < n; i += nth)
+    a.diag[i] = (double)bj_tile(a.A, nblk, i >> 4, i >> 4)[(i & 15) * kBjB + (i & 15)].x;
+  for (int64_t t = gtid; t < (int64_t)n * n; t += nth) {
+    const int j = (int)(t / n), i = (int)(t - (int64_t)j * n);
+    const float2 v = bj_tile(a.Q, nblk, i >> 4, j >> 4)[(j & 15) * kBjB + (i & 15)];
+    a.Qout[(size_t)j * a.ldq + i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// FP64 start (n x n, ld lda) -> FP32 tiles of A (row-major tiles, zero
+// padded) and Q = identity (column-major tiles).
+__global__ void k_bj_init(const double2* __restrict__ A, int64_t lda, int n, int nblk,
+                          float2* __restrict__ At, float2* __restrict__ Qt) {
+  const int64_t tot = (int64_t)nblk * nblk * kBjTile;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t / kBjTile;
+    const int e = (int)(t - tile * kBjTile);
+    const int I = (int)(tile / nblk), J = (int)(tile % nblk);
+    const int i = I * kBjB + (e >> 4), j = J * kBjB + (e & 15);  // A: row-major in the tile
+    const double2 z = (i < n && j < n) ? A[(size_t)j * lda + i] : make_double2(0.0, 0.0);
+    At[t] = make_float2((float)z.x, (float)z.y);
+    const int qi = I * kBjB + (e & 15), qj = J * kBjB + (e >> 4);  // Q: column-major
+    Qt[t] = make_float2(qi == qj ? 1.f : 0.f, 0.f);
+  }
+}
+
+static int bj_nblk(int n) {
+  const int nblk = (n + kBjB - 1) / kBjB;
+  return nblk + (nblk & 1);
+}
+static size_t bj_buf_bytes(int n) {
+  const size_t np = (size_t)bj_nblk(n) * kBjB;
+  return (2 * np * np + (size_t)(np / kBjG) * kBjG * kBjG) * sizeof(float2) + 1024;
+}
+
+// Work of one sweep of k_jacobi_blk, in real flops: the phase-2 GEMMs
+// (8 x 32^3 each: two per pair of groups, one per row group and pair group)
+// and phase 1 (31 rounds of 20 flops per element of the block and 10 per
+// element of its rotation, and the Newton-Schulz step's two products).
+double jacobi32_blk_sweep_flops(int n) {
+  const double nb = bj_nblk(n), nb2 = nb / 2;
+  const double g3 = 8.0 * kBjG * kBjG * kBjG;
+  const double p2 = g3 * (2.0 * nb2 * (nb2 - 1) / 2 + nb2 * nb2);
+  const double p1 = nb2 * ((kBjG - 1) * 30.0 * kBjG * kBjG + 2 * g3);
+  return (nb - 1) * (p1 + p2);
+}
+
+// FP32 stage for n > 512 (contract of jacobi32_cluster; info = [0, sweeps,
+// 0]).  Returns false, launching nothing, outside its range.
+static bool jacobi32_blk(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
+                         int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
+                         cudaStream_t st) {
+  if (n < 64 || n > kJacobiMaxN || max_sweeps > 64) return false;
+  const int nblk = bj_nblk(n);
+  const size_t np = (size_t)nblk * kBjB;
+  ensure(w.pj, bj_buf_bytes(n));
+  float2* At = (float2*)w.pj.p;
+  float2* Qt = At + np * np;
+  float2* U = Qt + np * np;
+  unsigned* red = (unsigned*)(U + (size_t)(nblk / 2) * kBjG * kBjG);
+  PWH_CUDA(cudaMemsetAsync(red, 0, 2 * max_sweeps * sizeof(unsigned), st));
+  unsigned* ctl = (unsigned*)w.ctl;
+  PWH_CUDA(cudaMemsetAsync(ctl, 0, 3 * sizeof(unsigned), st));  // barrier words
+  k_bj_init<<<(int)std::min<int64_t>(2048, ((int64_t)np * np + 255) / 256), 256, 0, st>>>(
+      A, lda, n, nblk, At, Qt);
+  PWH_LAUNCH_CHECK();
+  BjArgs a;
+  a.A = At;
+  a.Q = Qt;
+  a.U = U;
+  a.diag = diag;
+  a.Qout = Q;
+  a.ldq = ldq;
+  a.info = info;
+  a.red = red;
+  a.n = n; a.nblk = nblk; a.max_sweeps = max_sweeps;
+  a.tol = (float)tol;
+  a.gb.count = ctl; a.gb.unused = ctl + 1; a.gb.abort = (int*)(ctl + 2);
+  a.gb.err = device_error_word(s);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_jacobi_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBjSmem);
+  });
+  int dev = 0, nsm = 0, per_sm = 0;
+  PWH_CUDA(cudaGetDevice(&dev));
+  PWH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PWH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_blk, kBjThreads, kBjSmem));
+  if (per_sm < 1) return false;
+  void* args[] = {&a};
+  PWH_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_blk, nsm, kBjThreads, args, kBjSmem, st));
+  note_launch();
+  return true;
+}
+
+// FP32 stage: above n = 512 the whole-GPU block Jacobi; for 64 <= n <= 512 the cluster kernel or the
 // position-order one, whichever was faster on the first matrix of the size
 // class (n rounded up to 32): both are run on it (same read-only input, same
 // outputs; the second run's result is kept), timed with CUDA events.  While
@@ -861,7 +1292,7 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
 static bool jacobi32_tuned(System& s, DenseWs& w, const double2* A, int64_t lda, int n, double tol,
                            int max_sweeps, double2* Q, int64_t ldq, double* diag, int* info,
                            cudaStream_t st) {
-  if (n > 512) return jacobi32_pos(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
+  if (n > 512) return jacobi32_blk(s, w, A, lda, n, tol, max_sweeps, Q, ldq, diag, info, st);
   if (n < 64) return false;
   static std::mutex mu;
   static std::map<int, int> choice;  // size class -> 0 cluster, 1 position order
@@ -1100,8 +1531,13 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   cgemm<double>(s, true, n, n, n, one, Q1, n, G, n, zero, A0, n, st);    // A0 = Q^H H Q
   hermitize(A0, n, 0, n, st);
   PWH_CUDA(cudaMemcpyAsync(Q0, Q1, nn * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  // ---- stage 3 (FP64): polish sweeps on the nearly diagonal matrix
-  launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 12, out_buf, st);
+  // ---- stage 3 (FP64): polish sweeps on the nearly diagonal matrix.  Inside
+  // a cluster of (nearly) equal eigenvalues the FP32 basis leaves an
+  // unstructured block of FP32-rounding size that the polish diagonalises
+  // from scratch, at linear convergence (about a factor 2.3 a sweep on
+  // 128-fold degenerate levels), hence the allowance of 30 sweeps; a
+  // warm-started Rayleigh-Ritz matrix needs two or three.
+  launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 30, out_buf, st);
   k_diag_of<double><<<(n + 255) / 256, 256, 0, st>>>(A0, A1, out_buf, n, dg);
   PWH_LAUNCH_CHECK();
   k_select_buf64<<<gq, 256, 0, st>>>(Q0, Q1, out_buf, (int64_t)nn, G);
@@ -1118,11 +1554,15 @@ void jacobi_reserve(DenseWs& w, int nmax, int kmax) {
   // per-column words (the FP32 factorisation needs less)
   ensure(w.chol, 2 * (size_t)kmax * kmax * sizeof(double2) + (size_t)kmax * 16 + 256);
   ensure(w.ns, (size_t)4 * kmax * kmax * sizeof(double2) + 64);
-  if (nmax >= 64 && nmax <= 512) ensure(w.jlog, jacobi32_log_bytes(nmax, 30));
-  if (nmax >= 64 && nmax <= 4096) {
-    ensure(w.jlog, pj_log_bytes(nmax, 30));
-    ensure(w.pj, pj_buf_bytes(nmax));
+  // rotation logs and buffers of the kernels for n <= 512, the block
+  // kernel's tiles above
+  const int nsmall = std::min(nmax, 512);
+  if (nsmall >= 64) {
+    ensure(w.jlog, jacobi32_log_bytes(nsmall, 30));
+    ensure(w.jlog, pj_log_bytes(nsmall, 30));
+    ensure(w.pj, pj_buf_bytes(nsmall));
   }
+  if (nmax > 512 && nmax <= kJacobiMaxN) ensure(w.pj, bj_buf_bytes(nmax));
   if (!w.ctl) PWH_CUDA(cudaMalloc((void**)&w.ctl, 64));
 }
 

@@ -24,6 +24,10 @@ struct DenseWs {
 
 constexpr int kJacobiMaxN = 4096;
 
+// Work of one sweep of the whole-GPU FP32 block Jacobi (subspaces above 512),
+// in real flops.
+double jacobi32_blk_sweep_flops(int n);
+
 // Lowest nk eigenpairs of the n x n Hermitian H (ld = ldh, read only):
 // theta[0..nk) ascending (device), C (n x nk, ld = n, device).  Qkeep
 // (optional, ld = ldk) receives all n eigenvectors sorted by eigenvalue; with

@@ -233,8 +233,10 @@ __global__ void __launch_bounds__(256) ks_zinv(const double2* __restrict__ psi, 
 //   y inverse  pass 1 loads the plane's sticks from W through stick_at (zero
 //              where no stick), pass 2 in place in C[column][y];
 //   x inverse  pass 1 loads the columns of C through xcol (zero elsewhere),
-//              pass 2 in place in R[row][x] times V(r) before the store;
-//   x forward  pass 1 in place, pass 2 stores only the columns back into C;
+//              pass 2 in registers, times V(r), straight into
+//   x forward  pass 1 of the transposed factorisation N = N2 N1 (the
+//              registers of a thread already hold its inputs), then pass 2
+//              stores only the columns back into C;
 //   y forward  pass 1 in place, pass 2 stores only the sticks back into W.
 // No zero fill, scatter or gather pass of its own; row chunks of `rows` rows
 // bound the shared memory.
@@ -284,6 +286,51 @@ __device__ __forceinline__ void fs_pass2_inplace(cx<T>* data, int nf, int ld, co
       cx<T>* xf = data + f * ld + k1;
 #pragma unroll
       for (int k2 = 0; k2 < N2; ++k2) xf[N1 * k2] = post(f, k1 + N1 * k2, w[k2]);
+    }
+  }
+  __syncthreads();
+}
+
+// The middle of the row transforms, in place on nf rows of shared memory (row
+// f at data + f ld): pass 2 of the inverse transform, times V(r), then pass 1
+// of the forward transform in the transposed factorisation N = N2 N1.  Thread
+// (row, k1) loads x[N2 k1 + n2] (n2 < N2) and after the inverse DFT over n2
+// holds the natural-order values x[k1 + N1 m] (m < N2), which are exactly the
+// inputs of the forward transform's first pass for residue k1 mod N1: the
+// forward N2-point DFT over m and the twiddle w^(k1 j) give Y[k1][j], stored
+// at k1 + N1 j.  Ends with __syncthreads().
+template <typename T, int N, int NT>
+__device__ __forceinline__ void fs_rows_mid(cx<T>* data, int nf, int ld, const cx<T>* tw,
+                                            const cx<T>* tw4, const T* Vy) {
+  constexpr int N1 = fft_factor(N), N2 = N / N1;
+  constexpr int per = NT / N1;
+  const int fl = (int)threadIdx.x / N1;
+  const int k1 = (int)threadIdx.x - fl * N1;
+  for (int f0 = 0; f0 < nf; f0 += per) {
+    const int f = f0 + fl;
+    const bool act = fl < per && f < nf;
+    cx<T> w[N2];
+    if (act) {
+      const cx<T>* xf = data + f * ld + N2 * k1;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) w[n2] = xf[n2];
+      dft_reg<T, N2, true, N>(w, tw);
+      const T* vr = Vy + (size_t)f * N + k1;
+#pragma unroll
+      for (int m = 0; m < N2; ++m) w[m] = scl<T>(w[m], vr[N1 * m]);
+      dft_reg<T, N2, false, N>(w, tw);
+#pragma unroll
+      for (int j = 1; j < N2; ++j) {
+        cx<T> t = tw4[k1 * N2 + j];
+        t.y = -t.y;
+        w[j] = mul<T>(w[j], t);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      cx<T>* xf = data + f * ld + k1;
+#pragma unroll
+      for (int j = 0; j < N2; ++j) xf[N1 * j] = w[j];
     }
   }
   __syncthreads();
@@ -349,32 +396,19 @@ __global__ void __launch_bounds__(NT) ks_plane(cx<T>* __restrict__ W, int64_t wb
       for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
     }
     __syncthreads();
-    const T* Vy = Vz + (size_t)y0 * N;
-    fs_pass2_inplace<T, N, NT, true, false>(R, nr, LD, tw, [Vy](int r, int x, cx<T> v) {
-      return scl<T>(v, Vy[(size_t)r * N + x]);
-    });
+    fs_rows_mid<T, N, NT>(R, nr, LD, tw, tw4, Vz + (size_t)y0 * N);
+    // forward pass 2 (N1-point DFTs over k1): X[j + N2 l], only the columns
     for (int t = threadIdx.x; t < nr * N2; t += NT) {
-      const int r = t / N2, n2 = t - r * N2;
-      cx<T>* rr = R + r * LD + n2;
+      const int r = t % nr, j = t / nr;  // neighbouring rows: conflict-free
+      const cx<T>* rr = R + r * LD + N1 * j;
       cx<T> v[N1];
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) v[n1] = rr[N2 * n1];
-      fs_pass1<T, N, false>(v, n2, tw, tw4);
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = rr[k1];
+      dft_reg<T, N1, false, N>(v, tw);
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) rr[N2 * k1] = v[k1];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nr * N1; t += NT) {
-      const int r = t % nr, k1 = t / nr;  // neighbouring rows: conflict-free
-      const cx<T>* rr = R + r * LD + N2 * k1;
-      cx<T> w[N2];
-#pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) w[n2] = rr[n2];
-      dft_reg<T, N2, false, N>(w, tw);
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) {
-        const int c = xcol[k1 + N1 * k2];
-        if (c >= 0) C[c * LD + y0 + r] = w[k2];
+      for (int l = 0; l < N1; ++l) {
+        const int c = xcol[j + N2 * l];
+        if (c >= 0) C[c * LD + y0 + r] = v[l];
       }
     }
     __syncthreads();

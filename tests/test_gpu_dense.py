@@ -1,8 +1,8 @@
 """Subspace diagonalisation (device Jacobi, FP32 sweeps + FP64 polish) against
 LAPACK (numpy.linalg.eigh): random, structured, degenerate and diagonal
 matrices, odd and even sizes, on every FP32 stage (the 16-CTA cluster kernel
-for 64 <= n <= 512, the position-order kernel over the whole GPU beyond, the
-small cluster kernel below 64).  Bar: eigenvalues
+or the position-order kernel for 64 <= n <= 512, the block Jacobi over the
+whole GPU beyond, the small cluster kernel below 64).  Bar: eigenvalues
 within 1e-12 of max |lambda|, eigenvectors orthonormal and with residual
 <= 1e-11 max |lambda|.  The FP32 result (precision="mixed"): eigenvalues within
 2e-6 max |lambda|, orthonormality 2e-6, residual 2e-5 max |lambda| (about 30
@@ -35,9 +35,11 @@ def degenerate(n, seed):
 CASES = [("random", 12), ("random", 7), ("random", 96), ("random", 257), ("degenerate", 12),
          ("degenerate", 40), ("degenerate", 131), ("diagonal", 33), ("kinetic", 60),
          ("random", 384), ("degenerate", 384), ("kinetic", 383), ("random", 440), ("random", 450),
-         # the position-order kernel over the whole GPU (n > 512): odd (a dummy
-         # player), partial tiles, degenerate and Davidson-like spectra
-         ("random", 513), ("degenerate", 640), ("kinetic", 1031), ("random", 1536)]
+         # the block Jacobi over the whole GPU (n > 512): a padded last block,
+         # an odd block count (a padding block), degenerate and Davidson-like
+         # spectra, the largest subspace of the 512-band solve
+         ("random", 513), ("degenerate", 640), ("kinetic", 1031), ("random", 1536),
+         ("kinetic", 1632)]
 
 # bars: (eigenvalue, orthonormality, residual), relative to max |lambda| where scaled
 BARS = {"fp64": (1e-12, 1e-12, 1e-11), "mixed": (2e-6, 2e-6, 2e-5)}
