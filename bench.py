@@ -611,11 +611,20 @@ def run_batched(pwh, syn, torch, ncells=32, nthreads=16):
             "max_dlambda_k_vs_minus_k_ha": tr}
 
 
+# The FP64-accurate FFT passes of the compiled box sizes run in double-float
+# arithmetic (pairs of FP32 numbers) on the FP32 pipes: a double-float add is
+# 20 FP32 instructions, a multiply 7, and the nominal 5 N log2 N flops of a
+# transform are 6 adds and 4 multiplies in 10, so one FP64-equivalent flop
+# costs 14.8 FP32 instructions; the pipes issue 152 x 128 x 2.07e9 of those a
+# second (half the FP32 flop rate, which counts an FMA as two).
+DF_FP32_OPS_PER_FLOP = (6 * 20 + 4 * 7) / 10
+DF_ALU_TFLOPS = FP32_ALU_TFLOPS / 2 / DF_FP32_OPS_PER_FLOP
+
 FAMILY_BOUND = {
     # family: (bound, counter, peak key)
-    "fft_plane_fp32": ("alu", "flops", "fp32"), "fft_plane_fp64": ("alu", "flops", "fp64"),
+    "fft_plane_fp32": ("alu", "flops", "fp32"), "fft_plane_fp64": ("alu", "flops", "df"),
     "fft_z_inverse_fp32": ("hbm", "bytes", "hbm"), "fft_z_forward_fp32": ("hbm", "bytes", "hbm"),
-    "fft_z_inverse_fp64": ("alu", "flops", "fp64"), "fft_z_forward_fp64": ("alu", "flops", "fp64"),
+    "fft_z_inverse_fp64": ("alu", "flops", "df"), "fft_z_forward_fp64": ("alu", "flops", "df"),
     "tc_gemm_becp": ("tensor", "flops", "bf16"), "tc_gemm_backproj": ("tensor", "flops", "bf16"),
     "cgemm_fp64": ("alu", "flops", "fp64"), "cgemm_fp32": ("alu", "flops", "fp32"),
     "jacobi_fp64": ("alu", "flops", "fp64"), "cholqr_fp64": ("alu", "flops", "fp64"),
@@ -635,10 +644,10 @@ FAMILY_BOUND = {
 # launch's flops.  A family whose kernels changed after the capture is absent
 # (traffic null).
 TRAFFIC_PER_LAUNCH = {    # family -> bytes per launch
-    # every k_to_pos32, k_jacobi_pos and k_jacobi_qlog_rows launch of one large
-    # solve (bench.py --profile --steps 1 --warmup 0 under ncu): 2.749 GB over
-    # the 13 Rayleigh-Ritz eigensolves (profiles/jacobi_fp32_large_solve_dram.md)
-    "jacobi_fp32": 2.7494e9 / 13,
+    # every k_bj_init and k_jacobi_blk launch of one large solve (bench.py
+    # --profile --steps 1 --warmup 0 under ncu): 564.5 MB over the 13
+    # Rayleigh-Ritz eigensolves (profiles/jacobi_fp32_large_solve_dram.md)
+    "jacobi_fp32": 564.5e6 / 13,
 }
 TRAFFIC_PER_FLOP = {      # family -> bytes per counted flop
     # one 1088 x 544 x 16,384 FP64-equivalent product on the persistent
@@ -664,6 +673,10 @@ def family_roofline(fam, d, s=None):
         achieved = work / sec / 1e12
     elif key == "fp32":
         peak, unit, psrc = FP32_ALU_TFLOPS, "TFLOP/s", "derived FP32 CUDA-core rate"
+        achieved = work / sec / 1e12
+    elif key == "df":
+        peak, unit = DF_ALU_TFLOPS, "TFLOP/s"
+        psrc = "derived double-float rate (FP32 instruction rate / 14.8)"
         achieved = work / sec / 1e12
     else:
         peak, unit, psrc = FP64_ALU_TFLOPS, "TFLOP/s", "nominal FP64 rate"

@@ -208,6 +208,7 @@ struct System {
   FftPlan plan[3];
   double2* d_tw64 = nullptr;        // twiddle tables, FP64
   float2* d_tw32 = nullptr;         // same, rounded to FP32
+  float4* d_twdf = nullptr;         // same as double-float pairs (re.hi, re.lo, im.hi, im.lo)
   int16_t* d_perm = nullptr;        // digit-reversal tables
   int32_t* d_shell = nullptr;       // shell of each internal plane wave
   double* d_Tshell = nullptr;       // nshell kinetic energies
@@ -217,6 +218,7 @@ struct System {
   double vbar = 0.0;                // mean of V_LOC(r) over the grid
   double* d_v64 = nullptr;
   float* d_v32 = nullptr;
+  float2* d_vdf = nullptr;          // V as double-float pairs (hi, lo)
 
   // projectors (internal plane-wave order, column-major ld = npw)
   int nproj = 0;

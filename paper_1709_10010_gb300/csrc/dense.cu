@@ -1445,12 +1445,21 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
     // ---- stage 1 (FP32): rotate the start to near-diagonal
     const double2* start = H;
     int64_t ld_start = ldh;
+    // FP32-accurate n x n products of the warm start: on the tensor cores
+    // (x3_gemm) above n = 512, where Newton-Schulz steps in FP64 arithmetic
+    // follow, else on the FP32 pipe
+    auto f32 = [&](bool cj, const double2* A, int64_t lda, const double2* B, double2* C) {
+      if (n > 512)
+        cgemm_f32(s, cj, n, n, n, one, A, lda, B, n, zero, C, n, st);
+      else
+        cgemm_f32_simt(s, cj, n, n, n, one, A, lda, B, n, zero, C, n, st);
+    };
     if (warm) {
       // start in the previous eigenbasis: A = Qw^H H Qw (FP32 arithmetic suffices)
       k_warm_basis<<<gq, 256, 0, st>>>(Qkeep, ldk, warm_m0, n, Q1);
       PWH_LAUNCH_CHECK();
-      cgemm_f32_simt(s, false, n, n, n, one, H, ldh, Q1, n, zero, G, n, st);
-      cgemm_f32_simt(s, true, n, n, n, one, Q1, n, G, n, zero, A1, n, st);
+      f32(false, H, ldh, Q1, G);
+      f32(true, Q1, n, G, A1);
       start = A1;
       ld_start = n;
     }
@@ -1472,7 +1481,7 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
       PWH_LAUNCH_CHECK();
     }
     if (warm) {
-      cgemm_f32_simt(s, false, n, n, n, one, Q1, n, Q0, n, zero, A0, n, st);  // Qw Q32
+      f32(false, Q1, n, Q0, A0);  // Qw Q32
       Q = A0;
     }
     if (!polish) {

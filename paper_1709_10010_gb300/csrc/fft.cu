@@ -29,8 +29,10 @@
 #include <cstdlib>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "fft_device.cuh"
 #include "fft_spec.cuh"
 
@@ -87,6 +89,14 @@ void build_fft_plans(System& s) {
   PWH_CUDA(cudaMalloc((void**)&s.d_perm, perm.size() * sizeof(int16_t)));
   PWH_CUDA(cudaMemcpy(s.d_tw64, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
   PWH_CUDA(cudaMemcpy(s.d_tw32, tw32.data(), tw32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  // double-float pairs: hi the FP32 rounding, lo the FP32 rounding of the rest
+  std::vector<float4> twdf(tw.size());
+  for (size_t i = 0; i < tw.size(); ++i) {
+    const float xh = (float)tw[i].x, yh = (float)tw[i].y;
+    twdf[i] = make_float4(xh, (float)(tw[i].x - (double)xh), yh, (float)(tw[i].y - (double)yh));
+  }
+  PWH_CUDA(cudaMalloc((void**)&s.d_twdf, twdf.size() * sizeof(float4)));
+  PWH_CUDA(cudaMemcpy(s.d_twdf, twdf.data(), twdf.size() * sizeof(float4), cudaMemcpyHostToDevice));
   PWH_CUDA(cudaMemcpy(s.d_perm, perm.data(), perm.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
 }
 
@@ -124,6 +134,7 @@ __device__ void fft_block(cx<T>* data, int nfft, int fstride, int estride, const
 template <typename T> struct TwT;
 template <> struct TwT<double> { static const double2* get(const System& s) { return s.d_tw64; } };
 template <> struct TwT<float> { static const float2* get(const System& s) { return s.d_tw32; } };
+template <> struct TwT<df> { static const dfc* get(const System& s) { return (const dfc*)s.d_twdf; } };
 
 template <typename T> __device__ __forceinline__ cx<T> from64(double2 z) {
   return widen_from64<T>(z);
@@ -295,6 +306,16 @@ template <typename T>
 void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* hpsi, int64_t ldh,
                    cudaStream_t st, const float2* vnl, int64_t ldv) {
   if (nb <= 0) return;
+  constexpr bool kDf = std::is_same<T, df>::value;
+  if constexpr (std::is_same<T, double>::value) {
+    // the FP64 local part in double-float arithmetic on the FP32 pipes where
+    // the box has compiled passes (48-bit significands, relative rounding of
+    // about 2^-46 an operation)
+    if (spec_box(s)) {
+      local_kinetic<df>(s, nb, psi, ldp, hpsi, ldh, st, vnl, ldv);
+      return;
+    }
+  }
   const int64_t wband = (int64_t)s.n3 * s.nsticks;
   // batch so that the stick buffer stays around 64 MB (L2-resident between passes)
   int64_t per = wband * (int64_t)sizeof(cx<T>);
@@ -310,14 +331,16 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
   while (rows > 1 && plane_smem<T>(s, rows) > budget) rows = (rows + 1) / 2;
   const size_t psmem = plane_smem<T>(s, rows);
   if (psmem > 227 * 1024) throw Error{PWH_ERR_ARG, "FFT plane does not fit in shared memory"};
-  static std::once_flag attr_once;
-  std::call_once(attr_once, [] {
-    cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  });
-  const T* V = sizeof(T) == 8 ? (const T*)s.d_v64 : (const T*)s.d_v32;
-  const bool dp = sizeof(T) == 8;
+  if constexpr (!kDf) {
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+      cudaFuncSetAttribute(k_plane<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_zinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_zfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+  }
+  const T* V = kDf ? (const T*)s.d_vdf : sizeof(T) == 8 ? (const T*)s.d_v64 : (const T*)s.d_v32;
+  const bool dp = sizeof(T) == 8;  // FP64 and double-float: the FP64 timer families
   // algorithmic work per band (nominal 5 N log2 N flops per complex transform of
   // length N; bytes each pass must move at minimum)
   auto l2 = [](int n) { return std::log2((double)n); };
@@ -337,28 +360,40 @@ void local_kinetic(System& s, int nb, const double2* psi, int64_t ldp, double2* 
     {
       TimedScope ts(s, dp ? KF_FFT_ZINV64 : KF_FFT_ZINV32, st, bb * fz, bb * (16.0 * s.npw + bw));
       if (!spec_pass<T>(SPEC_ZINV, s, pa)) {
-        k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
-                                           s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
-        PWH_LAUNCH_CHECK();
+        if constexpr (kDf) {
+          throw Error{PWH_ERR_ARG, "double-float FFT passes need a compiled box size"};
+        } else {
+          k_zinv<T><<<gz, 256, zsmem, st>>>(psi + (size_t)b0 * ldp, ldp, s.d_stick_off, s.d_stick_of,
+                                             s.d_zpos, s.nsticks, s.plan[2], tw, s.d_perm, W, wband, spb);
+          PWH_LAUNCH_CHECK();
+        }
       }
     }
     dim3 gp(s.n3, bb);
     {
       TimedScope ts(s, dp ? KF_FFT_PLANE64 : KF_FFT_PLANE32, st, bb * fp, bb * 2.0 * bw + bv);
       if (!spec_pass<T>(SPEC_PLANE, s, pa)) {
-        k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
-                                            s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
-        PWH_LAUNCH_CHECK();
+        if constexpr (kDf) {
+          throw Error{PWH_ERR_ARG, "double-float FFT passes need a compiled box size"};
+        } else {
+          k_plane<T><<<gp, 512, psmem, st>>>(W, wband, s.nsticks, s.ncols, s.d_stick_col, s.d_stick_y,
+                                              s.d_col_x, V, s.plan[0], s.plan[1], tw, s.d_perm, rows);
+          PWH_LAUNCH_CHECK();
+        }
       }
     }
     {
       TimedScope ts(s, dp ? KF_FFT_ZFWD64 : KF_FFT_ZFWD32, st, bb * fz,
                     bb * (bw + 2.0 * 16.0 * s.npw + 8.0 * s.npw + (vb ? 8.0 * s.npw : 0.0)));
       if (!spec_pass<T>(SPEC_ZFWD, s, pa)) {
-        k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
-                                           s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp,
-                                           ldp, hpsi + (size_t)b0 * ldh, ldh, spb, vb, ldv);
-        PWH_LAUNCH_CHECK();
+        if constexpr (kDf) {
+          throw Error{PWH_ERR_ARG, "double-float FFT passes need a compiled box size"};
+        } else {
+          k_zfwd<T><<<gz, 256, zsmem, st>>>(W, wband, s.d_stick_off, s.d_stick_of, s.d_zpos, s.nsticks,
+                                             s.plan[2], tw, s.d_perm, s.d_kin, psi + (size_t)b0 * ldp,
+                                             ldp, hpsi + (size_t)b0 * ldh, ldh, spb, vb, ldv);
+          PWH_LAUNCH_CHECK();
+        }
       }
     }
   }

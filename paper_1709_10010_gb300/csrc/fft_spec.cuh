@@ -1,6 +1,6 @@
 // FFT passes specialised at compile time for cubic boxes of common sizes
 // (interface).  The kernels are in fft_spec_impl.cuh, instantiated once per
-// precision in fft_spec32.cu and fft_spec64.cu.
+// arithmetic in fft_spec32.cu, fft_spec64.cu and fft_specdf.cu (double-float).
 #pragma once
 #include "common.cuh"
 
@@ -28,6 +28,23 @@ struct PassArgs {
 };
 
 enum SpecPass { SPEC_ZINV = 0, SPEC_PLANE = 1, SPEC_ZFWD = 2 };
+
+// The compiled box edges (cubic boxes only).
+#define PWH_SPEC_SIZES(X) \
+  X(30) X(36) X(40) X(48) X(50) X(60) X(72) X(80) X(90) X(96) X(120) X(144)
+
+// True when the system's box has compiled passes.
+inline bool spec_box(const System& s) {
+  if (s.n1 != s.n2 || s.n2 != s.n3) return false;
+  switch (s.n1) {
+#define PWH_SPEC_BOX(n) case n:
+    PWH_SPEC_SIZES(PWH_SPEC_BOX)
+#undef PWH_SPEC_BOX
+      return true;
+    default:
+      return false;
+  }
+}
 
 // Launch the specialised kernel of this pass for the system's box and return
 // true, or return false (nothing launched) when the box has no specialisation:

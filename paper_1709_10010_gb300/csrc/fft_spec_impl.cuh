@@ -608,9 +608,7 @@ template <typename T> bool spec_pass(SpecPass pass, System& s, const PassArgs& a
   switch (s.n1) {
 #define PWH_SPEC_CASE(n) \
   case n: spec_launch<T, n>(pass, s, a); return true;
-    PWH_SPEC_CASE(30) PWH_SPEC_CASE(36) PWH_SPEC_CASE(40) PWH_SPEC_CASE(48) PWH_SPEC_CASE(50)
-    PWH_SPEC_CASE(60) PWH_SPEC_CASE(72) PWH_SPEC_CASE(80) PWH_SPEC_CASE(90) PWH_SPEC_CASE(96)
-    PWH_SPEC_CASE(120) PWH_SPEC_CASE(144)
+    PWH_SPEC_SIZES(PWH_SPEC_CASE)
 #undef PWH_SPEC_CASE
     default: return false;
   }

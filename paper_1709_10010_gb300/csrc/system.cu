@@ -85,7 +85,7 @@ System::~System() {
   if (stream) cudaStreamSynchronize(stream);
   free_davidson_ws(dav);
   void* ptrs[] = {d_int_to_pub, d_kin, d_stick_off, d_stick_of, d_zpos, d_stick_col,
-                  d_stick_y, d_col_x, d_stick_at, d_xcol, d_tw64, d_tw32, d_perm, d_v64, d_v32, d_beta64,
+                  d_stick_y, d_col_x, d_stick_at, d_xcol, d_tw64, d_tw32, d_twdf, d_perm, d_v64, d_v32, d_vdf, d_beta64,
                   d_ddiag, d_dfull, d_beta32, d_beta_bf16, d_beta_bf16_t,
                   ws_fft.p, ws_vnl.p, ws_grid.p, ws_tune.p, ws_psi.p, ws_hpsi.p, ws_becp.p, ws_split.p, ws_host.p,
                   ws_tc.p, ws_oz.p, d_err, d_shell, d_Tshell, d_mlp, d_gam_pos,
@@ -272,7 +272,7 @@ static void upload_basis(System& s) {
 // ------------------------------------------------------- device helpers -----
 __global__ void k_potential_layout(const double* __restrict__ v, int n1, int n2, int n3,
                                    double scale, double* __restrict__ v64,
-                                   float* __restrict__ v32) {
+                                   float* __restrict__ v32, float2* __restrict__ vdf) {
   int64_t tot = (int64_t)n1 * n2 * n3;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -284,6 +284,8 @@ __global__ void k_potential_layout(const double* __restrict__ v, int n1, int n2,
     double x = v[((int64_t)i1 * n2 + i2) * n3 + i3] * scale;
     v64[t] = x;
     v32[t] = (float)x;
+    const float hi = __double2float_rn(x);
+    vdf[t] = make_float2(hi, __double2float_rn(x - (double)hi));
   }
 }
 
@@ -408,6 +410,7 @@ pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_devi
     int64_t tot = (int64_t)s.n1 * s.n2 * s.n3;
     if (!s.d_v64) PWH_CUDA(cudaMalloc((void**)&s.d_v64, tot * sizeof(double)));
     if (!s.d_v32) PWH_CUDA(cudaMalloc((void**)&s.d_v32, tot * sizeof(float)));
+    if (!s.d_vdf) PWH_CUDA(cudaMalloc((void**)&s.d_vdf, tot * sizeof(float2)));
     const double* src = v_r;
     double* tmp = nullptr;
     if (!on_device) {
@@ -416,7 +419,7 @@ pwh_status pwh_set_potential(pwh_system* sys, const double* v_r, int32_t on_devi
       src = tmp;
     }
     k_potential_layout<<<1024, 256, 0, s.stream>>>(src, s.n1, s.n2, s.n3, 1.0 / (double)tot,
-                                                  s.d_v64, s.d_v32);
+                                                  s.d_v64, s.d_v32, s.d_vdf);
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (tmp) {
