@@ -48,7 +48,7 @@ METRIC = "Hpsi band-applies/s and Davidson time-to-1e-8 residual, mixed vs FP64,
 WORKLOAD = "large"
 TOL = 1e-8
 SWITCH_TOL = 1e-3
-JD_INNER = 20
+JD_INNER = 16         # inner CG steps of a Jacobi-Davidson correction (sweep: 12, 14, 16, 20, 24)
 MULT = 3
 HPSI_REPS = 20      # H|psi>-only repeats (median reported)
 ACE_NOCC = 32       # occupied bands of the exact-exchange (ACE) leg

@@ -757,7 +757,13 @@ pwh_status davidson_solve(System& s, const pwh_davidson_opts& o, double2* psi, i
     // current residuals: FP32 sweeps to 1e-3 of the last largest residual
     // (relative to the largest diagonal entry), between 4e-7 and 1e-4
     const double tol32 = polish || it == 1 ? 4e-7 : std::min(1e-4, std::max(4e-7, 1e-3 * maxr_target));
-    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32);
+    // the FP64 phase's Ritz vectors feed residuals that stop at o.tol: an
+    // off-diagonal left at 1e-3 o.tol (relative to the largest diagonal
+    // entry) moves a residual by about that much and a Ritz value only to
+    // second order, so the FP64 sweeps stop there (between 1e-13 and 1e-11)
+    const double tol64 = std::min(1e-11, std::max(1e-13, 1e-3 * o.tol));
+    jacobi_eigh(s, w.dense, L.Hs, mmax, m, nb, L.theta, L.C, st, L.Qk, mmax, warm, polish, tol32,
+                tol64);
     sgemm(s, gp, false, (int)npw, nb, m, one, L.V, npw, L.C, m, zero, L.X, npw, st);
     sgemm(s, gp, false, (int)npw, nb, m, one, L.HV, npw, L.C, m, zero, L.HX, npw, st);
     k_residual<<<nb, 256, 0, st>>>(L.X, L.HX, npw, npw, L.theta, w.kin, L.R, L.rn, L.eref, w.m2);

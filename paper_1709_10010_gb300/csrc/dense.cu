@@ -858,9 +858,10 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
 // with one other in each round, so a round holds nblk / 2 pair groups
 // P = (I, J) of 32 indices.  A round has two phases, each closed by a grid
 // barrier:
-//   1. per pair group, one cyclic Jacobi sweep (31 rounds of 16 plane
-//      rotations) of the 32 x 32 diagonal block A_PP in shared memory, the
-//      rotations accumulated into the block rotation U_P (32 x 32), which one
+//   1. per pair group, plane rotations of the 32 x 32 diagonal block A_PP in
+//      shared memory (in the first round of a sweep one cyclic sweep over all
+//      its index pairs, in the others the 256 pairs across its two blocks),
+//      accumulated into the block rotation U_P (32 x 32), which one
 //      Newton-Schulz step brings back to unitary before it is used;
 //   2. every other block of the matrix and the eigenvector basis as small
 //      complex GEMMs on the CUDA cores, groups of 64 threads each taking one
@@ -876,11 +877,13 @@ static bool jacobi32_pos(System& s, DenseWs& w, const double2* A, int64_t lda, i
 constexpr int kBjB = 16;
 constexpr int kBjG = 2 * kBjB;
 constexpr int kBjTile = kBjB * kBjB;
-constexpr int kBjThreads = 512;
+constexpr int kBjThreads = 256;
 constexpr int kBjGroups = kBjThreads / 64;
 constexpr int kBjLd = kBjG + 1;  // padded row of the phase-1 block
-constexpr int kBjGroupElems = 3 * kBjG * kBjG;
-constexpr size_t kBjSmem = (size_t)kBjGroups * kBjGroupElems * sizeof(float2);
+constexpr int kBjGroupElems = 3 * kBjG * kBjG;  // one item's operands
+// two item buffers per group: the next item's operands arrive by cp.async
+// while the current one is multiplied
+constexpr size_t kBjSmem = (size_t)kBjGroups * 2 * kBjGroupElems * sizeof(float2);
 
 struct BjArgs {
   float2* A;          // nblk x nblk tiles, row-major tiles, full Hermitian
@@ -922,9 +925,23 @@ __device__ __forceinline__ void bj_ld2(const float2* p, float2& a, float2& b) {
 __device__ __forceinline__ void bj_st2(float2* p, float2 a, float2 b) {
   *(float4*)p = make_float4(a.x, a.y, b.x, b.y);
 }
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned)
+__device__ __forceinline__ void bj_cp16(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void bj_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void bj_cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-// Phase 1 for pair group (I, J): one sweep on A_PP, U_P to Ub.
-__device__ void bj_phase1(const BjArgs& a, float2* sm, int I, int J, float2* Ub) {
+// Phase 1 for pair group (I, J): rotations on A_PP, their product U_P to Ub.
+// full: one cyclic sweep over all 496 index pairs of the group (31 rounds);
+// else only the 256 pairs across the two blocks (16 rounds, pair (i, 16 +
+// (i + r) mod 16) in round r).  The first round of a sweep runs full, so
+// every index pair of the matrix is rotated once a sweep, as in the scalar
+// cyclic method.
+__device__ void bj_phase1(const BjArgs& a, float2* sm, int I, int J, float2* Ub, bool full) {
   float2* S = sm;                         // 32 x kBjLd
   float2* Us = sm + kBjG * kBjLd;         // 32 x kBjLd
   float4* rot = (float4*)(Us + kBjG * kBjLd);
@@ -936,17 +953,24 @@ __device__ void bj_phase1(const BjArgs& a, float2* sm, int I, int J, float2* Ub)
     Us[row * kBjLd + col] = make_float2(row == col ? 1.f : 0.f, 0.f);
   }
   __syncthreads();
-  for (int ir = 0; ir < kBjG - 1; ++ir) {
+  const int nround = full ? kBjG - 1 : kBjB;
+  for (int ir = 0; ir < nround; ++ir) {
     if (tid < kBjB) {
       int p, q;
-      bj_pair(ir, tid, kBjG, p, q);
+      if (full) {
+        bj_pair(ir, tid, kBjG, p, q);
+      } else {
+        p = tid;
+        q = kBjB + ((tid + ir) & (kBjB - 1));
+      }
       float c;
       float2 sv;
       jacobi_rotation<float>(S[p * kBjLd + q], S[p * kBjLd + p].x, S[q * kBjLd + q].x, c, sv);
       rot[tid] = make_float4(sv.x, sv.y, c, __int_as_float(p | (q << 8)));
     }
     __syncthreads();
-    if (tid < kBjB * kBjB) {
+    static_assert(kBjThreads == kBjB * kBjB, "one 2 x 2 block of S and two U pairs a thread");
+    {
       // 2 x 2 block (pair kk rows, pair ll columns) of J^H S J
       const int kk = tid >> 4, ll = tid & 15;
       const float4 rk = rot[kk], rl = rot[ll];
@@ -966,11 +990,12 @@ __device__ void bj_phase1(const BjArgs& a, float2* sm, int I, int J, float2* Ub)
       S[pk * kBjLd + ql] = y01;
       S[qk * kBjLd + pl] = y10;
       S[qk * kBjLd + ql] = y11;
-    } else {
+    }
+    {
       // U <- U J on the column pairs: [u_p, u_q] <- [c u_p - conj(s) u_q, s u_p + c u_q]
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int idx = tid - kBjB * kBjB + h * (kBjThreads - kBjB * kBjB);
+        const int idx = tid + h * kBjThreads;
         const int row = idx >> 4, l = idx & 15;
         const float4 rl = rot[l];
         const int pl_ql = __float_as_int(rl.w);
@@ -1047,6 +1072,116 @@ __device__ __forceinline__ void bj_gemm(const float2* X, const float2* Y, int ti
   }
 }
 
+// One phase-2 item of round r: a Q item (row group R, pair group P) or a
+// pair of pair groups (P, Qg), P < Qg, numbered row by row after the Q items.
+struct BjItem {
+  bool q;
+  int R, P, Qg, I1, J1, I2, J2;
+};
+__device__ __forceinline__ BjItem bj_decode(int r, int it, int nblk, int nb2, int nQ) {
+  BjItem x;
+  if (it < nQ) {
+    x.q = true;
+    x.R = it / nb2;
+    x.P = it - x.R * nb2;
+    x.Qg = 0;
+    bj_pair(r, x.P, nblk, x.I1, x.J1);
+    x.I2 = x.J2 = 0;
+  } else {
+    x.q = false;
+    x.R = 0;
+    const int t = it - nQ;
+    const int m2 = 2 * nb2 - 1;
+    int P = (int)((m2 - sqrtf((float)m2 * m2 - 8.f * t)) * 0.5f);
+    P = max(0, min(P, nb2 - 2));
+    while (P > 0 && P * (m2 - P) / 2 > t) --P;
+    while ((P + 1) * (m2 - P - 1) / 2 <= t) ++P;
+    x.P = P;
+    x.Qg = P + 1 + (t - P * (m2 - P) / 2);
+    bj_pair(r, x.P, nblk, x.I1, x.J1);
+    bj_pair(r, x.Qg, nblk, x.I2, x.J2);
+  }
+  return x;
+}
+
+// Issue the asynchronous copies of an item's operands into buf (thread lt of
+// its group): X0 the 32 x 32 block (Q item: transposed, X0[k][i] = Q[32 R +
+// i][column k of P], contiguous in i in the column-major tiles; A item:
+// A_PQ row-major), X1 = U_P, X2 = U_Q.
+__device__ __forceinline__ void bj_issue(const BjArgs& a, const BjItem& x, int lt, float2* buf) {
+  float2* X0 = buf;
+  float2* X1 = buf + kBjG * kBjG;
+  float2* X2 = buf + 2 * kBjG * kBjG;
+  const float2* U1 = a.U + (size_t)x.P * kBjG * kBjG;
+  if (x.q) {
+    for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
+      const int e = 2 * v, k = e >> 5, i = e & 31;
+      const float2* src = bj_tile(a.Q, a.nblk, 2 * x.R + (i >> 4), k < kBjB ? x.I1 : x.J1);
+      bj_cp16(X0 + e, src + (k & 15) * kBjB + (i & 15));
+      bj_cp16(X1 + e, U1 + e);
+    }
+  } else {
+    const float2* U2 = a.U + (size_t)x.Qg * kBjG * kBjG;
+    for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
+      const int e = 2 * v, row = e >> 5, col = e & 31;
+      const float2* src =
+          bj_tile(a.A, a.nblk, row < kBjB ? x.I1 : x.J1, col < kBjB ? x.I2 : x.J2);
+      bj_cp16(X0 + e, src + (row & 15) * kBjB + (col & 15));
+      bj_cp16(X1 + e, U1 + e);
+      bj_cp16(X2 + e, U2 + e);
+    }
+  }
+}
+
+// Multiply an item whose operands are in buf and store the result:
+// Q_RP <- Q_RP U_P, or A_PQ <- U_P^H A_PQ U_Q with A_QP its conjugate
+// transpose.  Every thread of the group; X0 is reused for T^T.
+__device__ __forceinline__ void bj_item(const BjArgs& a, const BjItem& x, int ti, int tj, int grp,
+                                        float2* buf) {
+  float2* X0 = buf;
+  float2* X1 = buf + kBjG * kBjG;
+  float2* X2 = buf + 2 * kBjG * kBjG;
+  float2 acc[4][4];
+  if (x.q) {
+    bj_gemm<false>(X0, X1, ti, tj, acc);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = 4 * tj + j;
+      float2* dst = bj_tile(a.Q, a.nblk, 2 * x.R + (ti >> 2), col < kBjB ? x.I1 : x.J1) +
+                    (col & 15) * kBjB + ((4 * ti) & 15);
+      bj_st2(dst, acc[0][j], acc[1][j]);
+      bj_st2(dst + 2, acc[2][j], acc[3][j]);
+    }
+    return;
+  }
+  bj_gemm<true>(X1, X0, ti, tj, acc);  // T = U_P^H A_PQ
+  bj_bar(grp + 1);
+  // X0 <- T^T (row k holds column k of T)
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2* d = X0 + (4 * tj + j) * kBjG + 4 * ti;
+    bj_st2(d, acc[0][j], acc[1][j]);
+    bj_st2(d + 2, acc[2][j], acc[3][j]);
+  }
+  bj_bar(grp + 1);
+  bj_gemm<false>(X0, X2, ti, tj, acc);  // T U_Q
+  const int rb = (4 * ti) < kBjB ? x.I1 : x.J1, cb = (4 * tj) < kBjB ? x.I2 : x.J2;
+  float2* up = bj_tile(a.A, a.nblk, rb, cb);
+  float2* lo = bj_tile(a.A, a.nblk, cb, rb);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2* d = up + (((4 * ti) & 15) + i) * kBjB + ((4 * tj) & 15);
+    bj_st2(d, acc[i][0], acc[i][1]);
+    bj_st2(d + 2, acc[i][2], acc[i][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float2* d = lo + (((4 * tj) & 15) + j) * kBjB + ((4 * ti) & 15);
+    bj_st2(d, make_float2(acc[0][j].x, -acc[0][j].y), make_float2(acc[1][j].x, -acc[1][j].y));
+    bj_st2(d + 2, make_float2(acc[2][j].x, -acc[2][j].y), make_float2(acc[3][j].x, -acc[3][j].y));
+  }
+}
+
 __global__ void __launch_bounds__(kBjThreads, 1) k_jacobi_blk(BjArgs a) {
   extern __shared__ __align__(16) unsigned char bjs[];
   float2* sm = (float2*)bjs;
@@ -1056,10 +1191,7 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_jacobi_blk(BjArgs a) {
   const int nblk = a.nblk, nb2 = nblk / 2, n = a.n;
   const int nA = nb2 * (nb2 - 1) / 2, nQ = nb2 * nb2, nItems = nQ + nA;
   const int gtid = blockIdx.x * blockDim.x + tid, nth = gridDim.x * blockDim.x;
-  float2* gs = sm + (size_t)grp * kBjGroupElems;
-  float2* X0 = gs;
-  float2* X1 = gs + kBjG * kBjG;
-  float2* X2 = gs + 2 * kBjG * kBjG;
+  float2* gs = sm + (size_t)grp * 2 * kBjGroupElems;  // the group's two item buffers
   unsigned epoch = 0;
   int sweep = 0;
   bool done = false;
@@ -1069,81 +1201,32 @@ __global__ void __launch_bounds__(kBjThreads, 1) k_jacobi_blk(BjArgs a) {
       for (int k = blockIdx.x; k < nb2; k += gridDim.x) {
         int I, J;
         bj_pair(r, k, nblk, I, J);
-        bj_phase1(a, sm, I, J, a.U + (size_t)k * kBjG * kBjG);
+        bj_phase1(a, sm, I, J, a.U + (size_t)k * kBjG * kBjG, r == 0);
       }
       if (!grid_sync(a.gb, epoch)) return;
-      // ---- phase 2: Q row groups, then the off-diagonal pair blocks
-      for (int it = blockIdx.x * kBjGroups + grp; it < nItems; it += gridDim.x * kBjGroups) {
-        float2 acc[4][4];
-        if (it < nQ) {
-          const int R = it / nb2, P = it - R * nb2;
-          int I, J;
-          bj_pair(r, P, nblk, I, J);
-          // X0[k][i] = Q[32 R + i][col k of P] (column-major tiles: contiguous in i)
-          for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
-            const int e = 2 * v, k = e >> 5, i = e & 31;
-            const float2* src = bj_tile(a.Q, nblk, 2 * R + (i >> 4), k < kBjB ? I : J);
-            *(float4*)(X0 + e) = *(const float4*)(src + (k & 15) * kBjB + (i & 15));
-            *(float4*)(X1 + e) = *(const float4*)(a.U + (size_t)P * kBjG * kBjG + e);
-          }
-          bj_bar(grp + 1);
-          bj_gemm<false>(X0, X1, ti, tj, acc);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int col = 4 * tj + j;
-            float2* dst = bj_tile(a.Q, nblk, 2 * R + (ti >> 2), col < kBjB ? I : J) +
-                          (col & 15) * kBjB + ((4 * ti) & 15);
-            bj_st2(dst, acc[0][j], acc[1][j]);
-            bj_st2(dst + 2, acc[2][j], acc[3][j]);
-          }
-        } else {
-          // pair of groups (P, Q), P < Q, numbered row by row
-          const int t = it - nQ;
-          const int m2 = 2 * nb2 - 1;
-          int P = (int)((m2 - sqrtf((float)m2 * m2 - 8.f * t)) * 0.5f);
-          P = max(0, min(P, nb2 - 2));
-          while (P > 0 && P * (m2 - P) / 2 > t) --P;
-          while ((P + 1) * (m2 - P - 1) / 2 <= t) ++P;
-          const int Qg = P + 1 + (t - P * (m2 - P) / 2);
-          int I1, J1, I2, J2;
-          bj_pair(r, P, nblk, I1, J1);
-          bj_pair(r, Qg, nblk, I2, J2);
-          for (int v = lt; v < kBjG * kBjG / 2; v += 64) {
-            const int e = 2 * v, row = e >> 5, col = e & 31;
-            const float2* src = bj_tile(a.A, nblk, row < kBjB ? I1 : J1, col < kBjB ? I2 : J2);
-            *(float4*)(X0 + e) = *(const float4*)(src + (row & 15) * kBjB + (col & 15));
-            *(float4*)(X1 + e) = *(const float4*)(a.U + (size_t)P * kBjG * kBjG + e);
-            *(float4*)(X2 + e) = *(const float4*)(a.U + (size_t)Qg * kBjG * kBjG + e);
-          }
-          bj_bar(grp + 1);
-          bj_gemm<true>(X1, X0, ti, tj, acc);  // T = U_P^H A_PQ
-          bj_bar(grp + 1);
-          // X0 <- T^T (row k holds column k of T)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float2* d = X0 + (4 * tj + j) * kBjG + 4 * ti;
-            bj_st2(d, acc[0][j], acc[1][j]);
-            bj_st2(d + 2, acc[2][j], acc[3][j]);
-          }
-          bj_bar(grp + 1);
-          bj_gemm<false>(X0, X2, ti, tj, acc);  // T U_Q
-          const int rb = (4 * ti) < kBjB ? I1 : J1, cb = (4 * tj) < kBjB ? I2 : J2;
-          float2* up = bj_tile(a.A, nblk, rb, cb);
-          float2* lo = bj_tile(a.A, nblk, cb, rb);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float2* d = up + (((4 * ti) & 15) + i) * kBjB + ((4 * tj) & 15);
-            bj_st2(d, acc[i][0], acc[i][1]);
-            bj_st2(d + 2, acc[i][2], acc[i][3]);
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float2* d = lo + (((4 * tj) & 15) + j) * kBjB + ((4 * ti) & 15);
-            bj_st2(d, make_float2(acc[0][j].x, -acc[0][j].y), make_float2(acc[1][j].x, -acc[1][j].y));
-            bj_st2(d + 2, make_float2(acc[2][j].x, -acc[2][j].y), make_float2(acc[3][j].x, -acc[3][j].y));
-          }
+      // ---- phase 2: Q row groups, then the off-diagonal pair blocks; each
+      // group of 64 threads walks its items with the next item's operands in
+      // flight (cp.async into its other buffer) while it multiplies the
+      // current one
+      {
+        const int stride = gridDim.x * kBjGroups;
+        int it = blockIdx.x * kBjGroups + grp;
+        int b = 0;
+        if (it < nItems) bj_issue(a, bj_decode(r, it, nblk, nb2, nQ), lt, gs);
+        bj_cp_commit();
+        for (; it < nItems; it += stride) {
+          float2* cur = gs + (size_t)b * kBjGroupElems;
+          if (it + stride < nItems)
+            bj_issue(a, bj_decode(r, it + stride, nblk, nb2, nQ), lt,
+                     gs + (size_t)(b ^ 1) * kBjGroupElems);
+          bj_cp_commit();
+          bj_cp_wait<1>();  // this thread's copies of the current item have landed
+          bj_bar(grp + 1);  // and every thread's
+          bj_item(a, bj_decode(r, it, nblk, nb2, nQ), ti, tj, grp, cur);
+          bj_bar(grp + 1);  // the buffer is free for the item after next
+          b ^= 1;
         }
-        bj_bar(grp + 1);
+        bj_cp_wait<0>();
       }
       if (!grid_sync(a.gb, epoch)) return;
     }
@@ -1227,14 +1310,16 @@ static size_t bj_buf_bytes(int n) {
 
 // Work of one sweep of k_jacobi_blk, in real flops: the phase-2 GEMMs
 // (8 x 32^3 each: two per pair of groups, one per row group and pair group)
-// and phase 1 (31 rounds of 20 flops per element of the block and 10 per
-// element of its rotation, and the Newton-Schulz step's two products).
+// and phase 1 (rotation rounds of 20 flops per element of the block and 10
+// per element of its rotation: 31 in the first round of a sweep, 16 in the
+// others; and the Newton-Schulz step's two products).
 double jacobi32_blk_sweep_flops(int n) {
   const double nb = bj_nblk(n), nb2 = nb / 2;
   const double g3 = 8.0 * kBjG * kBjG * kBjG;
   const double p2 = g3 * (2.0 * nb2 * (nb2 - 1) / 2 + nb2 * nb2);
-  const double p1 = nb2 * ((kBjG - 1) * 30.0 * kBjG * kBjG + 2 * g3);
-  return (nb - 1) * (p1 + p2);
+  const double rot = (kBjG - 1) + (double)kBjB * (nb - 2);  // rotation rounds a sweep
+  const double p1 = nb2 * (rot * 30.0 * kBjG * kBjG + (nb - 1) * 2 * g3);
+  return (nb - 1) * p2 + p1;
 }
 
 // FP32 stage for n > 512 (contract of jacobi32_cluster; info = [0, sweeps,
@@ -1412,7 +1497,7 @@ static size_t jacobi_ws_bytes(size_t nn, int n) {
 
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep, int64_t ldk,
-                 int warm_m0, bool polish, double tol32) {
+                 int warm_m0, bool polish, double tol32, double tol64) {
   if (n > kJacobiMaxN) throw Error{PWH_ERR_ARG, "subspace larger than the Jacobi limit"};
   const size_t nn = (size_t)n * n;
   ensure(w.jac, jacobi_ws_bytes(nn, n));
@@ -1546,7 +1631,7 @@ void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, in
   // from scratch, at linear convergence (about a factor 2.3 a sweep on
   // 128-fold degenerate levels), hence the allowance of 30 sweeps; a
   // warm-started Rayleigh-Ritz matrix needs two or three.
-  launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, 1e-13, 30, out_buf, st);
+  launch_jacobi<double>(s, w, A0, A1, Q0, Q1, n, tol64, 30, out_buf, st);
   k_diag_of<double><<<(n + 255) / 256, 256, 0, st>>>(A0, A1, out_buf, n, dg);
   PWH_LAUNCH_CHECK();
   k_select_buf64<<<gq, 256, 0, st>>>(Q0, Q1, out_buf, (int64_t)nn, G);

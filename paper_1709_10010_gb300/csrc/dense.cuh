@@ -37,10 +37,12 @@ double jacobi32_blk_sweep_flops(int n);
 // FP64 sweeps); otherwise the FP32 result (eigenvalues to about FP32 rounding
 // of ||H||, eigenvectors orthonormal to about FP32 rounding).  tol32: the
 // FP32 sweeps stop at max|A_ij| <= tol32 max|A_ii| (4e-7, about five FP32
-// roundings, lets one FP64 sweep finish the polish).
+// roundings, lets one FP64 sweep finish the polish); the FP64 sweeps at
+// max|A_ij| <= tol64 max|A_ii|.
 void jacobi_eigh(System& s, DenseWs& w, const double2* H, int64_t ldh, int n, int nk,
                  double* theta, double2* C, cudaStream_t st, double2* Qkeep = nullptr,
-                 int64_t ldk = 0, int warm_m0 = 0, bool polish = true, double tol32 = 4e-7);
+                 int64_t ldk = 0, int warm_m0 = 0, bool polish = true, double tol32 = 4e-7,
+                 double tol64 = 1e-13);
 
 // FP32 stage of jacobi_eigh in one 16-CTA thread-block cluster with the matrix
 // in distributed shared memory (jacobi_dsm.cu): sweeps of the n x n Hermitian

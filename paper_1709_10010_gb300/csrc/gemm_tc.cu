@@ -1050,6 +1050,7 @@ static OzGeom oz_geom(bool conjA, int M, int N, int K) {
 // its larger output dimension, which give the same bits as the whole segment
 // (the exponents belong to single rows of op(A) and single columns of B).
 constexpr size_t kOzPartCap = (size_t)4 << 30;
+constexpr int kOzSegChunks = 8;
 
 struct OzSplit {
   int kseg;      // complex K per segment
@@ -1058,9 +1059,12 @@ struct OzSplit {
 };
 static OzSplit oz_split_of(bool conjA, int M, int N, int K) {
   OzSplit sp{K, M >= N, M >= N ? M : N};
-  // at most 2^20 real K a segment (at most 512 chunks, OZ_PAIRS x chunks
-  // partials along grid z)
-  const int kmax = conjA ? (1 << 20) : (1 << 19);
+  // at most kOzSegChunks 4096-wide real chunks a segment: the slices are
+  // stored [row][slice * seg + k], so the row pitch grows with the segment
+  // and one chunk's tiles spread over as many memory pages as there are rows
+  // (a 544 x 544 x 161,235 A^H B product ran its 25-chunk first segment at
+  // 0.57 ms a chunk and its 15-chunk second one at 0.36 ms)
+  const int kmax = (conjA ? 64 : 32) * OZ_CHUNK_KB * kOzSegChunks;
   if (K > kmax) sp.kseg = kmax;
   const OzGeom g = oz_geom(conjA, M, N, sp.kseg);
   if (g.bytes_p <= kOzPartCap) return sp;
