@@ -294,6 +294,21 @@ static bool slice_grid_ok(bool conjA, int M, int N, int K) {
   return N <= 65535 && (conjA ? M <= 65535 : K <= 65535 * 32);
 }
 
+// Whether a product of FP32-level accuracy takes the tensor-core path: large
+// enough, and not too narrow.  Narrow products of moderate length stay on the
+// FP32 pipe (the tensor-core path's slicing and reduction cost more than they
+// save below about 48 columns of A^H B and 96 of A B at 34k plane waves).  On
+// long products (K or M of at least 65,536) the tensor-core path costs about
+// the slicing of the long operand whatever the width, while the FP32-pipe
+// kernel reaches only about 1 TB/s: at 161,235 plane waves a 544 x 19 A^H B
+// took 0.93 ms against 1.82 ms and a 161,235 x 19 x 544 A B 0.97 against
+// 1.18 ms (the FP32 pipe still won at 6 columns of A B, 0.64 against 1.50).
+static bool tc_width_ok(bool conjA, int M, int N, int K) {
+  const int narrow = conjA ? std::min(M, N) : N;
+  if (conjA ? K >= 65536 : M >= 65536) return narrow >= (conjA ? 1 : 16);
+  return narrow >= (conjA ? 48 : 96);
+}
+
 template <typename T>
 void cgemm(System& s, bool conjA, int M, int N, int K, cx<T> alpha, const cx<T>* A, int64_t lda,
            const cx<T>* B, int64_t ldb, cx<T> beta, cx<T>* C, int64_t ldc, cudaStream_t st,
@@ -319,8 +334,7 @@ void cgemm_r16(System& s, bool conjA, int M, int N, int K, double2 alpha, const 
                cudaStream_t st) {
   // the tensor-core path above the same size and width thresholds as
   // cgemm_f32 (narrower products: the FP32 pipe, more accurate anyway)
-  const int narrow = conjA ? std::min(M, N) : N;
-  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
+  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && tc_width_ok(conjA, M, N, K) &&
       slice_grid_ok(conjA, M, N, K)) {
     x2_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     return;
@@ -332,11 +346,7 @@ void cgemm_f32(System& s, bool conjA, int M, int N, int K, double2 alpha, const 
                int64_t lda, const double2* B, int64_t ldb, double2 beta, double2* C, int64_t ldc,
                cudaStream_t st) {
   // large products run on the tensor cores as three-slice BF16 products
-  // (narrow products stay on the FP32 pipe: the tensor-core path's slicing and
-  // reduction cost more than it saves below about 48 columns of A^H B and 96
-  // of A B)
-  const int narrow = conjA ? std::min(M, N) : N;
-  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && narrow >= (conjA ? 48 : 96) &&
+  if (K > 0 && 8.0 * M * (double)N * K >= kX3MinFlops && tc_width_ok(conjA, M, N, K) &&
       slice_grid_ok(conjA, M, N, K)) {
     x3_gemm(s, conjA, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, st);
     return;

@@ -32,7 +32,11 @@ SHAPES = [(63, 1, 17), (129, 5, 40), (300, 8, 33), (257, 9, 100), (64, 16, 64), 
           # the tensor cores: long and short K, padded chunks, narrow outputs
           (34265, 128, 384), (5000, 40, 1200), (3000, 7, 2000), (576, 33, 34265),
           # narrow inner products of few rows (the Jacobi-Davidson projections)
-          (128, 9, 34265), (100, 20, 5000)]
+          (128, 9, 34265), (100, 20, 5000),
+          # long narrow products: A^H B over K >= 65,536 and A B over M >= 65,536
+          # take the tensor cores down to 1 and 16 columns (6 stays on the FP32
+          # pipe for A B)
+          (128, 5, 80000), (70000, 20, 200), (70000, 6, 300)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
