@@ -644,10 +644,8 @@ FAMILY_BOUND = {
 # launch's flops.  A family whose kernels changed after the capture is absent
 # (traffic null).
 TRAFFIC_PER_LAUNCH = {    # family -> bytes per launch
-    # every k_bj_init and k_jacobi_blk launch of one large solve (bench.py
-    # --profile --steps 1 --warmup 0 under ncu): 564.5 MB over the 13
-    # Rayleigh-Ritz eigensolves (profiles/jacobi_fp32_large_solve_dram.md)
-    "jacobi_fp32": 564.5e6 / 13,
+    # (the FP32 Jacobi's capture, profiles/jacobi_fp32_large_solve_dram.md,
+    # predates the kernel's current phase-1 schedule and double buffering)
 }
 TRAFFIC_PER_FLOP = {      # family -> bytes per counted flop
     # one 1088 x 544 x 16,384 FP64-equivalent product on the persistent
