@@ -53,7 +53,13 @@ typedef enum {
 } pwh_status;
 
 typedef enum {
-  PWH_FP64 = 0,       /* every step in FP64 */
+  PWH_FP64 = 0,       /* every step to FP64 accuracy: FP64 arithmetic, except
+                         the FFT passes of the compiled cubic boxes (edges 30,
+                         36, 40, 48, 50, 60, 72, 80, 90, 96, 120, 144), which
+                         compute in double-float (pairs of FP32 numbers, 48
+                         significant bits, about 2^-46 relative rounding per
+                         operation), and the large GEMMs (exact integer-slice
+                         products on the tensor cores) */
   PWH_MIXED = 1,      /* FFT + potential in FP32; projector GEMMs on the BF16
                          tensor cores with FP32 accumulation, each operand split
                          into two BF16 terms (hi*hi + hi*lo + lo*hi, about 16
@@ -515,8 +521,9 @@ pwh_status pwh_subspace_cholqr(pwh_system* sys, int32_t precision, int32_t k, co
  * at least 2e8 flops as exact integer-slice products on the tensor cores);
  * PWH_MIXED: operands rounded to FP32, FP32 accumulation (relative error about
  * sqrt(K) 1e-7), result widened (products of at least 4e8 flops and 48
- * columns of A^H B or 96 of A B as three BF16 slices of each FP32 operand, six
- * slice products on the tensor cores).
+ * columns of A^H B or 96 of A B, or 1 and 16 columns when K (A^H B) or M (A B)
+ * is at least 65,536, as three BF16 slices of each FP32 operand, six slice
+ * products on the tensor cores).
  * Asynchronous on the system's stream; uses the system's workspaces (one GEMM
  * at a time per system). */
 pwh_status pwh_subspace_gemm(pwh_system* sys, int32_t precision, int32_t conj_a, int32_t M,
