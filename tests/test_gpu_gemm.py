@@ -36,7 +36,7 @@ SHAPES = [(63, 1, 17), (129, 5, 40), (300, 8, 33), (257, 9, 100), (64, 16, 64), 
           # long narrow products: A^H B over K >= 65,536 and A B over M >= 65,536
           # take the tensor cores down to 1 and 16 columns (6 stays on the FP32
           # pipe for A B)
-          (128, 5, 80000), (70000, 20, 200), (70000, 6, 300)]
+          (128, 5, 80000), (640, 1, 80000), (70000, 20, 200), (70000, 6, 300)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
